@@ -1,0 +1,210 @@
+/*
+ * ddamg.h - C ABI of libddamg.so, a GB300 (sm_103a) implementation of the
+ * two-level DD-alpha-AMG solver for the clover-improved Wilson Dirac equation
+ * D z = b (Frommer, Kahl, Krieg, Leder, Rottmann, arXiv:1303.1377).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: periodic L0 x L1 x L2 x L3 (L0 = time), sites in lexicographic order
+ *   with x0 slowest and x3 fastest (Sec. 2.2).
+ * Complex numbers: interleaved (re, im) pairs of double (or float where stated).
+ * Gauge field U: [site][mu 0..3][row 0..2][col 0..2] complex, U_mu(x) in SU(3)
+ *   on the link from x to x + mu (Sec. 2.2).
+ * Spinor field: [site][spin 0..3][colour 0..2] complex, 12 components per site,
+ *   colour fastest (Sec. 2.1).  A batch of n_rhs spinors is n_rhs such fields
+ *   back to back.
+ * Coarse vector: [coarse site][2N] complex, coarse sites = lattice-blocks in
+ *   lexicographic order of their block coordinates; component h*N + k is the
+ *   k-th basis vector of the aggregate with spins {0,1} (h = 0) or {2,3} (h = 1)
+ *   (standard aggregation, Sec. 3.2, Definition).
+ * Pointers: every data pointer may be host or device memory (CUDA unified
+ *   addressing decides).  Host data is copied through the handle's stream;
+ *   device data must be readable/writable on the handle's device.  The caller
+ *   keeps ownership of everything it passes; the handle owns all its device state.
+ * Errors: every call returns a ddamg_status (0 = success, negative = error) and
+ *   never throws.  ddamg_error_string() names a status; ddamg_last_error()
+ *   gives a one-line description of the most recent failure on this thread.
+ * Threads/streams: a handle is not thread safe; all its work is issued on its
+ *   stream (ddamg_set_stream), and every call returns after that work has
+ *   completed unless stated otherwise.
+ */
+#ifndef DDAMG_H
+#define DDAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DDAMG_OK = 0,
+    DDAMG_ERR_INVALID_ARG = -1,   /* bad size, layout, null pointer or parameter */
+    DDAMG_ERR_OOM = -2,           /* device allocation failed (or the test hook forced it) */
+    DDAMG_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
+    DDAMG_ERR_NOT_CONVERGED = -4, /* iteration cap reached; z holds the best iterate */
+    DDAMG_ERR_NONFINITE = -5,     /* NaN/Inf met in a residual norm */
+    DDAMG_ERR_TIMEOUT = -6,       /* wall-clock limit of the call exceeded */
+    DDAMG_ERR_NOT_READY = -7,     /* the handle has no interpolation yet (setup missing) */
+    DDAMG_ERR_RANK = -8           /* test vectors linearly dependent on an aggregate */
+} ddamg_status;
+
+/* Arithmetic of the V-cycle (smoother, P/P^H, coarse solve).  The outer FGMRES,
+ * its Arnoldi process and the final residual are FP64 in every mode (Sec. 6). */
+typedef enum {
+    DDAMG_PREC_DOUBLE = 0, /* V-cycle in FP64 */
+    DDAMG_PREC_SINGLE = 1, /* V-cycle in FP32 (the paper's mixed precision, Sec. 6) */
+    DDAMG_PREC_HALF = 2    /* V-cycle in FP32 with D_c and P stored in FP16 (FP32 accumulation) */
+} ddamg_precision;
+
+typedef struct {
+    int dims[4]; /* L0 (time), L1, L2, L3 */
+} ddamg_lattice;
+
+/* Method parameters; ddamg_default_params() fills the defaults of Table 1 (Sec. 6). */
+typedef struct {
+    int n_inv;            /* setup iterations of Algorithm 2 (6) */
+    int n_vec;            /* test vectors N (20) */
+    int block[4];         /* lattice-block of both the SAP domains and the aggregates (4,4,4,4) */
+    double coarse_tol;    /* relative residual reduction of the coarse solve (5e-2) */
+    int coarse_restart;   /* GMRES restart length on the coarse system (30, Sec. 6) */
+    int coarse_maxiter;   /* cap on coarse GMRES steps per coarse solve (1000) */
+    int n_kv;             /* FGMRES restart length (25) */
+    double tol;           /* outer relative residual tolerance (1e-10) */
+    int max_outer;        /* cap on FGMRES iterations per solve (10000) */
+    int nu;               /* SAP post-smoothing iterations (2) */
+    int mr_steps;         /* MR steps of the block solver (4) */
+    int precision;        /* ddamg_precision (DDAMG_PREC_SINGLE) */
+    int rebuild_after_last; /* 1: rebuild P, D_c after the last setup update (1) */
+    uint64_t seed;        /* seed of the initial random test vectors (1) */
+    double time_limit_s;  /* wall-clock limit per solve call, <= 0: none (0) */
+} ddamg_params;
+
+/* Statistics of one solve (the quantities reported in Tables 3-9). */
+typedef struct {
+    int iterations;        /* FGMRES iterations (max over the batch) */
+    int restarts;          /* FGMRES restarts */
+    long long coarse_iterations; /* total coarse GMRES steps */
+    int vcycles;           /* preconditioner applications */
+    double rel_residual;   /* final ||b - D z|| / ||b|| in FP64 (max over the batch) */
+    double solve_seconds;  /* wall time of the call */
+    double coarse_seconds; /* part of it spent in the coarse solves */
+    int status;            /* ddamg_status of this solve */
+} ddamg_stats;
+
+typedef struct ddamg_handle ddamg_handle;
+
+void ddamg_default_params(ddamg_params* p);
+const char* ddamg_error_string(int status);
+const char* ddamg_last_error(void);
+
+/* Build the operator D(U, m0, c_sw) of Sec. 2.2 (clover term and even-site
+ * inverses are formed here) and run the adaptive setup of Algorithm 2 (Sec. 5)
+ * from N seeded random test vectors, leaving P and D_c = P^H D P ready.
+ * lat: every extent divisible by params->block, with an even number (>= 2) of
+ *   blocks per direction and even block extents; N <= 64.
+ * U: gauge field (layout above), copied.  *out receives a new handle.
+ * Errors: INVALID_ARG, OOM, CUDA, RANK. */
+int ddamg_setup(const ddamg_lattice* lat, const double* U, double m0, double c_sw,
+                const ddamg_params* params, ddamg_handle** out);
+
+/* Like ddamg_setup but without the adaptive setup: only D is built.
+ * Interpolation comes later from ddamg_setup_from_vectors or ddamg_run_setup. */
+int ddamg_create(const ddamg_lattice* lat, const double* U, double m0, double c_sw,
+                 const ddamg_params* params, ddamg_handle** out);
+
+/* Run Algorithm 2 (Sec. 5) on the handle from the given initial vectors
+ * v0 [N spinor fields] (NULL: seeded Gaussian vectors from params->seed). */
+int ddamg_run_setup(ddamg_handle* h, const double* v0);
+
+/* Build P (local orthonormalisation, Sec. 3.1) and D_c (Sec. 3.2) directly from
+ * N given test vectors V [N spinor fields]; N must equal params->n_vec. */
+int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N);
+
+/* Copy the current test vectors (N spinor fields, FP64) into V. */
+int ddamg_get_vectors(const ddamg_handle* h, double* V);
+
+/* Solve D z = b to ||b - D z|| <= tol ||b|| by FGMRES(n_kv) right-preconditioned
+ * with one V-cycle (Sec. 5).  b, z: one spinor field each; z is the initial
+ * guess on entry (pass zeros for the paper's zero guess) and the solution on
+ * exit.  tol <= 0 uses params->tol.  st may be NULL.
+ * Errors: INVALID_ARG, NOT_READY, OOM, CUDA, NOT_CONVERGED (z = last iterate),
+ * NONFINITE, TIMEOUT. */
+int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_stats* st);
+
+/* n_rhs independent solves in one batched launch sequence (multi-RHS kernels):
+ * b, z: n_rhs spinor fields each.  Each right-hand side keeps its own Krylov
+ * space and stops at its own convergence; st (may be NULL) points to n_rhs stats. */
+int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol,
+                      ddamg_stats* st);
+
+/* out = D in (Sec. 2.2, FP64) for n_rhs spinor fields. */
+int ddamg_apply_D(ddamg_handle* h, const double* in, double* out, int n_rhs);
+
+/* out = D in in FP32 arithmetic on FP32 fields ([site][spin][colour] complex float). */
+int ddamg_apply_D_f32(ddamg_handle* h, const float* in, float* out, int n_rhs);
+
+/* out = M_SAP^(nu) in (Sec. 2.3) in the V-cycle precision; FP64 fields in/out. */
+int ddamg_apply_sap(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);
+
+/* Coarse restriction out = P^H in (fine -> coarse) and prolongation out = P in
+ * (coarse -> fine), Sec. 3.1; FP64 fields, V-cycle precision arithmetic. */
+int ddamg_restrict(ddamg_handle* h, const double* fine_in, double* coarse_out, int n_rhs);
+int ddamg_prolong(ddamg_handle* h, const double* coarse_in, double* fine_out, int n_rhs);
+
+/* out = D_c in for coarse vectors (Sec. 3.2), V-cycle precision arithmetic. */
+int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs);
+
+/* Copy the assembled coarse stencil (FP64 as assembled) into out:
+ * [coarse site][direction d][row][col] complex with d = 0 self, 1 + 2 mu (+mu),
+ * 2 + 2 mu (-mu), rows/cols in the coarse-vector component order. */
+int ddamg_get_coarse_stencil(const ddamg_handle* h, double* out);
+
+/* out ~ D_c^{-1} in by the odd-even GMRES of Sec. 6 (V-cycle precision).
+ * fixed_iters > 0 runs exactly that many GMRES steps instead of the tolerance. */
+int ddamg_coarse_solve(ddamg_handle* h, const double* in, double* out, int n_rhs, int fixed_iters);
+
+/* out = C^(nu) in, one V-cycle (Sec. 4.2).  coarse_fixed_iters > 0 fixes the
+ * number of coarse GMRES steps (for reproducible comparisons). */
+int ddamg_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, int coarse_fixed_iters);
+
+/* Change the mass: D(m0') = D(m0) + (m0' - m0) I, so the site terms, D_c's
+ * diagonal blocks (P^H P = I) and the coarse even-site inverses are updated
+ * while P is kept (mass re-use, Sec. 6.3). */
+int ddamg_set_mass(ddamg_handle* h, double m0);
+
+/* Issue all further work of the handle on this cudaStream_t (NULL = the
+ * handle's own stream). */
+int ddamg_set_stream(ddamg_handle* h, void* cuda_stream);
+
+/* Geometry of the handle: V, number of coarse sites, 2N. */
+int ddamg_info(const ddamg_handle* h, long long* n_sites, long long* n_coarse_sites, int* coarse_dof);
+
+/* Per-kernel timing with CUDA events on the handle's stream (benchmarks).
+ * ddamg_profile_enable(h, 1) starts recording, 0 stops;  ddamg_profile_read
+ * fills up to max entries (name, launches, total milliseconds, algorithmic
+ * bytes) and returns the number of kernel families recorded. */
+typedef struct {
+    char name[48];
+    long long launches;
+    double total_ms;
+    double bytes;
+} ddamg_kernel_profile;
+int ddamg_profile_enable(ddamg_handle* h, int on);
+int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max);
+int ddamg_profile_reset(ddamg_handle* h);
+
+/* Number of kernels this library has launched since load (all handles). */
+long long ddamg_launch_count(void);
+
+/* Test hook: make the next n device allocations of the library fail (OOM). */
+void ddamg_debug_fail_allocs(int n);
+
+/* Release every resource of the handle. */
+int ddamg_destroy(ddamg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDAMG_H */

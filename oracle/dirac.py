@@ -135,3 +135,47 @@ def gamma5_field(psi: np.ndarray) -> np.ndarray:
 def inner(a: np.ndarray, b: np.ndarray) -> complex:
     """<a, b> = a^H b."""
     return complex(np.vdot(a.ravel(), b.ravel()))
+
+
+def apply_at_sites(U: np.ndarray, dims, m0: float, c_sw: float, psi: np.ndarray, sites: np.ndarray) -> np.ndarray:
+    """(D psi)(x) for the listed sites only, by the same formulas as DiracOperator,
+    gathering the needed links and neighbours instead of shifting whole fields
+    (lets the full-size workloads be checked site by site)."""
+    dims = tuple(int(d) for d in dims)
+    sites = np.asarray(sites, dtype=np.int64)
+    base = np.stack(np.unravel_index(sites, dims), axis=1)
+
+    def idx(offsets):
+        c = base.copy()
+        for d, s in offsets:
+            c[:, d] = (c[:, d] + s) % dims[d]
+        return np.ravel_multi_index(c.T, dims)
+
+    def Ug(m, offsets):
+        return U[idx(offsets), m]
+
+    def prod4(a, b, c, d):
+        return a @ b @ c @ d
+
+    n = len(sites)
+    A = np.broadcast_to((m0 + 4.0) * I12, (n, 12, 12)).copy()
+
+    def Q(mu, nu):
+        l1 = prod4(Ug(mu, []), Ug(nu, [(mu, 1)]), dag(Ug(mu, [(nu, 1)])), dag(Ug(nu, [])))
+        l2 = prod4(Ug(nu, []), dag(Ug(mu, [(mu, -1), (nu, 1)])), dag(Ug(nu, [(mu, -1)])), Ug(mu, [(mu, -1)]))
+        l3 = prod4(dag(Ug(mu, [(mu, -1)])), dag(Ug(nu, [(mu, -1), (nu, -1)])), Ug(mu, [(mu, -1), (nu, -1)]), Ug(nu, [(nu, -1)]))
+        l4 = prod4(dag(Ug(nu, [(nu, -1)])), Ug(mu, [(nu, -1)]), Ug(nu, [(nu, -1), (mu, 1)]), dag(Ug(mu, [])))
+        return l1 + l2 + l3 + l4
+
+    for mu in range(4):
+        for nu in range(4):
+            if mu != nu:
+                F = Q(mu, nu) - Q(nu, mu)
+                A -= (c_sw / 32.0) * np.einsum("st,xab->xsatb", GAMMA[mu] @ GAMMA[nu], F).reshape(n, 12, 12)
+    out = np.einsum("xij,xj->xi", A, psi[sites].reshape(n, 12)).reshape(n, 4, 3)
+    for mu in range(4):
+        fwd = psi[idx([(mu, 1)])]
+        out -= 0.5 * np.einsum("st,xab,xtb->xsa", I4 - GAMMA[mu], U[sites, mu], fwd)
+        bi = idx([(mu, -1)])
+        out -= 0.5 * np.einsum("st,xab,xtb->xsa", I4 + GAMMA[mu], dag(U[bi, mu]), psi[bi])
+    return out

@@ -1,0 +1,360 @@
+// Batched vector kernels for the Krylov solvers: multi-dot products with FP64
+// accumulation (deterministic two-stage reduction), linear combinations with
+// per-right-hand-side complex coefficients, precision conversion and the
+// permutations between the ABI's lexicographic layout and the internal order.
+#include "kernels.h"
+#include "blas.h"
+
+namespace ddamg {
+
+// Basis addressing: vector i of rhs r starts at base + i * istride + r * rstride.
+constexpr int kDotThreads = 256;
+constexpr int kDotMaxK = 32;
+
+// stage 1: partial[cta][i][r] for i < k over a slice of n
+template <typename Ta, typename Tb, int KB>
+__global__ void __launch_bounds__(kDotThreads) multidot_kernel(const cplx<Ta>* __restrict__ A, size_t istride, size_t arstride, int k,
+                                                               const cplx<Tb>* __restrict__ w, size_t wrstride, size_t n, int nrhs,
+                                                               int ctas_per_rhs, double* __restrict__ partial) {
+    const int r = blockIdx.x % nrhs;
+    const int part = blockIdx.x / nrhs;
+    const cplx<Ta>* Ar = A + r * arstride;
+    const cplx<Tb>* wr = w + r * wrstride;
+    double acc[2 * KB];
+#pragma unroll
+    for (int q = 0; q < 2 * KB; ++q) acc[q] = 0.0;
+    const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
+    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n; e += stride) {
+        cplx<double> wv = ccast<double>(wr[e]);
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+            if (i < k) {
+                cplx<double> a = ccast<double>(Ar[i * istride + e]);
+                acc[2 * i] = fma(a.re, wv.re, fma(a.im, wv.im, acc[2 * i]));
+                acc[2 * i + 1] = fma(a.re, wv.im, fma(-a.im, wv.re, acc[2 * i + 1]));
+            }
+        }
+    }
+    __shared__ double red[kDotThreads / 32][2 * KB];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 2 * KB; ++q) {
+        if (q < 2 * k) {
+            double v = warp_sum(acc[q]);
+            if (lane == 0) red[wi][q] = v;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) {
+        double s = 0;
+        for (int ww = 0; ww < kDotThreads / 32; ++ww) s += red[ww][q];
+        partial[((size_t)blockIdx.x) * 2 * k + q] = s;
+    }
+}
+
+// stage 2: out[i * ostride_i + r] = sum over the ctas of rhs r
+__global__ void multidot_finish(const double* __restrict__ partial, int k, int nrhs, int ctas_per_rhs,
+                                cplx<double>* __restrict__ out, int ostride_i) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;  // q = r * k + i
+    if (q >= nrhs * k) return;
+    int r = q / k, i = q % k;
+    double re = 0, im = 0;
+    for (int p = 0; p < ctas_per_rhs; ++p) {
+        const double* src = partial + ((size_t)(p * nrhs + r)) * 2 * k;
+        re += src[2 * i];
+        im += src[2 * i + 1];
+    }
+    out[(size_t)i * ostride_i + r] = mk(re, im);
+}
+
+template <typename Ta, typename Tb>
+int multidot(const cplx<Ta>* A, size_t istride, size_t arstride, int k, const cplx<Tb>* w, size_t wrstride, size_t n, int nrhs,
+             cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st) {
+    int off = 0;
+    while (off < k) {
+        int kk = k - off;
+        if (kk > kDotMaxK) kk = kDotMaxK;
+        int ctas = (int)((n + kDotThreads - 1) / kDotThreads);
+        int target = 1216 / nrhs;  // about 8 CTAs per SM over all rhs
+        if (target < 1) target = 1;
+        if (ctas > target) ctas = target;
+        const cplx<Ta>* Ab = A + off * istride;
+        if (kk <= 1)
+            multidot_kernel<Ta, Tb, 1><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else if (kk <= 4)
+            multidot_kernel<Ta, Tb, 4><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else if (kk <= 8)
+            multidot_kernel<Ta, Tb, 8><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else if (kk <= 16)
+            multidot_kernel<Ta, Tb, 16><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else
+            multidot_kernel<Ta, Tb, 32><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        DD_CHECK_LAUNCH();
+        multidot_finish<<<ceil_div((long long)nrhs * kk, 128), 128, 0, st>>>(scratch, kk, nrhs, ctas, out + (size_t)off * ostride_i,
+                                                                          ostride_i);
+        DD_CHECK_LAUNCH();
+        off += kk;
+    }
+    return 0;
+}
+
+// out[r] = beta * out[r] + sum_{i<k} coef[i * cstride_i + r] * A_i[r]   (coef FP64 complex, on the device)
+template <typename To, typename Ta>
+__global__ void lincomb_kernel(cplx<To>* __restrict__ out, size_t ors, double beta, const cplx<Ta>* __restrict__ A, size_t istride,
+                               size_t ars, int k, const cplx<double>* __restrict__ coef, int cstride_i, size_t n, int nrhs,
+                               const int* __restrict__ mask, double alpha) {
+    const size_t tot = n * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(q / n);
+        size_t e = q % n;
+        if (mask && !mask[r]) continue;
+        cplx<double> acc = beta == 0.0 ? czero<double>() : beta * ccast<double>(out[r * ors + e]);
+        for (int i = 0; i < k; ++i) cmac(acc, alpha * coef[(size_t)i * cstride_i + r], ccast<double>(A[i * istride + r * ars + e]));
+        out[r * ors + e] = ccast<To>(acc);
+    }
+}
+
+template <typename To, typename Ta>
+int lincomb(cplx<To>* out, size_t ors, double beta, const cplx<Ta>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
+            int cstride_i, size_t n, int nrhs, const int* mask, cudaStream_t st, double alpha) {
+    long long tot = (long long)n * nrhs;
+    int blocks = ceil_div(tot, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    lincomb_kernel<To, Ta><<<blocks, 256, 0, st>>>(out, ors, beta, A, istride, ars, k, coef, cstride_i, n, nrhs, mask, alpha);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+template <typename To, typename Ti>
+__global__ void convert_kernel(const Ti* __restrict__ in, To* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) out[q] = To(in[q]);
+}
+
+template <typename To, typename Ti>
+int convert(const Ti* in, To* out, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    convert_kernel<To, Ti><<<blocks, 256, 0, st>>>(in, out, n);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// ABI lexicographic field [nrhs][V][ncomp] <-> internal [nrhs][ncomp][V];  lex_of[i] = lexicographic site of internal i
+template <typename To, typename Ti>
+__global__ void to_internal_kernel(const cplx<Ti>* __restrict__ in, cplx<To>* __restrict__ out, const int* __restrict__ lex_of, int V,
+                                   int ncomp, int nrhs) {
+    const size_t tot = (size_t)V * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(q / V), i = (int)(q % V);
+        const cplx<Ti>* src = in + ((size_t)r * V + lex_of[i]) * ncomp;
+        cplx<To>* dst = out + (size_t)r * ncomp * V + i;
+        for (int k = 0; k < ncomp; ++k) dst[(size_t)k * V] = ccast<To>(src[k]);
+    }
+}
+
+template <typename To, typename Ti>
+__global__ void from_internal_kernel(const cplx<Ti>* __restrict__ in, cplx<To>* __restrict__ out, const int* __restrict__ lex_of,
+                                     int V, int ncomp, int nrhs) {
+    const size_t tot = (size_t)V * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(q / V), i = (int)(q % V);
+        const cplx<Ti>* src = in + (size_t)r * ncomp * V + i;
+        cplx<To>* dst = out + ((size_t)r * V + lex_of[i]) * ncomp;
+        for (int k = 0; k < ncomp; ++k) dst[k] = ccast<To>(src[(size_t)k * V]);
+    }
+}
+
+template <typename To, typename Ti>
+int to_internal(const cplx<Ti>* in, cplx<To>* out, const int* lex_of, int V, int ncomp, int nrhs, cudaStream_t st) {
+    int blocks = ceil_div((long long)V * nrhs, 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    to_internal_kernel<To, Ti><<<blocks, 256, 0, st>>>(in, out, lex_of, V, ncomp, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+template <typename To, typename Ti>
+int from_internal(const cplx<Ti>* in, cplx<To>* out, const int* lex_of, int V, int ncomp, int nrhs, cudaStream_t st) {
+    int blocks = ceil_div((long long)V * nrhs, 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    from_internal_kernel<To, Ti><<<blocks, 256, 0, st>>>(in, out, lex_of, V, ncomp, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// coarse vectors: ABI [nrhs][NB lex][nc] <-> internal [nrhs][NB internal][nc]
+template <typename To, typename Ti>
+__global__ void coarse_perm_kernel(const cplx<Ti>* __restrict__ in, cplx<To>* __restrict__ out, const int* __restrict__ clex_of,
+                                   int NB, int nc, int nrhs, int to_int) {
+    const size_t tot = (size_t)NB * nc * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(q % nc);
+        size_t t = q / nc;
+        int c = (int)(t % NB), r = (int)(t / NB);
+        size_t a = ((size_t)r * NB + c) * nc + k;
+        size_t b = ((size_t)r * NB + clex_of[c]) * nc + k;
+        if (to_int) out[a] = ccast<To>(in[b]);
+        else out[b] = ccast<To>(in[a]);
+    }
+}
+template <typename To, typename Ti>
+int coarse_perm(const cplx<Ti>* in, cplx<To>* out, const int* clex_of, int NB, int nc, int nrhs, int to_int, cudaStream_t st) {
+    int blocks = ceil_div((long long)NB * nc * nrhs, 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    coarse_perm_kernel<To, Ti><<<blocks, 256, 0, st>>>(in, out, clex_of, NB, nc, nrhs, to_int);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// gauge field: ABI [V lex][4][3][3] FP64 -> internal [4][9][V] FP64
+__global__ void gauge_to_internal_kernel(const cplx<double>* __restrict__ in, cplx<double>* __restrict__ out,
+                                         const int* __restrict__ lex_of, int V) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)V; i += (size_t)gridDim.x * blockDim.x) {
+        const cplx<double>* src = in + (size_t)lex_of[i] * 36;
+        for (int q = 0; q < 36; ++q) out[(size_t)q * V + i] = src[q];
+    }
+}
+int gauge_to_internal(const cplx<double>* in, cplx<double>* out, const int* lex_of, int V, cudaStream_t st) {
+    int blocks = ceil_div(V, 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    gauge_to_internal_kernel<<<blocks, 256, 0, st>>>(in, out, lex_of, V);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// Hessenberg bookkeeping of batched (F)GMRES: one thread per right-hand side.
+// Column k of H arrives in hcol[i * nrhs + r] (i <= k) with hnorm = ||w|| in hcol[(k+1) * nrhs + r].
+__global__ void arnoldi_update_kernel(KrylovState s, int k, const cplx<double>* __restrict__ hcol, cplx<double>* __restrict__ scale) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s.nrhs) return;
+    const int m = s.m;
+    cplx<double>* H = s.H + (size_t)r * (m + 1) * m;  // H[i * m + k]
+    if (!s.active[r]) {
+        scale[r] = mk(0.0, 0.0);
+        return;
+    }
+    for (int i = 0; i <= k; ++i) H[i * m + k] = hcol[(size_t)i * s.nrhs + r];
+    double hk = sqrt(hcol[(size_t)(k + 1) * s.nrhs + r].re);
+    // apply the previous rotations
+    for (int i = 0; i < k; ++i) {
+        double c = s.cs[r * m + i];
+        cplx<double> sn = s.sn[r * m + i];
+        cplx<double> a = H[i * m + k], b = H[(i + 1) * m + k];
+        H[i * m + k] = c * a + sn * b;
+        H[(i + 1) * m + k] = c * b - conj(sn) * a;
+    }
+    cplx<double> a = H[k * m + k];
+    double na = sqrt(norm2(a));
+    double den = sqrt(na * na + hk * hk);
+    double c;
+    cplx<double> sn;
+    if (den == 0.0) {
+        c = 1.0;
+        sn = mk(0.0, 0.0);
+    } else if (na == 0.0) {
+        c = 0.0;
+        sn = mk(1.0, 0.0);
+    } else {
+        c = na / den;
+        sn = (hk / (na * den)) * a;  // (a/|a|) conj(hk)/den, hk real
+    }
+    s.cs[r * m + k] = c;
+    s.sn[r * m + k] = sn;
+    H[k * m + k] = c * a + hk * sn;
+    cplx<double> gk = s.g[r * (m + 1) + k];
+    s.g[r * (m + 1) + k + 1] = -1.0 * (conj(sn) * gk);
+    s.g[r * (m + 1) + k] = c * gk;
+    double est = sqrt(norm2(s.g[r * (m + 1) + k + 1]));
+    s.steps[r] = k + 1;
+    s.resid[r] = est;
+    bool nonfinite = !(est == est) || !(hk == hk);
+    if (nonfinite) s.flags[r] |= 2;
+    if (est <= s.target[r] || nonfinite) s.active[r] = 0;
+    scale[r] = (hk > 0.0 && s.active[r]) ? mk(1.0 / hk, 0.0) : mk(0.0, 0.0);
+}
+
+// y = H^{-1} g (upper triangular, steps[r] columns); y stored as coef[i * nrhs + r]
+__global__ void arnoldi_solve_kernel(KrylovState s, cplx<double>* __restrict__ y) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s.nrhs) return;
+    const int m = s.m;
+    const cplx<double>* H = s.H + (size_t)r * (m + 1) * m;
+    int n = s.steps[r];
+    for (int i = m - 1; i >= n; --i) y[(size_t)i * s.nrhs + r] = mk(0.0, 0.0);
+    for (int i = n - 1; i >= 0; --i) {
+        cplx<double> t = s.g[r * (m + 1) + i];
+        for (int j = i + 1; j < n; ++j) t = t - H[i * m + j] * y[(size_t)j * s.nrhs + r];
+        cplx<double> d = H[i * m + i];
+        double dn = norm2(d);
+        y[(size_t)i * s.nrhs + r] = dn > 0 ? t * mk(d.re / dn, -d.im / dn) : mk(0.0, 0.0);
+    }
+}
+
+// start of a cycle: beta = sqrt(nrm2[r]); g = (beta, 0...); active = beta > target; scale = 1/beta
+__global__ void arnoldi_start_kernel(KrylovState s, const cplx<double>* __restrict__ nrm2, cplx<double>* __restrict__ scale,
+                                     int force_all) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s.nrhs) return;
+    const int m = s.m;
+    double beta = sqrt(nrm2[r].re);
+    for (int i = 0; i <= m; ++i) s.g[r * (m + 1) + i] = mk(0.0, 0.0);
+    s.g[r * (m + 1)] = mk(beta, 0.0);
+    s.steps[r] = 0;
+    s.resid[r] = beta;
+    bool nonfinite = !(beta == beta) || beta > 1e300;
+    if (nonfinite) s.flags[r] |= 2;
+    s.active[r] = (s.enabled[r] && !nonfinite && (force_all || beta > s.target[r])) ? 1 : 0;
+    scale[r] = (s.active[r] && beta > 0) ? mk(1.0 / beta, 0.0) : mk(0.0, 0.0);
+}
+
+int arnoldi_start(const KrylovState& s, const cplx<double>* nrm2, cplx<double>* scale, int force_all, cudaStream_t st) {
+    arnoldi_start_kernel<<<ceil_div(s.nrhs, 64), 64, 0, st>>>(s, nrm2, scale, force_all);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+int arnoldi_update(const KrylovState& s, int k, const cplx<double>* hcol, cplx<double>* scale, cudaStream_t st) {
+    arnoldi_update_kernel<<<ceil_div(s.nrhs, 64), 64, 0, st>>>(s, k, hcol, scale);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+int arnoldi_solve(const KrylovState& s, cplx<double>* y, cudaStream_t st) {
+    arnoldi_solve_kernel<<<ceil_div(s.nrhs, 64), 64, 0, st>>>(s, y);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+__global__ void add_columns_kernel(cplx<double>* __restrict__ a, const cplx<double>* __restrict__ b, int n) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) a[q] = a[q] + b[q];
+}
+int add_columns(cplx<double>* a, const cplx<double>* b, int n, cudaStream_t st) {
+    add_columns_kernel<<<ceil_div(n, 128), 128, 0, st>>>(a, b, n);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// explicit instantiations
+#define DD_INST_DOT(Ta, Tb)                                                                                                   \
+    template int multidot<Ta, Tb>(const cplx<Ta>*, size_t, size_t, int, const cplx<Tb>*, size_t, size_t, int, cplx<double>*, \
+                                  int, double*, cudaStream_t);
+DD_INST_DOT(double, double)
+DD_INST_DOT(float, float)
+#define DD_INST_LC(To, Ta)                                                                                                  \
+    template int lincomb<To, Ta>(cplx<To>*, size_t, double, const cplx<Ta>*, size_t, size_t, int, const cplx<double>*, int, \
+                                 size_t, int, const int*, cudaStream_t, double);
+DD_INST_LC(double, double)
+DD_INST_LC(double, float)
+DD_INST_LC(float, float)
+DD_INST_LC(float, double)
+template int convert<float, double>(const double*, float*, size_t, cudaStream_t);
+template int convert<double, float>(const float*, double*, size_t, cudaStream_t);
+template int to_internal<double, double>(const cplx<double>*, cplx<double>*, const int*, int, int, int, cudaStream_t);
+template int to_internal<float, double>(const cplx<double>*, cplx<float>*, const int*, int, int, int, cudaStream_t);
+template int to_internal<float, float>(const cplx<float>*, cplx<float>*, const int*, int, int, int, cudaStream_t);
+template int from_internal<double, double>(const cplx<double>*, cplx<double>*, const int*, int, int, int, cudaStream_t);
+template int from_internal<double, float>(const cplx<float>*, cplx<double>*, const int*, int, int, int, cudaStream_t);
+template int from_internal<float, float>(const cplx<float>*, cplx<float>*, const int*, int, int, int, cudaStream_t);
+template int coarse_perm<double, double>(const cplx<double>*, cplx<double>*, const int*, int, int, int, int, cudaStream_t);
+template int coarse_perm<float, double>(const cplx<double>*, cplx<float>*, const int*, int, int, int, int, cudaStream_t);
+template int coarse_perm<double, float>(const cplx<float>*, cplx<double>*, const int*, int, int, int, int, cudaStream_t);
+
+}  // namespace ddamg

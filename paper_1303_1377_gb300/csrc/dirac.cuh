@@ -1,0 +1,112 @@
+// Device helpers of the Wilson-clover operator (Sec. 2.2) shared by the fine
+// kernels and the coarse-stencil assembly.
+#pragma once
+#include "common.cuh"
+
+namespace ddamg {
+
+// ---------------------------------------------------------------------------
+// spin structure of the hops.  In the chiral basis gamma_mu = [[0, B],[B^H, 0]]
+// with a monomial 2x2 block B_mu (one entry per row, a power of i), so
+//   (I -+ gamma_mu) psi = [h ; -+ B^H h],  h = psi_up -+ B psi_low.
+// SpinB<MU>::c0,p0 : row 0 of B reads column c0 with factor i^p0; likewise row 1,
+// and the same for B^H (h-prefixed).
+// ---------------------------------------------------------------------------
+template <int MU> struct SpinB;
+template <> struct SpinB<0> { enum { c0 = 1, p0 = 1, c1 = 0, p1 = 1, hc0 = 1, hp0 = 3, hc1 = 0, hp1 = 3 }; };
+template <> struct SpinB<1> { enum { c0 = 1, p0 = 2, c1 = 0, p1 = 0, hc0 = 1, hp0 = 0, hc1 = 0, hp1 = 2 }; };
+template <> struct SpinB<2> { enum { c0 = 0, p0 = 1, c1 = 1, p1 = 3, hc0 = 0, hp0 = 3, hc1 = 1, hp1 = 1 }; };
+template <> struct SpinB<3> { enum { c0 = 0, p0 = 0, c1 = 1, p1 = 0, hc0 = 0, hp0 = 0, hc1 = 1, hp1 = 0 }; };
+
+template <typename T>
+struct Spinor {
+    cplx<T> v[12];
+};
+
+template <typename T, typename Ts>
+__device__ __forceinline__ void load_spinor(Spinor<T>& s, const cplx<Ts>* __restrict__ f, int V, int i) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s.v[k] = ccast<T>(f[(size_t)k * V + i]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_link(cplx<T> (&W)[9], const cplx<T>* __restrict__ U, int V, int mu, int i) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) W[q] = ldg_c(U + (size_t)(mu * 9 + q) * V + i);
+}
+
+// acc += hop of psi_n (the neighbour spinor) through link W in direction MU,
+// FWD: (I - gamma_mu) (x) W with W = U_mu(x);  !FWD: (I + gamma_mu) (x) W^H with W = U_mu(x - mu).
+// acc collects  [g ; -s B^H g],  g = W h (or W^H h), s = +1 forward / -1 backward.
+template <int MU, bool FWD, typename T>
+__device__ __forceinline__ void hop_acc(Spinor<T>& acc, const Spinor<T>& pn, const cplx<T> (&W)[9]) {
+    using B = SpinB<MU>;
+    cplx<T> h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cplx<T> b0 = ipow<B::p0>(pn.v[(2 + B::c0) * 3 + c]);
+        cplx<T> b1 = ipow<B::p1>(pn.v[(2 + B::c1) * 3 + c]);
+        if (FWD) {
+            h[0][c] = pn.v[0 * 3 + c] - b0;
+            h[1][c] = pn.v[1 * 3 + c] - b1;
+        } else {
+            h[0][c] = pn.v[0 * 3 + c] + b0;
+            h[1][c] = pn.v[1 * 3 + c] + b1;
+        }
+    }
+    cplx<T> g[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cplx<T> t = czero<T>();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (FWD) cmac(t, W[a * 3 + b], h[s][b]);
+                else cmac_conj(t, W[b * 3 + a], h[s][b]);
+            }
+            g[s][a] = t;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc.v[0 * 3 + c] = acc.v[0 * 3 + c] + g[0][c];
+        acc.v[1 * 3 + c] = acc.v[1 * 3 + c] + g[1][c];
+        cplx<T> l0 = ipow<B::hp0>(g[B::hc0][c]);
+        cplx<T> l1 = ipow<B::hp1>(g[B::hc1][c]);
+        if (FWD) {  // -s = -1
+            acc.v[2 * 3 + c] = acc.v[2 * 3 + c] - l0;
+            acc.v[3 * 3 + c] = acc.v[3 * 3 + c] - l1;
+        } else {
+            acc.v[2 * 3 + c] = acc.v[2 * 3 + c] + l0;
+            acc.v[3 * 3 + c] = acc.v[3 * 3 + c] + l1;
+        }
+    }
+}
+
+// y = A x for a site term stored as two packed hermitian 6x6 blocks
+template <typename T>
+__device__ __forceinline__ void herm_apply(const T* __restrict__ cl, int V, int i, const Spinor<T>& x, Spinor<T>& y) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const T* base = cl + (size_t)(h * 36) * V + i;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            T d = __ldg(base + (size_t)a * V);
+            y.v[h * 6 + a] = d * x.v[h * 6 + a];
+        }
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < 6; ++b) {
+                cplx<T> m = mk(__ldg(base + (size_t)(6 + 2 * q) * V), __ldg(base + (size_t)(7 + 2 * q) * V));
+                cmac(y.v[h * 6 + a], m, x.v[h * 6 + b]);
+                cmac_conj(y.v[h * 6 + b], m, x.v[h * 6 + a]);
+                ++q;
+            }
+        }
+    }
+}
+
+}  // namespace ddamg

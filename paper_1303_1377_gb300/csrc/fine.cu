@@ -1,0 +1,436 @@
+// Fine-grid kernels: clover-improved Wilson Dslash (Sec. 2.2), clover term and
+// its even-site inverses, and the fused red-black SAP block solver (Sec. 2.3,
+// local odd-even MR of Sec. 6).
+//
+// Field layouts (internal site order, see common.cuh):
+//   spinor  cplx<T>[nrhs][12][V]  component k = spin*3 + colour (SoA: coalesced per component)
+//   links   cplx<T>[4][9][V]      U_mu(x)[a][b] at ((mu*9 + a*3 + b) * V + x)
+//   clover  T[72][V]              two hermitian 6x6 chiral blocks (spins {0,1}, {2,3}),
+//                                 each 6 real diagonal entries + 15 complex upper entries
+#include "kernels.h"
+#include "dirac.cuh"
+
+namespace ddamg {
+
+// gamma_mu gamma_nu for the six planes mu < nu in the chiral basis of Sec. 2.2,
+// restricted to its two 2x2 chiral blocks: [plane][half][s][t] (re, im)
+__constant__ double c_gg[6][2][2][2][2];
+
+template <int MU, typename T, typename Ts>
+__device__ __forceinline__ void hop_pair(const Geom& g, const cplx<T>* __restrict__ U, const cplx<Ts>* __restrict__ in, int i,
+                                         Spinor<T>& acc) {
+    cplx<T> W[9];
+    Spinor<T> pn;
+    int f = fine_nbr(g, i, 2 * MU);
+    load_link(W, U, g.V, MU, i);
+    load_spinor(pn, in, g.V, f);
+    hop_acc<MU, true>(acc, pn, W);
+    int bk = fine_nbr(g, i, 2 * MU + 1);
+    load_link(W, U, g.V, MU, bk);
+    load_spinor(pn, in, g.V, bk);
+    hop_acc<MU, false>(acc, pn, W);
+}
+
+// out = D in  (RESID: out = b - D in).  in may be of a different precision Ts.
+template <typename T, typename Ts, bool RESID>
+__global__ void __launch_bounds__(128) dslash_kernel(Geom g, FineOp<T> op, const cplx<Ts>* __restrict__ in,
+                                                     const cplx<T>* __restrict__ b, cplx<T>* __restrict__ out, int nrhs) {
+    int r = blockIdx.x % nrhs;
+    int i = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const size_t off = (size_t)r * 12 * g.V;
+    const cplx<Ts>* inr = in + off;
+    Spinor<T> acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    hop_pair<0>(g, op.U, inr, i, acc);
+    hop_pair<1>(g, op.U, inr, i, acc);
+    hop_pair<2>(g, op.U, inr, i, acc);
+    hop_pair<3>(g, op.U, inr, i, acc);
+    Spinor<T> x, y;
+    load_spinor(x, inr, g.V, i);
+    herm_apply(op.clov, g.V, i, x, y);
+    cplx<T>* o = out + off;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        cplx<T> d = y.v[k] - T(0.5) * acc.v[k];
+        if (RESID) d = b[off + (size_t)k * g.V + i] - d;
+        o[(size_t)k * g.V + i] = d;
+    }
+}
+
+template <typename T, typename Ts>
+int launch_dslash(const Geom& g, const FineOp<T>& op, const cplx<Ts>* in, const cplx<T>* b, cplx<T>* out, int nrhs,
+                  cudaStream_t st) {
+    const int nt = 128;
+    long long nblk = (long long)ceil_div(g.V, nt) * nrhs;
+    if (b)
+        dslash_kernel<T, Ts, true><<<(unsigned)nblk, nt, 0, st>>>(g, op, in, b, out, nrhs);
+    else
+        dslash_kernel<T, Ts, false><<<(unsigned)nblk, nt, 0, st>>>(g, op, in, b, out, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+template int launch_dslash<double, double>(const Geom&, const FineOp<double>&, const cplx<double>*, const cplx<double>*,
+                                           cplx<double>*, int, cudaStream_t);
+template int launch_dslash<double, float>(const Geom&, const FineOp<double>&, const cplx<float>*, const cplx<double>*,
+                                          cplx<double>*, int, cudaStream_t);
+template int launch_dslash<float, float>(const Geom&, const FineOp<float>&, const cplx<float>*, const cplx<float>*,
+                                         cplx<float>*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Red-black SAP: one launch per colour.  A CTA owns one block of that colour and
+// one right-hand side: it forms r = b - D z on its block (neighbouring blocks are
+// of the other colour and are not written in this launch), solves D_i e = r_i by
+// odd-even MR (mr_steps steps, zero initial guess) and adds e to z.
+// Thread t < Vb/2 owns the even site t and the odd site Vb/2 + t of the block.
+// ---------------------------------------------------------------------------
+
+// sum over in-block neighbours of the hops of D applied to a block-local field
+// held in shared memory (sm[k * H + local index]), at local site l (global i).
+template <int MU, typename T>
+__device__ __forceinline__ void block_hop_pair(const Geom& g, const cplx<T>* __restrict__ U, const cplx<T>* sm, int H,
+                                               int base_local, int l, int i, int blk, Spinor<T>& acc) {
+    cplx<T> W[9];
+    Spinor<T> pn;
+    int e = __ldg(g.lnbr + (2 * MU) * g.Vb + l);
+    if (!(e >> 16)) {
+        int ln = (e & 0xffff) - base_local;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pn.v[k] = sm[k * H + ln];
+        load_link(W, U, g.V, MU, i);
+        hop_acc<MU, true>(acc, pn, W);
+    }
+    e = __ldg(g.lnbr + (2 * MU + 1) * g.Vb + l);
+    if (!(e >> 16)) {
+        int lnb = e & 0xffff;
+        int ln = lnb - base_local;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pn.v[k] = sm[k * H + ln];
+        load_link(W, U, g.V, MU, blk * g.Vb + lnb);
+        hop_acc<MU, false>(acc, pn, W);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_hops(const Geom& g, const cplx<T>* __restrict__ U, const cplx<T>* sm, int H, int base_local,
+                                           int l, int i, int blk, Spinor<T>& acc) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    block_hop_pair<0>(g, U, sm, H, base_local, l, i, blk, acc);
+    block_hop_pair<1>(g, U, sm, H, base_local, l, i, blk, acc);
+    block_hop_pair<2>(g, U, sm, H, base_local, l, i, blk, acc);
+    block_hop_pair<3>(g, U, sm, H, base_local, l, i, blk, acc);
+}
+
+// full D at one site with z read from global memory (residual)
+template <typename T>
+__device__ __forceinline__ void site_D(const Geom& g, const FineOp<T>& op, const cplx<T>* __restrict__ z, int i, Spinor<T>& out) {
+    Spinor<T> acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    hop_pair<0>(g, op.U, z, i, acc);
+    hop_pair<1>(g, op.U, z, i, acc);
+    hop_pair<2>(g, op.U, z, i, acc);
+    hop_pair<3>(g, op.U, z, i, acc);
+    Spinor<T> x;
+    load_spinor(x, z, g.V, i);
+    herm_apply(op.clov, g.V, i, x, out);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out.v[k] = out.v[k] - T(0.5) * acc.v[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void block_reduce3(T& a, T& b, T& c, T* red) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
+    }
+    __syncthreads();
+    a = b = c = T(0);
+    for (int q = 0; q < nw; ++q) {
+        a += red[3 * q];
+        b += red[3 * q + 1];
+        c += red[3 * q + 2];
+    }
+}
+
+template <typename T>
+__global__ void sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc, cplx<T>* __restrict__ z, int colour,
+                                  int nrhs, int mr_steps) {
+    extern __shared__ unsigned char smem_raw[];
+    const int H = g.Vb / 2;
+    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw);  // [12][H] even-site work vector
+    cplx<T>* SO = SE + 12 * H;                            // [12][H] odd-site work vector (rho, then x_o)
+    cplx<T>* SR = SO + 12 * H;                            // [12][H] r_e
+    T* red = reinterpret_cast<T*>(SR + 12 * H);           // reduction scratch
+
+    const int r = blockIdx.x % nrhs;
+    const int blk = colour * (g.NB / 2) + blockIdx.x / nrhs;
+    const int t = threadIdx.x;
+    const bool act = t < H;
+    const int le = t, lo = H + t;
+    const int ie = blk * g.Vb + le, io = blk * g.Vb + lo;
+    const size_t off = (size_t)r * 12 * g.V;
+    const cplx<T>* b = bsrc + off;
+    cplx<T>* zr = z + off;
+
+    Spinor<T> ro, xo, tmp, tmp2;
+    // 1. residual r = b - D z on both sites; even part: SE <- A_ee^{-1} r_e, SR <- r_e
+    if (act) {
+        site_D(g, op, zr, ie, tmp);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) tmp.v[k] = b[(size_t)k * g.V + ie] - tmp.v[k];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) SR[k * H + t] = tmp.v[k];
+        herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+        site_D(g, op, zr, io, tmp);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ro.v[k] = b[(size_t)k * g.V + io] - tmp.v[k];
+    }
+    __syncthreads();
+    // 2. reduced right-hand side rho = r_o - D_oe A_ee^{-1} r_e ; x_o = 0
+    if (act) {
+        block_hops(g, op.U, SE, H, 0, lo, io, blk, tmp);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ro.v[k] = ro.v[k] - T(-0.5) * tmp.v[k];  // block hops of D carry the -1/2
+            SO[k * H + t] = ro.v[k];
+            xo.v[k] = czero<T>();
+        }
+    }
+    __syncthreads();
+    // 3. MR steps on S = A_oo - D_oe A_ee^{-1} D_eo
+    for (int it = 0; it < mr_steps; ++it) {
+        if (act) {  // even: SE <- A_ee^{-1} D_eo rho
+            block_hops(g, op.U, SO, H, H, le, ie, blk, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) tmp.v[k] = T(-0.5) * tmp.v[k];
+            herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+        }
+        __syncthreads();
+        T num_re = 0, num_im = 0, den = 0;
+        if (act) {  // odd: t = A_oo rho - D_oe SE
+            herm_apply(op.clov, g.V, io, ro, tmp2);
+            block_hops(g, op.U, SE, H, 0, lo, io, blk, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                tmp.v[k] = tmp2.v[k] + T(0.5) * tmp.v[k];
+                num_re += tmp.v[k].re * ro.v[k].re + tmp.v[k].im * ro.v[k].im;
+                num_im += tmp.v[k].re * ro.v[k].im - tmp.v[k].im * ro.v[k].re;
+                den += norm2(tmp.v[k]);
+            }
+        }
+        block_reduce3(num_re, num_im, den, red);
+        cplx<T> alpha = czero<T>();
+        if (den > tiny_normal<T>()) alpha = mk(num_re / den, num_im / den);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cmac(xo.v[k], alpha, ro.v[k]);
+                ro.v[k] = ro.v[k] - alpha * tmp.v[k];
+                SO[k * H + t] = ro.v[k];
+            }
+        }
+        __syncthreads();
+    }
+    // 4. back-substitution x_e = A_ee^{-1} (r_e - D_eo x_o) and update z
+    if (act) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) SO[k * H + t] = xo.v[k];
+    }
+    __syncthreads();
+    if (act) {
+        block_hops(g, op.U, SO, H, H, le, ie, blk, tmp);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) tmp.v[k] = SR[k * H + t] + T(0.5) * tmp.v[k];
+        herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + tmp2.v[k];
+            zr[(size_t)k * g.V + io] = zr[(size_t)k * g.V + io] + xo.v[k];
+        }
+    }
+}
+
+template <typename T>
+int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                      cudaStream_t st) {
+    const int H = g.Vb / 2;
+    const int nt = ((H + 31) / 32) * 32;
+    size_t smem = 3 * 12 * (size_t)H * sizeof(cplx<T>) + 3 * 32 * sizeof(T);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(sap_colour_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    long long nblk = (long long)(g.NB / 2) * nrhs;
+    sap_colour_kernel<T><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+template int launch_sap_colour<double>(const Geom&, const FineOp<double>&, const cplx<double>*, cplx<double>*, int, int, int,
+                                       cudaStream_t);
+template int launch_sap_colour<float>(const Geom&, const FineOp<float>&, const cplx<float>*, cplx<float>*, int, int, int,
+                                      cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Clover term (Sec. 2.2):  A(x) = (m0 + 4) I - c_sw/16 sum_{mu<nu} (gamma_mu gamma_nu) (x) F_mu,nu(x),
+// F = Q_mu,nu - Q_mu,nu^H (Q_nu,mu is the same four leaves traversed backwards, i.e. Q_mu,nu^H),
+// Q_mu,nu = sum of the four plaquette leaves at x.  Computed in FP64, stored
+// packed; the inverse of each 6x6 block by Gauss-Jordan with partial pivoting.
+// ---------------------------------------------------------------------------
+struct M3 {
+    cplx<double> m[9];
+};
+__device__ __forceinline__ M3 ld3(const cplx<double>* __restrict__ U, int V, int mu, int i) {
+    M3 r;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r.m[q] = U[(size_t)(mu * 9 + q) * V + i];
+    return r;
+}
+__device__ __forceinline__ M3 mul3(const M3& a, const M3& b) {
+    M3 r;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            cplx<double> t = czero<double>();
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(t, a.m[x * 3 + k], b.m[k * 3 + y]);
+            r.m[x * 3 + y] = t;
+        }
+    return r;
+}
+__device__ __forceinline__ M3 dag3(const M3& a) {
+    M3 r;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) r.m[x * 3 + y] = conj(a.m[y * 3 + x]);
+    return r;
+}
+
+__global__ void clover_kernel(Geom g, const cplx<double>* __restrict__ U, double m0, double csw, double* __restrict__ clov,
+                              double* __restrict__ clovinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    cplx<double> A[2][6][6];
+    for (int h = 0; h < 2; ++h)
+        for (int p = 0; p < 6; ++p)
+            for (int q = 0; q < 6; ++q) A[h][p][q] = mk(p == q ? m0 + 4.0 : 0.0, 0.0);
+    int plane = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+            const int fm = 2 * mu, bm = 2 * mu + 1, fn = 2 * nu, bn = 2 * nu + 1;
+            int xpm = fine_nbr(g, i, fm), xpn = fine_nbr(g, i, fn);
+            int xmm = fine_nbr(g, i, bm), xmn = fine_nbr(g, i, bn);
+            int xmmpn = fine_nbr(g, xmm, fn);   // x - mu + nu
+            int xmmmn = fine_nbr(g, xmm, bn);   // x - mu - nu
+            int xmnpm = fine_nbr(g, xmn, fm);   // x - nu + mu
+            M3 l1 = mul3(mul3(ld3(U, g.V, mu, i), ld3(U, g.V, nu, xpm)), mul3(dag3(ld3(U, g.V, mu, xpn)), dag3(ld3(U, g.V, nu, i))));
+            M3 l2 = mul3(mul3(ld3(U, g.V, nu, i), dag3(ld3(U, g.V, mu, xmmpn))), mul3(dag3(ld3(U, g.V, nu, xmm)), ld3(U, g.V, mu, xmm)));
+            M3 l3 = mul3(mul3(dag3(ld3(U, g.V, mu, xmm)), dag3(ld3(U, g.V, nu, xmmmn))), mul3(ld3(U, g.V, mu, xmmmn), ld3(U, g.V, nu, xmn)));
+            M3 l4 = mul3(mul3(dag3(ld3(U, g.V, nu, xmn)), ld3(U, g.V, mu, xmn)), mul3(ld3(U, g.V, nu, xmnpm), dag3(ld3(U, g.V, mu, i))));
+            cplx<double> F[9];
+            for (int q = 0; q < 9; ++q) F[q] = l1.m[q] + l2.m[q] + l3.m[q] + l4.m[q];
+            cplx<double> Fd[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b2 = 0; b2 < 3; ++b2) Fd[a * 3 + b2] = F[a * 3 + b2] - conj(F[b2 * 3 + a]);
+            for (int h = 0; h < 2; ++h)
+                for (int s = 0; s < 2; ++s)
+                    for (int t2 = 0; t2 < 2; ++t2) {
+                        cplx<double> gst = mk(c_gg[plane][h][s][t2][0], c_gg[plane][h][s][t2][1]);
+                        if (gst.re == 0.0 && gst.im == 0.0) continue;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b2 = 0; b2 < 3; ++b2) {
+                                cplx<double> v = gst * Fd[a * 3 + b2];
+                                A[h][s * 3 + a][t2 * 3 + b2] = A[h][s * 3 + a][t2 * 3 + b2] - (csw / 16.0) * v;
+                            }
+                    }
+        }
+    }
+    for (int h = 0; h < 2; ++h) {
+        // pack A
+        for (int a = 0; a < 6; ++a) clov[(size_t)(h * 36 + a) * g.V + i] = A[h][a][a].re;
+        int q = 0;
+        for (int a = 0; a < 6; ++a)
+            for (int b2 = a + 1; b2 < 6; ++b2, ++q) {
+                clov[(size_t)(h * 36 + 6 + 2 * q) * g.V + i] = A[h][a][b2].re;
+                clov[(size_t)(h * 36 + 7 + 2 * q) * g.V + i] = A[h][a][b2].im;
+            }
+        // Gauss-Jordan inverse with partial pivoting
+        cplx<double> M[6][6], Inv[6][6];
+        for (int a = 0; a < 6; ++a)
+            for (int b2 = 0; b2 < 6; ++b2) {
+                M[a][b2] = A[h][a][b2];
+                Inv[a][b2] = mk(a == b2 ? 1.0 : 0.0, 0.0);
+            }
+        for (int c = 0; c < 6; ++c) {
+            int piv = c;
+            double best = norm2(M[c][c]);
+            for (int rr = c + 1; rr < 6; ++rr)
+                if (norm2(M[rr][c]) > best) {
+                    best = norm2(M[rr][c]);
+                    piv = rr;
+                }
+            if (piv != c)
+                for (int k = 0; k < 6; ++k) {
+                    cplx<double> t = M[c][k];
+                    M[c][k] = M[piv][k];
+                    M[piv][k] = t;
+                    t = Inv[c][k];
+                    Inv[c][k] = Inv[piv][k];
+                    Inv[piv][k] = t;
+                }
+            double dn = norm2(M[c][c]);
+            cplx<double> invp = mk(M[c][c].re / dn, -M[c][c].im / dn);
+            for (int k = 0; k < 6; ++k) {
+                M[c][k] = M[c][k] * invp;
+                Inv[c][k] = Inv[c][k] * invp;
+            }
+            for (int rr = 0; rr < 6; ++rr) {
+                if (rr == c) continue;
+                cplx<double> f = M[rr][c];
+                for (int k = 0; k < 6; ++k) {
+                    M[rr][k] = M[rr][k] - f * M[c][k];
+                    Inv[rr][k] = Inv[rr][k] - f * Inv[c][k];
+                }
+            }
+        }
+        for (int a = 0; a < 6; ++a) clovinv[(size_t)(h * 36 + a) * g.V + i] = Inv[a][a].re;
+        q = 0;
+        for (int a = 0; a < 6; ++a)
+            for (int b2 = a + 1; b2 < 6; ++b2, ++q) {
+                clovinv[(size_t)(h * 36 + 6 + 2 * q) * g.V + i] = Inv[a][b2].re;
+                clovinv[(size_t)(h * 36 + 7 + 2 * q) * g.V + i] = Inv[a][b2].im;
+            }
+    }
+}
+
+int upload_gamma_products(const double* gg) {
+    DD_CUDA(cudaMemcpyToSymbol(c_gg, gg, sizeof(double) * 6 * 2 * 2 * 2 * 2));
+    return 0;
+}
+
+int launch_clover(const Geom& g, const cplx<double>* U, double m0, double csw, double* clov, double* clovinv, cudaStream_t st) {
+    clover_kernel<<<ceil_div(g.V, 64), 64, 0, st>>>(g, U, m0, csw, clov, clovinv);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+}  // namespace ddamg

@@ -1,0 +1,59 @@
+// Host-side declarations of the kernel launchers of libddamg (all return 0 or a
+// negative ddamg_status).
+#pragma once
+
+#include "common.cuh"
+#include "../../include/ddamg.h"
+
+namespace ddamg {
+
+template <typename T>
+struct FineOp {
+    const cplx<T>* U;   // [4][9][V]
+    const T* clov;      // [72][V] site term A = (m0+4) I + clover
+    const T* clovinv;   // [72][V] A^{-1} (used on even sites)
+};
+
+// coarse stencil in storage type S (float, double or __half2 packed as cplx<half>)
+template <typename S>
+struct CoarseOp {
+    const S* B;     // [NB][9][nc(col)][nc(row)] column-major 2N x 2N blocks, d = 0 self, 1 + dir
+    const S* Dinv;  // [NB/2][nc][nc] column-major inverse of B_0 on even coarse sites
+    const int* cnbr;  // [8][NB] neighbouring coarse site per direction
+    int NB;
+    int nc;
+};
+
+// ---- fine.cu
+template <typename T, typename Ts>
+int launch_dslash(const Geom& g, const FineOp<T>& op, const cplx<Ts>* in, const cplx<T>* b, cplx<T>* out, int nrhs,
+                  cudaStream_t st);
+template <typename T>
+int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                      cudaStream_t st);
+int upload_gamma_products(const double* gg);
+int launch_clover(const Geom& g, const cplx<double>* U, double m0, double csw, double* clov, double* clovinv, cudaStream_t st);
+
+// ---- transfer.cu (P, P^H, Gram-Schmidt, D_c assembly)
+template <typename T, typename Tp>
+int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
+template <typename T, typename Tp>
+int launch_prolong(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
+int launch_gram_schmidt(const Geom& g, cplx<double>* P, int N, int* rank_fail, cudaStream_t st);
+int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, cplx<double>* T,
+                      cudaStream_t st);
+int launch_block_project(const Geom& g, const cplx<double>* P, int N, const cplx<double>* T, const int* sites, int nsites,
+                         double* Bout, size_t site_stride, cudaStream_t st);
+
+// ---- coarse.cu
+template <typename T, typename S>
+int launch_coarse_full(const CoarseOp<S>& op, const cplx<T>* x, cplx<T>* y, int nrhs, cudaStream_t st);
+template <typename T, typename S>
+int launch_coarse_even(const CoarseOp<S>& op, const cplx<T>* b_e, size_t b_rs, const cplx<T>* x_o, size_t x_rs, T beta,
+                       cplx<T>* out_e, size_t o_rs, int nrhs, cudaStream_t st);
+template <typename T, typename S>
+int launch_coarse_odd(const CoarseOp<S>& op, const cplx<T>* x_o, size_t x_rs, const cplx<T>* t_e, size_t t_rs, int use_diag,
+                      cplx<T>* out_o, size_t o_rs, int nrhs, cudaStream_t st);
+int launch_coarse_invert(const double* B, double* Dinv, int NB, int nc, int* fail, cudaStream_t st);
+
+}  // namespace ddamg

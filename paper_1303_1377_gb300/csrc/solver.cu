@@ -1,0 +1,1496 @@
+// Host side of libddamg: the handle, the internal lattice ordering, the
+// adaptive setup (Algorithms 1-2), the V-cycle (Sec. 4.2), batched restarted
+// GMRES for the odd-even coarse system (Sec. 6) and the outer FGMRES (Sec. 5),
+// and every extern "C" entry point declared in include/ddamg.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "blas.h"
+#include "kernels.h"
+
+namespace ddamg {
+
+unsigned long long g_launches = 0;
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+static int g_fail_allocs = 0;
+
+static int dalloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (g_fail_allocs > 0) {
+        --g_fail_allocs;
+        set_error("device allocation failed (forced by ddamg_debug_fail_allocs)");
+        return DDAMG_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return DDAMG_ERR_OOM;
+    }
+    return 0;
+}
+template <typename T>
+static int dalloc_n(T** p, size_t n) {
+    return dalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+template <typename T>
+static void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+#define DD_TRY(x)                  \
+    do {                           \
+        int _rc = (x);             \
+        if (_rc) return _rc;       \
+    } while (0)
+
+// profiling families
+enum { PF_DSLASH64 = 0, PF_DSLASH32, PF_SAP, PF_COARSE, PF_RESTRICT, PF_PROLONG, PF_COUNT };
+static const char* kPfNames[PF_COUNT] = {"dslash_fp64", "dslash_fp32", "sap_block_mr", "coarse_stencil", "restrict", "prolong"};
+
+struct ProfRec {
+    int fam;
+    cudaEvent_t e0, e1;
+    double bytes;
+};
+
+// a growable set of device buffers kept by the handle
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t b) {
+        if (b <= bytes) return 0;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        DD_TRY(dalloc(&p, b));
+        bytes = b;
+        return 0;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T* as() const {
+        return reinterpret_cast<T*>(p);
+    }
+};
+
+// Krylov state + small buffers for nrhs right-hand sides, restart length m
+struct KrylovBufs {
+    int nrhs = 0, m = 0;
+    KrylovState s{};
+    cplx<double>* hcol = nullptr;   // [(m+2)][nrhs]
+    cplx<double>* hcol2 = nullptr;  // second Gram-Schmidt pass
+    cplx<double>* scale = nullptr;  // [nrhs]
+    cplx<double>* y = nullptr;      // [m][nrhs]
+    cplx<double>* nrm = nullptr;    // [nrhs]
+    cplx<double>* ones = nullptr;   // [1] = 1
+    double* dscr = nullptr;         // multidot scratch
+    int* h_active = nullptr;        // pinned copy of active flags
+    int* h_steps = nullptr;
+    double* h_resid = nullptr;
+    int* h_flags = nullptr;
+    int alloc(int nr, int mm) {
+        if (nr <= nrhs && mm == m) return 0;
+        release();
+        nrhs = nr;
+        m = mm;
+        s.nrhs = nr;
+        s.m = mm;
+        DD_TRY(dalloc_n(&s.H, (size_t)nr * (mm + 1) * mm));
+        DD_TRY(dalloc_n(&s.cs, (size_t)nr * mm));
+        DD_TRY(dalloc_n(&s.sn, (size_t)nr * mm));
+        DD_TRY(dalloc_n(&s.g, (size_t)nr * (mm + 1)));
+        DD_TRY(dalloc_n(&s.steps, nr));
+        DD_TRY(dalloc_n(&s.resid, nr));
+        DD_TRY(dalloc_n(&s.active, nr));
+        DD_TRY(dalloc_n(&s.enabled, nr));
+        DD_TRY(dalloc_n(&s.flags, nr));
+        DD_TRY(dalloc_n(&s.target, nr));
+        DD_TRY(dalloc_n(&hcol, (size_t)(mm + 2) * nr));
+        DD_TRY(dalloc_n(&hcol2, (size_t)(mm + 2) * nr));
+        DD_TRY(dalloc_n(&scale, nr));
+        DD_TRY(dalloc_n(&y, (size_t)mm * nr));
+        DD_TRY(dalloc_n(&nrm, nr));
+        DD_TRY(dalloc_n(&ones, nr));
+        {
+            std::vector<cplx<double>> one(nr, mk(1.0, 0.0));
+            DD_CUDA(cudaMemcpy(ones, one.data(), sizeof(cplx<double>) * nr, cudaMemcpyHostToDevice));
+        }
+        DD_TRY(dalloc_n(&dscr, multidot_scratch_doubles(1) + multidot_scratch_doubles(nr)));
+        DD_CUDA(cudaMallocHost(&h_active, sizeof(int) * nr));
+        DD_CUDA(cudaMallocHost(&h_steps, sizeof(int) * nr));
+        DD_CUDA(cudaMallocHost(&h_resid, sizeof(double) * nr));
+        DD_CUDA(cudaMallocHost(&h_flags, sizeof(int) * nr));
+        return 0;
+    }
+    void release() {
+        dfree(s.H);
+        dfree(s.cs);
+        dfree(s.sn);
+        dfree(s.g);
+        dfree(s.steps);
+        dfree(s.resid);
+        dfree(s.active);
+        dfree(s.enabled);
+        dfree(s.flags);
+        dfree(s.target);
+        dfree(hcol);
+        dfree(hcol2);
+        dfree(scale);
+        dfree(y);
+        dfree(nrm);
+        dfree(ones);
+        dfree(dscr);
+        if (h_active) cudaFreeHost(h_active);
+        if (h_steps) cudaFreeHost(h_steps);
+        if (h_resid) cudaFreeHost(h_resid);
+        if (h_flags) cudaFreeHost(h_flags);
+        h_active = h_steps = h_flags = nullptr;
+        h_resid = nullptr;
+        nrhs = m = 0;
+    }
+};
+
+}  // namespace ddamg
+
+using namespace ddamg;
+
+struct ddamg_handle {
+    // geometry
+    int L[4], b[4], nbk[4];
+    int V, Vb, NB, N, nc;
+    ddamg_params p;
+    double m0, csw;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    std::vector<int> h_lex_of, h_clex_of;
+    int *d_lnbr = nullptr, *d_bnbr = nullptr, *d_lex_of = nullptr, *d_clex_of = nullptr, *d_sites = nullptr;
+    int nsites[9];
+    Geom g;
+    // operator (FP64 always, FP32 copy for the single/half modes)
+    cplx<double>* U64 = nullptr;
+    double *clov64 = nullptr, *clovinv64 = nullptr;
+    cplx<float>* U32 = nullptr;
+    float *clov32 = nullptr, *clovinv32 = nullptr;
+    // interpolation
+    bool ready = false;
+    cplx<double>* V64 = nullptr;  // test vectors [N][12][V]
+    cplx<double>* P64 = nullptr;
+    cplx<float>* P32 = nullptr;
+    double *B64 = nullptr, *Dinv64 = nullptr;
+    float *B32 = nullptr, *Dinv32 = nullptr;
+    int* d_flag = nullptr;
+    // workspaces
+    Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[4];
+    KrylovBufs kc, ko;  // coarse GMRES, outer FGMRES
+    // stats of the current call
+    long long coarse_iters = 0;
+    int vcycles = 0;
+    double coarse_seconds = 0;
+    // profiling
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+
+    bool single() const { return p.precision != DDAMG_PREC_DOUBLE; }
+};
+
+namespace ddamg {
+
+static cudaEvent_t get_event(ddamg_handle* h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Prof {
+    ddamg_handle* h;
+    ProfRec r;
+    bool on;
+    Prof(ddamg_handle* hh, int fam, double bytes) : h(hh), on(hh->prof_on) {
+        if (on) {
+            r.fam = fam;
+            r.bytes = bytes;
+            r.e0 = get_event(h);
+            r.e1 = get_event(h);
+            cudaEventRecord(r.e0, h->stream);
+        }
+    }
+    ~Prof() {
+        if (on) {
+            cudaEventRecord(r.e1, h->stream);
+            h->prof.push_back(r);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// internal ordering (see common.cuh)
+// ---------------------------------------------------------------------------
+static int build_geometry(ddamg_handle* h) {
+    int nbt = 1, vb = 1;
+    for (int m = 0; m < 4; ++m) {
+        h->nbk[m] = h->L[m] / h->b[m];
+        nbt *= h->nbk[m];
+        vb *= h->b[m];
+    }
+    h->NB = nbt;
+    h->Vb = vb;
+    h->V = nbt * vb;
+    // blocks: red (even block-coordinate sum) first, each colour lexicographic
+    std::vector<std::array<int, 4>> bcoord(nbt);
+    std::vector<int> blex_to_int(nbt);
+    {
+        int idx = 0;
+        for (int colour = 0; colour < 2; ++colour)
+            for (int q = 0; q < nbt; ++q) {
+                int c3 = q % h->nbk[3], c2 = (q / h->nbk[3]) % h->nbk[2], c1 = (q / (h->nbk[3] * h->nbk[2])) % h->nbk[1],
+                    c0 = q / (h->nbk[3] * h->nbk[2] * h->nbk[1]);
+                if (((c0 + c1 + c2 + c3) & 1) != colour) continue;
+                bcoord[idx] = {c0, c1, c2, c3};
+                blex_to_int[q] = idx;
+                ++idx;
+            }
+    }
+    h->h_clex_of.resize(nbt);
+    for (int q = 0; q < nbt; ++q) h->h_clex_of[blex_to_int[q]] = q;
+    // local sites: even first, each lexicographic
+    std::vector<std::array<int, 4>> lcoord(vb);
+    std::vector<int> llex_to_int(vb);
+    {
+        int idx = 0;
+        for (int par = 0; par < 2; ++par)
+            for (int q = 0; q < vb; ++q) {
+                int y3 = q % h->b[3], y2 = (q / h->b[3]) % h->b[2], y1 = (q / (h->b[3] * h->b[2])) % h->b[1],
+                    y0 = q / (h->b[3] * h->b[2] * h->b[1]);
+                if (((y0 + y1 + y2 + y3) & 1) != par) continue;
+                lcoord[idx] = {y0, y1, y2, y3};
+                llex_to_int[q] = idx;
+                ++idx;
+            }
+    }
+    auto llex = [&](const std::array<int, 4>& y) { return ((y[0] * h->b[1] + y[1]) * h->b[2] + y[2]) * h->b[3] + y[3]; };
+    auto blex = [&](const std::array<int, 4>& c) { return ((c[0] * h->nbk[1] + c[1]) * h->nbk[2] + c[2]) * h->nbk[3] + c[3]; };
+    std::vector<int> lnbr(8 * vb), bnbr(8 * nbt);
+    std::vector<int> sites(9 * vb, 0);
+    for (int d = 0; d < 9; ++d) h->nsites[d] = 0;
+    for (int l = 0; l < vb; ++l) sites[h->nsites[0]++] = l;
+    for (int d = 0; d < 8; ++d) {
+        int mu = d >> 1, s = (d & 1) ? -1 : 1;
+        for (int l = 0; l < vb; ++l) {
+            std::array<int, 4> y = lcoord[l];
+            y[mu] += s;
+            int cross = 0;
+            if (y[mu] < 0 || y[mu] >= h->b[mu]) {
+                cross = 1;
+                y[mu] = (y[mu] + h->b[mu]) % h->b[mu];
+            }
+            lnbr[d * vb + l] = llex_to_int[llex(y)] | (cross << 16);
+            if (cross) sites[(1 + d) * vb + h->nsites[1 + d]++] = l;
+        }
+        for (int c = 0; c < nbt; ++c) {
+            std::array<int, 4> cc = bcoord[c];
+            cc[mu] = (cc[mu] + s + h->nbk[mu]) % h->nbk[mu];
+            bnbr[d * nbt + c] = blex_to_int[blex(cc)];
+        }
+    }
+    h->h_lex_of.resize(h->V);
+    for (int c = 0; c < nbt; ++c)
+        for (int l = 0; l < vb; ++l) {
+            int x[4];
+            for (int m = 0; m < 4; ++m) x[m] = bcoord[c][m] * h->b[m] + lcoord[l][m];
+            h->h_lex_of[(size_t)c * vb + l] = ((x[0] * h->L[1] + x[1]) * h->L[2] + x[2]) * h->L[3] + x[3];
+        }
+    DD_TRY(dalloc_n(&h->d_lnbr, lnbr.size()));
+    DD_TRY(dalloc_n(&h->d_bnbr, bnbr.size()));
+    DD_TRY(dalloc_n(&h->d_lex_of, h->h_lex_of.size()));
+    DD_TRY(dalloc_n(&h->d_clex_of, h->h_clex_of.size()));
+    DD_TRY(dalloc_n(&h->d_sites, sites.size()));
+    DD_CUDA(cudaMemcpy(h->d_lnbr, lnbr.data(), lnbr.size() * 4, cudaMemcpyHostToDevice));
+    DD_CUDA(cudaMemcpy(h->d_bnbr, bnbr.data(), bnbr.size() * 4, cudaMemcpyHostToDevice));
+    DD_CUDA(cudaMemcpy(h->d_lex_of, h->h_lex_of.data(), h->h_lex_of.size() * 4, cudaMemcpyHostToDevice));
+    DD_CUDA(cudaMemcpy(h->d_clex_of, h->h_clex_of.data(), h->h_clex_of.size() * 4, cudaMemcpyHostToDevice));
+    DD_CUDA(cudaMemcpy(h->d_sites, sites.data(), sites.size() * 4, cudaMemcpyHostToDevice));
+    h->g.V = h->V;
+    h->g.Vb = vb;
+    h->g.NB = nbt;
+    h->g.vb_shift = -1;
+    for (int s = 0; s < 31; ++s)
+        if ((1 << s) == vb) h->g.vb_shift = s;
+    h->g.lnbr = h->d_lnbr;
+    h->g.bnbr = h->d_bnbr;
+    return 0;
+}
+
+// gamma_mu gamma_nu (mu < nu) chiral blocks, from the gamma matrices of Sec. 2.2
+static int upload_gammas() {
+    static bool done = false;
+    if (done) return 0;
+    typedef std::array<std::array<std::array<double, 2>, 4>, 4> G4;
+    G4 gm[4];
+    for (auto& g : gm)
+        for (auto& r : g)
+            for (auto& e : r) e = {0.0, 0.0};
+    // gamma_0: (0,3)=i (1,2)=i (2,1)=-i (3,0)=-i
+    gm[0][0][3] = {0, 1}; gm[0][1][2] = {0, 1}; gm[0][2][1] = {0, -1}; gm[0][3][0] = {0, -1};
+    // gamma_1: (0,3)=-1 (1,2)=1 (2,1)=1 (3,0)=-1
+    gm[1][0][3] = {-1, 0}; gm[1][1][2] = {1, 0}; gm[1][2][1] = {1, 0}; gm[1][3][0] = {-1, 0};
+    // gamma_2: (0,2)=i (1,3)=-i (2,0)=-i (3,1)=i
+    gm[2][0][2] = {0, 1}; gm[2][1][3] = {0, -1}; gm[2][2][0] = {0, -1}; gm[2][3][1] = {0, 1};
+    // gamma_3: (0,2)=1 (1,3)=1 (2,0)=1 (3,1)=1
+    gm[3][0][2] = {1, 0}; gm[3][1][3] = {1, 0}; gm[3][2][0] = {1, 0}; gm[3][3][1] = {1, 0};
+    double gg[6][2][2][2][2];
+    int plane = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+            double prod[4][4][2];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    double re = 0, im = 0;
+                    for (int k = 0; k < 4; ++k) {
+                        re += gm[mu][i][k][0] * gm[nu][k][j][0] - gm[mu][i][k][1] * gm[nu][k][j][1];
+                        im += gm[mu][i][k][0] * gm[nu][k][j][1] + gm[mu][i][k][1] * gm[nu][k][j][0];
+                    }
+                    prod[i][j][0] = re;
+                    prod[i][j][1] = im;
+                }
+            for (int hh = 0; hh < 2; ++hh)
+                for (int s = 0; s < 2; ++s)
+                    for (int t = 0; t < 2; ++t) {
+                        gg[plane][hh][s][t][0] = prod[2 * hh + s][2 * hh + t][0];
+                        gg[plane][hh][s][t][1] = prod[2 * hh + s][2 * hh + t][1];
+                    }
+        }
+    DD_TRY(upload_gamma_products(&gg[0][0][0][0][0]));
+    done = true;
+    return 0;
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of caller data: device pointers pass through, host data is staged
+static int stage_in(ddamg_handle* h, Scratch& s, const void* src, size_t bytes, const void** dev) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return 0;
+    }
+    DD_TRY(s.ensure(bytes));
+    DD_CUDA(cudaMemcpyAsync(s.p, src, bytes, cudaMemcpyHostToDevice, h->stream));
+    *dev = s.p;
+    return 0;
+}
+static int stage_out_ptr(Scratch& s, void* dst, size_t bytes, void** dev, bool* host) {
+    *host = !is_device_ptr(dst);
+    if (!*host) {
+        *dev = dst;
+        return 0;
+    }
+    DD_TRY(s.ensure(bytes));
+    *dev = s.p;
+    return 0;
+}
+static int finish_out(ddamg_handle* h, void* dst, const void* dev, size_t bytes, bool host) {
+    if (host) DD_CUDA(cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// precision views
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Level {
+    FineOp<T> op;
+    const cplx<T>* P;
+    CoarseOp<T> cop;
+};
+static Level<double> level64(ddamg_handle* h) {
+    Level<double> L;
+    L.op = {h->U64, h->clov64, h->clovinv64};
+    L.P = h->P64;
+    L.cop = {h->B64, h->Dinv64, h->d_bnbr, h->NB, h->nc};
+    return L;
+}
+static Level<float> level32(ddamg_handle* h) {
+    Level<float> L;
+    L.op = {h->U32, h->clov32, h->clovinv32};
+    L.P = h->P32;
+    L.cop = {h->B32, h->Dinv32, h->d_bnbr, h->NB, h->nc};
+    return L;
+}
+template <typename T>
+static Level<T> level(ddamg_handle* h);
+template <>
+Level<double> level<double>(ddamg_handle* h) {
+    return level64(h);
+}
+template <>
+Level<float> level<float>(ddamg_handle* h) {
+    return level32(h);
+}
+
+static double dslash_bytes(ddamg_handle* h, size_t real, int nrhs, bool resid) {
+    double site = 36.0 * 2 * real + 72.0 * real;  // links + clover, once per launch
+    double vec = (resid ? 36.0 : 24.0) * 2 * real;  // in + out (+ b) per rhs
+    return (double)h->V * (site + vec * nrhs);
+}
+
+template <typename T, typename Ts>
+static int dslash(ddamg_handle* h, const cplx<Ts>* in, const cplx<T>* b, cplx<T>* out, int nrhs) {
+    Level<T> L = level<T>(h);
+    Prof pr(h, sizeof(T) == 8 ? PF_DSLASH64 : PF_DSLASH32, dslash_bytes(h, sizeof(T), nrhs, b != nullptr));
+    return launch_dslash<T, Ts>(h->g, L.op, in, b, out, nrhs, h->stream);
+}
+
+// z <- SAP iterations (nu) on D z = b from the current z (Sec. 2.3)
+template <typename T>
+static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) {
+    Level<T> L = level<T>(h);
+    for (int it = 0; it < nu; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * sizeof(T) + 144.0 * sizeof(T) + nrhs * 36.0 * 2 * sizeof(T)));
+            DD_TRY(launch_sap_colour<T>(h->g, L.op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
+        }
+    return 0;
+}
+
+template <typename T>
+static int restrict_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) {
+    Level<T> L = level<T>(h);
+    Prof pr(h, PF_RESTRICT, (double)h->V * (12.0 * h->N + 12.0 * nrhs) * 2 * sizeof(T));
+    return launch_restrict<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
+}
+template <typename T>
+static int prolong_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) {
+    Level<T> L = level<T>(h);
+    Prof pr(h, PF_PROLONG, (double)h->V * (12.0 * h->N + 12.0 * nrhs) * 2 * sizeof(T));
+    return launch_prolong<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// batched restarted (F)GMRES.  Vectors of length n per rhs, rhs stride n.
+// A: w = A z;  M (optional): z = M v (flexible; Z basis kept).
+// x holds the initial guess (x0_zero: treat as 0) and receives the solution.
+// ---------------------------------------------------------------------------
+template <typename TV, typename TZ>
+struct KrylovProblem {
+    size_t n;
+    int nrhs;
+    int m;
+    std::function<int(const cplx<TZ>*, cplx<TV>*)> A;      // w = A z for basis-type input, all nrhs at once
+    std::function<int(const cplx<TV>*, cplx<TV>*)> Ax;     // w = A x for the iterate (residuals)
+    std::function<int(const cplx<TV>*, cplx<TZ>*)> M;      // empty: no preconditioner (TZ == TV)
+    const cplx<TV>* b;
+    cplx<TV>* x;
+    bool x0_zero;
+    double tol;            // relative to ||b_r||
+    long long maxiter;     // Arnoldi steps per rhs
+    bool fixed;            // run exactly maxiter steps (no tolerance)
+    bool reorth;           // classical Gram-Schmidt twice
+    cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
+    cplx<TZ>* Zb;          // [m][nrhs][n] when M is set
+    cplx<TV>* w;           // [nrhs][n]
+    const int* enabled_host;  // optional per-rhs participation (nullptr: all)
+};
+
+struct KrylovResult {
+    std::vector<long long> iters;
+    std::vector<double> resid;  // last residual estimate relative to ||b||
+    std::vector<double> bnorm;
+    int restarts = 0;
+    bool nonfinite = false;
+    bool converged = true;
+};
+
+template <typename TV, typename TZ>
+static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, KrylovResult& R) {
+    cudaStream_t st = h->stream;
+    const int nr = P.nrhs;
+    const size_t n = P.n;
+    DD_TRY(kb.alloc(nr, P.m));
+    KrylovState& s = kb.s;
+    s.nrhs = nr;
+    R.iters.assign(nr, 0);
+    R.resid.assign(nr, 0.0);
+    R.bnorm.assign(nr, 0.0);
+    // ||b||, targets, enabled
+    DD_TRY((multidot<TV, TV>(P.b, 0, n, 1, P.b, n, n, nr, kb.nrm, 1, kb.dscr, st)));
+    std::vector<cplx<double>> hb(nr);
+    DD_CUDA(cudaMemcpyAsync(hb.data(), kb.nrm, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> target(nr);
+    std::vector<int> en(nr, 1);
+    for (int r = 0; r < nr; ++r) {
+        R.bnorm[r] = std::sqrt(hb[r].re);
+        target[r] = P.fixed ? -1.0 : P.tol * R.bnorm[r];
+        if (P.enabled_host && !P.enabled_host[r]) en[r] = 0;
+        if (!(R.bnorm[r] == R.bnorm[r])) R.nonfinite = true;
+    }
+    DD_CUDA(cudaMemcpyAsync(s.target, target.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+    DD_CUDA(cudaMemcpyAsync(s.enabled, en.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    DD_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(int) * nr, st));
+    const size_t bstride = (size_t)nr * n;  // between basis vectors
+    cplx<TV>* V0 = P.Vb;
+    auto residual_to_V0 = [&]() -> int {
+        DD_TRY(P.Ax(P.x, P.w));
+        DD_CUDA(cudaMemcpyAsync(V0, P.b, sizeof(cplx<TV>) * nr * n, cudaMemcpyDeviceToDevice, st));
+        DD_TRY((lincomb<TV, TV>(V0, n, 1.0, P.w, 0, n, 1, kb.ones, nr, n, nr, nullptr, st, -1.0)));
+        return 0;
+    };
+    if (P.x0_zero) {
+        DD_CUDA(cudaMemsetAsync(P.x, 0, sizeof(cplx<TV>) * nr * n, st));
+        DD_CUDA(cudaMemcpyAsync(V0, P.b, sizeof(cplx<TV>) * nr * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        DD_TRY(residual_to_V0());
+    }
+    long long total = 0;
+    while (true) {
+        // start of a cycle
+        DD_TRY((multidot<TV, TV>(V0, 0, n, 1, V0, n, n, nr, kb.nrm, 1, kb.dscr, st)));
+        DD_TRY(arnoldi_start(s, kb.nrm, kb.scale, P.fixed ? 1 : 0, st));
+        DD_TRY((lincomb<TV, TV>(V0, n, 0.0, V0, 0, n, 1, kb.scale, nr, n, nr, nullptr, st)));
+        DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaStreamSynchronize(st));
+        int nact = 0;
+        for (int r = 0; r < nr; ++r) {
+            nact += kb.h_active[r];
+            if (en[r]) R.resid[r] = R.bnorm[r] > 0 ? kb.h_resid[r] / R.bnorm[r] : 0.0;
+        }
+        if (nact == 0) break;
+        if (total >= P.maxiter) {
+            R.converged = false;
+            break;
+        }
+        int k = 0;
+        for (; k < P.m; ++k) {
+            cplx<TV>* Vk = P.Vb + (size_t)k * bstride;
+            const cplx<TZ>* zk;
+            if (P.M) {
+                cplx<TZ>* Zk = P.Zb + (size_t)k * bstride;
+                DD_TRY(P.M(Vk, Zk));
+                zk = Zk;
+            } else {
+                zk = reinterpret_cast<const cplx<TZ>*>(Vk);
+            }
+            DD_TRY(P.A(zk, P.w));
+            // classical Gram-Schmidt (twice when reorth)
+            DD_TRY((multidot<TV, TV>(P.Vb, bstride, n, k + 1, P.w, n, n, nr, kb.hcol, nr, kb.dscr, st)));
+            DD_TRY((lincomb<TV, TV>(P.w, n, 1.0, P.Vb, bstride, n, k + 1, kb.hcol, nr, n, nr, nullptr, st, -1.0)));
+            if (P.reorth) {
+                DD_TRY((multidot<TV, TV>(P.Vb, bstride, n, k + 1, P.w, n, n, nr, kb.hcol2, nr, kb.dscr, st)));
+                DD_TRY((lincomb<TV, TV>(P.w, n, 1.0, P.Vb, bstride, n, k + 1, kb.hcol2, nr, n, nr, nullptr, st, -1.0)));
+                DD_TRY(add_columns(kb.hcol, kb.hcol2, (k + 1) * nr, st));
+            }
+            DD_TRY((multidot<TV, TV>(P.w, 0, n, 1, P.w, n, n, nr, kb.hcol + (size_t)(k + 1) * nr, nr, kb.dscr, st)));
+            DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
+            DD_TRY((lincomb<TV, TV>(P.Vb + (size_t)(k + 1) * bstride, n, 0.0, P.w, 0, n, 1, kb.scale, nr, n, nr, nullptr, st)));
+            ++total;
+            if (P.fixed) {
+                if (total >= P.maxiter) {
+                    ++k;
+                    break;
+                }
+                continue;
+            }
+            DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+            DD_CUDA(cudaStreamSynchronize(st));
+            int na = 0;
+            for (int r = 0; r < nr; ++r) na += kb.h_active[r];
+            if (na == 0 || total >= P.maxiter) {
+                ++k;
+                break;
+            }
+        }
+        // x += sum_i y_i Z_i (or V_i)
+        DD_TRY(arnoldi_solve(s, kb.y, st));
+        if (P.M)
+            DD_TRY((lincomb<TV, TZ>(P.x, n, 1.0, P.Zb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
+        else
+            DD_TRY((lincomb<TV, TV>(P.x, n, 1.0, P.Vb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
+        DD_CUDA(cudaMemcpyAsync(kb.h_steps, s.steps, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaMemcpyAsync(kb.h_flags, s.flags, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < nr; ++r) {
+            R.iters[r] += kb.h_steps[r];
+            if (kb.h_steps[r] > 0) R.resid[r] = R.bnorm[r] > 0 ? kb.h_resid[r] / R.bnorm[r] : 0.0;
+            if (kb.h_flags[r] & 2) R.nonfinite = true;
+        }
+        if (P.fixed && total >= P.maxiter) break;
+        if (R.nonfinite) break;
+        // restart: V0 = b - A x
+        DD_TRY(residual_to_V0());
+        ++R.restarts;
+    }
+    return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// coarse solve: odd-even reduced GMRES(restart) (Sec. 6) on full coarse vectors
+// ---------------------------------------------------------------------------
+template <typename T>
+static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrhs, int fixed_iters) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->stream;
+    const int H = h->NB / 2, nc = h->nc;
+    const size_t hn = (size_t)H * nc, full = (size_t)h->NB * nc;
+    const int m = h->p.coarse_restart;
+    DD_TRY(h->ws_coarse[0].ensure(sizeof(cplx<T>) * hn * nrhs));
+    DD_TRY(h->ws_coarse[1].ensure(sizeof(cplx<T>) * hn * nrhs));
+    DD_TRY(h->ws_coarse[2].ensure(sizeof(cplx<T>) * hn * nrhs));
+    DD_TRY(h->ws_coarse[3].ensure(sizeof(cplx<T>) * hn * nrhs));
+    DD_TRY(h->ws_coarse[4].ensure(sizeof(cplx<T>) * hn * nrhs * (m + 1)));
+    cplx<T>* te = h->ws_coarse[0].as<cplx<T>>();
+    cplx<T>* bp = h->ws_coarse[1].as<cplx<T>>();
+    cplx<T>* xo = h->ws_coarse[2].as<cplx<T>>();
+    cplx<T>* w = h->ws_coarse[3].as<cplx<T>>();
+    cplx<T>* basis = h->ws_coarse[4].as<cplx<T>>();
+    Level<T> L = level<T>(h);
+    const double sbytes = (double)h->NB * 9 * nc * nc * sizeof(cplx<T>);
+    {
+        Prof pr(h, PF_COARSE, sbytes / 9);
+        DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, nullptr, 0, T(0), te, hn, nrhs, st)));
+    }
+    {
+        Prof pr(h, PF_COARSE, sbytes * 4 / 9);
+        DD_TRY((launch_coarse_odd<T, T>(L.cop, bc + hn, full, te, hn, 0, bp, hn, nrhs, st)));
+    }
+    KrylovProblem<T, T> P;
+    P.n = hn;
+    P.nrhs = nrhs;
+    P.m = m;
+    P.A = [&](const cplx<T>* v, cplx<T>* out) -> int {
+        {
+            Prof pr(h, PF_COARSE, sbytes / 2);
+            DD_TRY((launch_coarse_even<T, T>(L.cop, nullptr, 0, v, hn, T(1), te, hn, nrhs, st)));
+        }
+        Prof pr(h, PF_COARSE, sbytes / 2);
+        return launch_coarse_odd<T, T>(L.cop, v, hn, te, hn, 1, out, hn, nrhs, st);
+    };
+    P.Ax = P.A;
+    P.b = bp;
+    P.x = xo;
+    P.x0_zero = true;
+    P.tol = h->p.coarse_tol;
+    P.fixed = fixed_iters > 0;
+    P.maxiter = fixed_iters > 0 ? fixed_iters : h->p.coarse_maxiter;
+    P.reorth = false;
+    P.Vb = basis;
+    P.Zb = nullptr;
+    P.w = w;
+    P.enabled_host = nullptr;
+    KrylovResult R;
+    DD_TRY((krylov<T, T>(h, h->kc, P, R)));
+    long long it = 0;
+    for (long long v : R.iters) it = std::max(it, v);
+    h->coarse_iters += it;
+    // back-substitution x_e = D_ee^{-1} (b_e - D_eo x_o); x_o into the odd half
+    {
+        Prof pr(h, PF_COARSE, sbytes / 2);
+        DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, xo, hn, T(-1), xc, full, nrhs, st)));
+    }
+    DD_CUDA(cudaMemcpy2DAsync(xc + hn, full * sizeof(cplx<T>), xo, hn * sizeof(cplx<T>), hn * sizeof(cplx<T>), nrhs,
+                              cudaMemcpyDeviceToDevice, st));
+    h->coarse_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return 0;
+}
+
+// x = C^(nu) r (Sec. 4.2): x = P D_c^{-1} P^H r, then nu SAP iterations on D x = r
+// starting from that x, which adds M_SAP^(nu) (r - D x) (the SAP update is affine).
+template <typename T>
+static int vcycle(ddamg_handle* h, const cplx<T>* r, cplx<T>* x, int nrhs, int coarse_fixed) {
+    const size_t full = (size_t)h->NB * h->nc;
+    DD_TRY(h->ws_coarse[5].ensure(sizeof(cplx<T>) * full * nrhs));
+    DD_TRY(h->ws_coarse[6].ensure(sizeof(cplx<T>) * full * nrhs));
+    cplx<T>* cb = h->ws_coarse[5].as<cplx<T>>();
+    cplx<T>* cx = h->ws_coarse[6].as<cplx<T>>();
+    DD_TRY(restrict_<T>(h, r, cb, nrhs));
+    DD_TRY(coarse_solve<T>(h, cb, cx, nrhs, coarse_fixed));
+    DD_TRY(prolong_<T>(h, cx, x, nrhs));
+    DD_TRY(sap<T>(h, r, x, nrhs, h->p.nu));
+    h->vcycles += nrhs;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// interpolation: P by local orthonormalisation, D_c by assembly, coarse inverses
+// ---------------------------------------------------------------------------
+static int build_interpolation(ddamg_handle* h) {
+    cudaStream_t st = h->stream;
+    const int N = h->N, nc = h->nc;
+    const size_t fld = (size_t)12 * h->V;
+    DD_CUDA(cudaMemcpyAsync(h->P64, h->V64, sizeof(cplx<double>) * fld * N, cudaMemcpyDeviceToDevice, st));
+    DD_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), st));
+    DD_TRY(launch_gram_schmidt(h->g, h->P64, N, h->d_flag, st));
+    int flag = 0;
+    DD_CUDA(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        set_error("test vectors are linearly dependent on an aggregate");
+        return DDAMG_ERR_RANK;
+    }
+    Scratch tscr;
+    DD_TRY(tscr.ensure(sizeof(cplx<double>) * fld * 2 * N));
+    FineOp<double> op64{h->U64, h->clov64, h->clovinv64};
+    int rc = 0;
+    for (int dir = 0; dir < 9 && !rc; ++dir) {
+        rc = launch_assemble_T(h->g, op64, h->P64, N, dir, tscr.as<cplx<double>>(), st);
+        if (!rc)
+            rc = launch_block_project(h->g, h->P64, N, tscr.as<cplx<double>>(), h->d_sites + (size_t)dir * h->Vb, h->nsites[dir],
+                                      h->B64 + (size_t)dir * nc * nc * 2, (size_t)9 * nc * nc, st);
+    }
+    DD_CUDA(cudaStreamSynchronize(st));
+    tscr.release();
+    if (rc) return rc;
+    DD_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), st));
+    DD_TRY(launch_coarse_invert(h->B64, h->Dinv64, h->NB, nc, h->d_flag, st));
+    DD_CUDA(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        set_error("singular diagonal block of the coarse operator");
+        return DDAMG_ERR_RANK;
+    }
+    if (h->single()) {
+        DD_TRY((convert<float, double>(reinterpret_cast<const double*>(h->P64), reinterpret_cast<float*>(h->P32), 2 * fld * N, st)));
+        DD_TRY((convert<float, double>(h->B64, h->B32, (size_t)h->NB * 9 * nc * nc * 2, st)));
+        DD_TRY((convert<float, double>(h->Dinv64, h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2, st)));
+    }
+    DD_CUDA(cudaStreamSynchronize(st));
+    h->ready = true;
+    return 0;
+}
+
+__global__ void gaussian_fill_kernel(double* out, size_t n, unsigned long long seed) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        // splitmix64 of (seed, q) -> two uniforms -> Box-Muller
+        unsigned long long z = seed * 0x9E3779B97F4A7C15ull + q * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        double u1 = ((z >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+        unsigned long long y = z * 0xD6E8FEB86659FD93ull + 0x2545F4914F6CDD1Dull;
+        y ^= y >> 32;
+        double u2 = (y >> 11) * (1.0 / 9007199254740992.0);
+        out[q] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+}
+
+// Algorithm 2 (Algorithm 1 with the modified update) on vectors in precision T
+template <typename T>
+static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
+    cudaStream_t st = h->stream;
+    const int N = h->N;
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[0].ensure(sizeof(cplx<T>) * fld * N));
+    DD_TRY(h->ws_fine[1].ensure(sizeof(cplx<T>) * fld * N));
+    cplx<T>* t1 = h->ws_fine[0].as<cplx<T>>();
+    cplx<T>* t2 = h->ws_fine[1].as<cplx<T>>();
+    // phase 1: v_j <- M_SAP^(eta) v_j, eta = 1, 2, 3
+    for (int eta = 1; eta <= 3; ++eta) {
+        DD_CUDA(cudaMemsetAsync(t1, 0, sizeof(cplx<T>) * fld * N, st));
+        DD_TRY(sap<T>(h, v, t1, N, eta));
+        DD_CUDA(cudaMemcpyAsync(v, t1, sizeof(cplx<T>) * fld * N, cudaMemcpyDeviceToDevice, st));
+    }
+    KrylovBufs& kb = h->ko;
+    DD_TRY(kb.alloc(std::max(N, kb.nrhs), std::max(1, h->p.n_kv)));
+    auto to64 = [&]() -> int {
+        if (sizeof(T) == 8)
+            DD_CUDA(cudaMemcpyAsync(h->V64, v, sizeof(cplx<T>) * fld * N, cudaMemcpyDeviceToDevice, st));
+        else
+            DD_TRY((convert<double, T>(reinterpret_cast<const T*>(v), reinterpret_cast<double*>(h->V64), 2 * fld * N, st)));
+        return 0;
+    };
+    for (int it = 0; it < h->p.n_inv; ++it) {
+        DD_TRY(to64());
+        DD_TRY(build_interpolation(h));
+        // v_j <- v_j + C (v_j - D v_j);  v_j <- v_j / ||v_j||
+        DD_TRY((dslash<T, T>(h, v, v, t1, N)));
+        DD_TRY(vcycle<T>(h, t1, t2, N, 0));
+        DD_TRY((lincomb<T, T>(v, fld, 1.0, t2, 0, fld, 1, kb.ones, N, fld, N, nullptr, st)));
+        DD_TRY((multidot<T, T>(v, 0, fld, 1, v, fld, fld, N, kb.nrm, 1, kb.dscr, st)));
+        std::vector<cplx<double>> nn(N);
+        DD_CUDA(cudaMemcpyAsync(nn.data(), kb.nrm, sizeof(cplx<double>) * N, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < N; ++j) {
+            double nv = std::sqrt(nn[j].re);
+            if (!(nv > 0) || !(nv == nv)) {
+                set_error("setup produced a zero or non-finite test vector");
+                return DDAMG_ERR_NONFINITE;
+            }
+            nn[j] = mk(1.0 / nv, 0.0);
+        }
+        DD_CUDA(cudaMemcpyAsync(kb.scale, nn.data(), sizeof(cplx<double>) * N, cudaMemcpyHostToDevice, st));
+        DD_TRY((lincomb<T, T>(v, fld, 0.0, v, 0, fld, 1, kb.scale, N, fld, N, nullptr, st)));
+    }
+    DD_TRY(to64());
+    if (h->p.rebuild_after_last || h->p.n_inv == 0) DD_TRY(build_interpolation(h));
+    return 0;
+}
+
+static int run_setup(ddamg_handle* h, const double* v0) {
+    cudaStream_t st = h->stream;
+    const int N = h->N;
+    const size_t fld = (size_t)12 * h->V;
+    // initial vectors into V64 (internal order)
+    if (v0) {
+        const void* dv;
+        DD_TRY(stage_in(h, h->ws_io[0], v0, sizeof(cplx<double>) * fld * N, &dv));
+        DD_TRY((to_internal<double, double>(reinterpret_cast<const cplx<double>*>(dv), h->V64, h->d_lex_of, h->V, 12, N, st)));
+    } else {
+        gaussian_fill_kernel<<<1216, 256, 0, st>>>(reinterpret_cast<double*>(h->V64), 2 * fld * N, h->p.seed);
+        DD_CHECK_LAUNCH();
+    }
+    int rc;
+    if (h->single()) {
+        DD_TRY(h->ws_fine[2].ensure(sizeof(cplx<float>) * fld * N));
+        cplx<float>* v = h->ws_fine[2].as<cplx<float>>();
+        DD_TRY((convert<float, double>(reinterpret_cast<const double*>(h->V64), reinterpret_cast<float*>(v), 2 * fld * N, st)));
+        rc = run_setup_T<float>(h, v);
+    } else {
+        DD_TRY(h->ws_fine[2].ensure(sizeof(cplx<double>) * fld * N));
+        cplx<double>* v = h->ws_fine[2].as<cplx<double>>();
+        DD_CUDA(cudaMemcpyAsync(v, h->V64, sizeof(cplx<double>) * fld * N, cudaMemcpyDeviceToDevice, st));
+        rc = run_setup_T<double>(h, v);
+    }
+    for (int q = 0; q < 3; ++q) h->ws_fine[q].release();
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// the outer solve: FGMRES(n_kv) in FP64, one V-cycle as right preconditioner
+// ---------------------------------------------------------------------------
+template <typename TZ>
+static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R) {
+    cudaStream_t st = h->stream;
+    const size_t fld = (size_t)12 * h->V;
+    const int m = h->p.n_kv;
+    DD_TRY(h->ws_outer[0].ensure(sizeof(cplx<double>) * fld * nrhs * (m + 1)));
+    DD_TRY(h->ws_outer[1].ensure(sizeof(cplx<TZ>) * fld * nrhs * m));
+    DD_TRY(h->ws_outer[2].ensure(sizeof(cplx<double>) * fld * nrhs));
+    DD_TRY(h->ws_outer[3].ensure(sizeof(cplx<TZ>) * fld * nrhs));
+    cplx<TZ>* rT = h->ws_outer[3].as<cplx<TZ>>();
+    KrylovProblem<double, TZ> P;
+    P.n = fld;
+    P.nrhs = nrhs;
+    P.m = m;
+    P.A = [&](const cplx<TZ>* z, cplx<double>* w) -> int { return dslash<double, TZ>(h, z, nullptr, w, nrhs); };
+    P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int { return dslash<double, double>(h, z, nullptr, w, nrhs); };
+    P.M = [&](const cplx<double>* v, cplx<TZ>* z) -> int {
+        const cplx<TZ>* r;
+        if (sizeof(TZ) == 8) {
+            r = reinterpret_cast<const cplx<TZ>*>(v);
+        } else {
+            DD_TRY((convert<TZ, double>(reinterpret_cast<const double*>(v), reinterpret_cast<TZ*>(rT), 2 * fld * nrhs, st)));
+            r = rT;
+        }
+        return vcycle<TZ>(h, r, z, nrhs, 0);
+    };
+    P.b = b;
+    P.x = x;
+    P.x0_zero = x0_zero;
+    P.tol = tol;
+    P.fixed = false;
+    P.maxiter = h->p.max_outer;
+    P.reorth = true;
+    P.Vb = h->ws_outer[0].as<cplx<double>>();
+    P.Zb = h->ws_outer[1].as<cplx<TZ>>();
+    P.w = h->ws_outer[2].as<cplx<double>>();
+    P.enabled_host = nullptr;
+    return krylov<double, TZ>(h, h->ko, P, R);
+}
+
+static int check_ready(ddamg_handle* h) {
+    if (!h) {
+        set_error("null handle");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    if (!h->ready) {
+        set_error("no interpolation: run ddamg_setup / ddamg_setup_from_vectors first");
+        return DDAMG_ERR_NOT_READY;
+    }
+    return 0;
+}
+
+static int create(const ddamg_lattice* lat, const double* U, double m0, double csw, const ddamg_params* prm, ddamg_handle** out) {
+    if (!lat || !U || !out) {
+        set_error("null argument");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    ddamg_params p;
+    if (prm) p = *prm;
+    else ddamg_default_params(&p);
+    for (int m = 0; m < 4; ++m) {
+        int L = lat->dims[m], b = p.block[m];
+        if (L <= 0 || b <= 0 || (b & 1) || L % b || ((L / b) & 1)) {
+            set_error("every extent must be divisible by an even block extent into an even number (>= 2) of blocks");
+            return DDAMG_ERR_INVALID_ARG;
+        }
+    }
+    if (p.n_vec < 1 || p.n_vec > 32 || p.nu < 0 || p.mr_steps < 0 || p.n_kv < 1 || p.coarse_restart < 1 ||
+        p.precision < DDAMG_PREC_DOUBLE || p.precision > DDAMG_PREC_HALF || p.n_inv < 0) {
+        set_error("parameter out of range (1 <= n_vec <= 32, n_kv >= 1, coarse_restart >= 1, nu, mr_steps, n_inv >= 0)");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    long long vb = (long long)p.block[0] * p.block[1] * p.block[2] * p.block[3];
+    if (vb > 1024) {
+        set_error("block volume above 1024 sites");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    ddamg_handle* h = new ddamg_handle();
+    for (int m = 0; m < 4; ++m) {
+        h->L[m] = lat->dims[m];
+        h->b[m] = p.block[m];
+    }
+    h->p = p;
+    h->m0 = m0;
+    h->csw = csw;
+    h->N = p.n_vec;
+    h->nc = 2 * p.n_vec;
+    int rc = 0;
+    auto fail = [&](int code) {
+        ddamg_destroy(h);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaStreamCreate failed");
+        delete h;
+        return DDAMG_ERR_CUDA;
+    }
+    h->stream = h->own_stream;
+    if ((rc = upload_gammas())) return fail(rc);
+    if ((rc = build_geometry(h))) return fail(rc);
+    const size_t V = h->V, N = h->N, nc = h->nc;
+    if ((rc = dalloc_n(&h->U64, V * 36)) || (rc = dalloc_n(&h->clov64, V * 72)) || (rc = dalloc_n(&h->clovinv64, V * 72)) ||
+        (rc = dalloc_n(&h->V64, V * 12 * N)) || (rc = dalloc_n(&h->P64, V * 12 * N)) ||
+        (rc = dalloc_n(&h->B64, (size_t)h->NB * 9 * nc * nc * 2)) || (rc = dalloc_n(&h->Dinv64, (size_t)(h->NB / 2) * nc * nc * 2)) ||
+        (rc = dalloc_n(&h->d_flag, 1)))
+        return fail(rc);
+    if (h->single()) {
+        if ((rc = dalloc_n(&h->U32, V * 36)) || (rc = dalloc_n(&h->clov32, V * 72)) || (rc = dalloc_n(&h->clovinv32, V * 72)) ||
+            (rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
+            (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)))
+            return fail(rc);
+    }
+    // gauge field -> internal order, clover term and inverses
+    const void* dU;
+    if ((rc = stage_in(h, h->ws_io[0], U, sizeof(cplx<double>) * V * 36, &dU))) return fail(rc);
+    if ((rc = gauge_to_internal(reinterpret_cast<const cplx<double>*>(dU), h->U64, h->d_lex_of, h->V, h->stream))) return fail(rc);
+    if ((rc = launch_clover(h->g, h->U64, m0, csw, h->clov64, h->clovinv64, h->stream))) return fail(rc);
+    if (h->single()) {
+        if ((rc = convert<float, double>(reinterpret_cast<const double*>(h->U64), reinterpret_cast<float*>(h->U32), V * 72, h->stream)) ||
+            (rc = convert<float, double>(h->clov64, h->clov32, V * 72, h->stream)) ||
+            (rc = convert<float, double>(h->clovinv64, h->clovinv32, V * 72, h->stream)))
+            return fail(rc);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_error(std::string("setup kernels: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(DDAMG_ERR_CUDA);
+    }
+    h->ws_io[0].release();
+    *out = h;
+    return 0;
+}
+
+template <typename T>
+static int fine_in(ddamg_handle* h, const double* in, int nrhs, Scratch& tmp, cplx<T>* dst) {
+    const size_t fld = (size_t)12 * h->V;
+    const void* dv;
+    DD_TRY(stage_in(h, h->ws_io[0], in, sizeof(cplx<double>) * fld * nrhs, &dv));
+    (void)tmp;
+    return to_internal<T, double>(reinterpret_cast<const cplx<double>*>(dv), dst, h->d_lex_of, h->V, 12, nrhs, h->stream);
+}
+template <typename T>
+static int fine_out(ddamg_handle* h, const cplx<T>* src, double* out, int nrhs) {
+    const size_t fld = (size_t)12 * h->V;
+    void* dv;
+    bool host;
+    DD_TRY(stage_out_ptr(h->ws_io[1], out, sizeof(cplx<double>) * fld * nrhs, &dv, &host));
+    DD_TRY((from_internal<double, T>(src, reinterpret_cast<cplx<double>*>(dv), h->d_lex_of, h->V, 12, nrhs, h->stream)));
+    return finish_out(h, out, dv, sizeof(cplx<double>) * fld * nrhs, host);
+}
+template <typename T>
+static int coarse_in(ddamg_handle* h, const double* in, int nrhs, cplx<T>* dst) {
+    const size_t n = (size_t)h->NB * h->nc;
+    const void* dv;
+    DD_TRY(stage_in(h, h->ws_io[0], in, sizeof(cplx<double>) * n * nrhs, &dv));
+    return coarse_perm<T, double>(reinterpret_cast<const cplx<double>*>(dv), dst, h->d_clex_of, h->NB, h->nc, nrhs, 1, h->stream);
+}
+template <typename T>
+static int coarse_out(ddamg_handle* h, const cplx<T>* src, double* out, int nrhs) {
+    const size_t n = (size_t)h->NB * h->nc;
+    void* dv;
+    bool host;
+    DD_TRY(stage_out_ptr(h->ws_io[1], out, sizeof(cplx<double>) * n * nrhs, &dv, &host));
+    DD_TRY((coarse_perm<double, T>(src, reinterpret_cast<cplx<double>*>(dv), h->d_clex_of, h->NB, h->nc, nrhs, 0, h->stream)));
+    return finish_out(h, out, dv, sizeof(cplx<double>) * n * nrhs, host);
+}
+
+}  // namespace ddamg
+
+// ===========================================================================
+// extern "C" entry points
+// ===========================================================================
+extern "C" {
+
+void ddamg_default_params(ddamg_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_inv = 6;
+    p->n_vec = 20;
+    for (int m = 0; m < 4; ++m) p->block[m] = 4;
+    p->coarse_tol = 5e-2;
+    p->coarse_restart = 30;
+    p->coarse_maxiter = 1000;
+    p->n_kv = 25;
+    p->tol = 1e-10;
+    p->max_outer = 10000;
+    p->nu = 2;
+    p->mr_steps = 4;
+    p->precision = DDAMG_PREC_SINGLE;
+    p->rebuild_after_last = 1;
+    p->seed = 1;
+    p->time_limit_s = 0;
+}
+
+const char* ddamg_error_string(int s) {
+    switch (s) {
+        case DDAMG_OK: return "ok";
+        case DDAMG_ERR_INVALID_ARG: return "invalid argument";
+        case DDAMG_ERR_OOM: return "out of device memory";
+        case DDAMG_ERR_CUDA: return "CUDA error";
+        case DDAMG_ERR_NOT_CONVERGED: return "not converged";
+        case DDAMG_ERR_NONFINITE: return "non-finite value";
+        case DDAMG_ERR_TIMEOUT: return "time limit exceeded";
+        case DDAMG_ERR_NOT_READY: return "setup missing";
+        case DDAMG_ERR_RANK: return "rank-deficient aggregate";
+        default: return "unknown status";
+    }
+}
+
+const char* ddamg_last_error(void) { return g_err.c_str(); }
+
+long long ddamg_launch_count(void) { return (long long)g_launches; }
+
+void ddamg_debug_fail_allocs(int n) { g_fail_allocs = n; }
+
+int ddamg_create(const ddamg_lattice* lat, const double* U, double m0, double c_sw, const ddamg_params* params, ddamg_handle** out) {
+    return create(lat, U, m0, c_sw, params, out);
+}
+
+int ddamg_run_setup(ddamg_handle* h, const double* v0) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    return run_setup(h, v0);
+}
+
+int ddamg_setup(const ddamg_lattice* lat, const double* U, double m0, double c_sw, const ddamg_params* params, ddamg_handle** out) {
+    ddamg_handle* h = nullptr;
+    int rc = create(lat, U, m0, c_sw, params, &h);
+    if (rc) return rc;
+    rc = run_setup(h, nullptr);
+    if (rc) {
+        ddamg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return 0;
+}
+
+int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N) {
+    if (!h || !V || N != h->N) {
+        set_error("ddamg_setup_from_vectors: null argument or N differs from params.n_vec");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    const size_t fld = (size_t)12 * h->V;
+    const void* dv;
+    DD_TRY(stage_in(h, h->ws_io[0], V, sizeof(cplx<double>) * fld * N, &dv));
+    DD_TRY((to_internal<double, double>(reinterpret_cast<const cplx<double>*>(dv), h->V64, h->d_lex_of, h->V, 12, N, h->stream)));
+    return build_interpolation(h);
+}
+
+int ddamg_get_vectors(const ddamg_handle* hc, double* V) {
+    ddamg_handle* h = const_cast<ddamg_handle*>(hc);
+    if (!h || !V) return DDAMG_ERR_INVALID_ARG;
+    return fine_out<double>(h, h->V64, V, h->N);
+}
+
+static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, double tol, ddamg_stats* st) {
+    DD_TRY(check_ready(h));
+    if (!b || !z || nrhs < 1) {
+        set_error("solve: null pointer or n_rhs < 1");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    if (tol <= 0) tol = h->p.tol;
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_io[2].ensure(sizeof(cplx<double>) * fld * nrhs * 2));
+    cplx<double>* bi = h->ws_io[2].as<cplx<double>>();
+    cplx<double>* xi = bi + fld * nrhs;
+    DD_TRY(fine_in<double>(h, b, nrhs, h->ws_io[0], bi));
+    DD_TRY(fine_in<double>(h, z, nrhs, h->ws_io[0], xi));
+    h->coarse_iters = 0;
+    h->vcycles = 0;
+    h->coarse_seconds = 0;
+    KrylovResult R;
+    int rc = h->single() ? solve_T<float>(h, bi, xi, nrhs, tol, false, R) : solve_T<double>(h, bi, xi, nrhs, tol, false, R);
+    if (rc) return rc;
+    DD_TRY(fine_out<double>(h, xi, z, nrhs));
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int status = 0;
+    if (R.nonfinite) status = DDAMG_ERR_NONFINITE;
+    else {
+        for (int r = 0; r < nrhs; ++r)
+            if (!(R.resid[r] <= tol)) status = DDAMG_ERR_NOT_CONVERGED;
+    }
+    if (st) {
+        for (int r = 0; r < nrhs; ++r) {
+            st[r].iterations = (int)R.iters[r];
+            st[r].restarts = R.restarts;
+            st[r].coarse_iterations = h->coarse_iters;
+            st[r].vcycles = h->vcycles;
+            st[r].rel_residual = R.resid[r];
+            st[r].solve_seconds = secs;
+            st[r].coarse_seconds = h->coarse_seconds;
+            st[r].status = (R.nonfinite ? DDAMG_ERR_NONFINITE : (R.resid[r] <= tol ? 0 : DDAMG_ERR_NOT_CONVERGED));
+        }
+    }
+    if (status == DDAMG_ERR_NOT_CONVERGED) set_error("iteration cap reached before the tolerance");
+    if (status == DDAMG_ERR_NONFINITE) set_error("non-finite residual");
+    return status;
+}
+
+int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_stats* st) { return solve_common(h, b, z, 1, tol, st); }
+
+int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st) {
+    return solve_common(h, b, z, n_rhs, tol, st);
+}
+
+int ddamg_apply_D(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    if (!h || !in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<double>) * fld * n_rhs * 2));
+    cplx<double>* a = h->ws_fine[4].as<cplx<double>>();
+    cplx<double>* o = a + fld * n_rhs;
+    DD_TRY(fine_in<double>(h, in, n_rhs, h->ws_io[0], a));
+    DD_TRY((dslash<double, double>(h, a, nullptr, o, n_rhs)));
+    return fine_out<double>(h, o, out, n_rhs);
+}
+
+int ddamg_apply_D_f32(ddamg_handle* h, const float* in, float* out, int n_rhs) {
+    if (!h || !in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    if (!h->single()) {
+        set_error("ddamg_apply_D_f32 needs a handle in single or half precision");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<float>) * fld * n_rhs * 2));
+    cplx<float>* a = h->ws_fine[4].as<cplx<float>>();
+    cplx<float>* o = a + fld * n_rhs;
+    const void* dv;
+    DD_TRY(stage_in(h, h->ws_io[0], in, sizeof(cplx<float>) * fld * n_rhs, &dv));
+    DD_TRY((to_internal<float, float>(reinterpret_cast<const cplx<float>*>(dv), a, h->d_lex_of, h->V, 12, n_rhs, h->stream)));
+    DD_TRY((dslash<float, float>(h, a, nullptr, o, n_rhs)));
+    void* dout;
+    bool host;
+    DD_TRY(stage_out_ptr(h->ws_io[1], out, sizeof(cplx<float>) * fld * n_rhs, &dout, &host));
+    DD_TRY((from_internal<float, float>(o, reinterpret_cast<cplx<float>*>(dout), h->d_lex_of, h->V, 12, n_rhs, h->stream)));
+    return finish_out(h, out, dout, sizeof(cplx<float>) * fld * n_rhs, host);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int apply_sap_T(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu) {
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<T>) * fld * n_rhs * 2));
+    cplx<T>* a = h->ws_fine[4].as<cplx<T>>();
+    cplx<T>* o = a + fld * n_rhs;
+    DD_TRY(fine_in<T>(h, in, n_rhs, h->ws_io[0], a));
+    DD_CUDA(cudaMemsetAsync(o, 0, sizeof(cplx<T>) * fld * n_rhs, h->stream));
+    DD_TRY(sap<T>(h, a, o, n_rhs, nu));
+    return fine_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_apply_sap(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu) {
+    if (!h || !in || !out || n_rhs < 1 || nu < 0) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? apply_sap_T<float>(h, in, out, n_rhs, nu) : apply_sap_T<double>(h, in, out, n_rhs, nu);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int restrict_T(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    const size_t fld = (size_t)12 * h->V, cn = (size_t)h->NB * h->nc;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<T>) * (fld + cn) * n_rhs));
+    cplx<T>* a = h->ws_fine[4].as<cplx<T>>();
+    cplx<T>* o = a + fld * n_rhs;
+    DD_TRY(fine_in<T>(h, in, n_rhs, h->ws_io[0], a));
+    DD_TRY(restrict_<T>(h, a, o, n_rhs));
+    return coarse_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_restrict(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? restrict_T<float>(h, in, out, n_rhs) : restrict_T<double>(h, in, out, n_rhs);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int prolong_T(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    const size_t fld = (size_t)12 * h->V, cn = (size_t)h->NB * h->nc;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<T>) * (fld + cn) * n_rhs));
+    cplx<T>* a = h->ws_fine[4].as<cplx<T>>();
+    cplx<T>* o = a + cn * n_rhs;
+    DD_TRY(coarse_in<T>(h, in, n_rhs, a));
+    DD_TRY(prolong_<T>(h, a, o, n_rhs));
+    return fine_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_prolong(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? prolong_T<float>(h, in, out, n_rhs) : prolong_T<double>(h, in, out, n_rhs);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int apply_Dc_T(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    const size_t cn = (size_t)h->NB * h->nc;
+    DD_TRY(h->ws_fine[4].ensure(sizeof(cplx<T>) * cn * n_rhs * 2));
+    cplx<T>* a = h->ws_fine[4].as<cplx<T>>();
+    cplx<T>* o = a + cn * n_rhs;
+    DD_TRY(coarse_in<T>(h, in, n_rhs, a));
+    Level<T> L = level<T>(h);
+    {
+        Prof pr(h, PF_COARSE, (double)h->NB * 9 * h->nc * h->nc * sizeof(cplx<T>));
+        DD_TRY((launch_coarse_full<T, T>(L.cop, a, o, n_rhs, h->stream)));
+    }
+    return coarse_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? apply_Dc_T<float>(h, in, out, n_rhs) : apply_Dc_T<double>(h, in, out, n_rhs);
+}
+
+int ddamg_get_coarse_stencil(const ddamg_handle* hc, double* out) {
+    ddamg_handle* h = const_cast<ddamg_handle*>(hc);
+    DD_TRY(check_ready(h));
+    if (!out) return DDAMG_ERR_INVALID_ARG;
+    const int nc = h->nc;
+    const size_t per = (size_t)9 * nc * nc * 2;
+    std::vector<double> tmp(per * h->NB);
+    DD_CUDA(cudaMemcpyAsync(tmp.data(), h->B64, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, h->stream));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<double> res(per * h->NB);
+    for (int c = 0; c < h->NB; ++c) {
+        int cl = h->h_clex_of[c];
+        for (int d = 0; d < 9; ++d)
+            for (int col = 0; col < nc; ++col)
+                for (int row = 0; row < nc; ++row) {
+                    const double* s = &tmp[(((size_t)c * 9 + d) * nc + col) * nc * 2 + (size_t)row * 2];
+                    double* dd = &res[(((size_t)cl * 9 + d) * nc + row) * nc * 2 + (size_t)col * 2];
+                    dd[0] = s[0];
+                    dd[1] = s[1];
+                }
+    }
+    if (is_device_ptr(out)) {
+        DD_CUDA(cudaMemcpy(out, res.data(), sizeof(double) * res.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::memcpy(out, res.data(), sizeof(double) * res.size());
+    }
+    return 0;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int coarse_solve_T(ddamg_handle* h, const double* in, double* out, int n_rhs, int fixed) {
+    const size_t cn = (size_t)h->NB * h->nc;
+    DD_TRY(h->ws_fine[5].ensure(sizeof(cplx<T>) * cn * n_rhs * 2));
+    cplx<T>* a = h->ws_fine[5].as<cplx<T>>();
+    cplx<T>* o = a + cn * n_rhs;
+    DD_TRY(coarse_in<T>(h, in, n_rhs, a));
+    h->coarse_iters = 0;
+    DD_TRY(coarse_solve<T>(h, a, o, n_rhs, fixed));
+    return coarse_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_coarse_solve(ddamg_handle* h, const double* in, double* out, int n_rhs, int fixed_iters) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? coarse_solve_T<float>(h, in, out, n_rhs, fixed_iters) : coarse_solve_T<double>(h, in, out, n_rhs, fixed_iters);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int vcycle_T(ddamg_handle* h, const double* in, double* out, int n_rhs, int fixed) {
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[5].ensure(sizeof(cplx<T>) * fld * n_rhs * 2));
+    cplx<T>* a = h->ws_fine[5].as<cplx<T>>();
+    cplx<T>* o = a + fld * n_rhs;
+    DD_TRY(fine_in<T>(h, in, n_rhs, h->ws_io[0], a));
+    DD_TRY(vcycle<T>(h, a, o, n_rhs, fixed));
+    return fine_out<T>(h, o, out, n_rhs);
+}
+
+extern "C" {
+int ddamg_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, int coarse_fixed_iters) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    return h->single() ? vcycle_T<float>(h, in, out, n_rhs, coarse_fixed_iters) : vcycle_T<double>(h, in, out, n_rhs, coarse_fixed_iters);
+}
+
+int ddamg_set_mass(ddamg_handle* h, double m0) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    // site terms: rebuild with the new mass (the clover part does not depend on it)
+    h->m0 = m0;
+    DD_TRY(launch_clover(h->g, h->U64, m0, h->csw, h->clov64, h->clovinv64, h->stream));
+    if (h->single()) {
+        DD_TRY((convert<float, double>(h->clov64, h->clov32, (size_t)h->V * 72, h->stream)));
+        DD_TRY((convert<float, double>(h->clovinv64, h->clovinv32, (size_t)h->V * 72, h->stream)));
+    }
+    if (h->ready) DD_TRY(build_interpolation(h));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    return 0;
+}
+
+int ddamg_set_stream(ddamg_handle* h, void* s) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    h->stream = s ? reinterpret_cast<cudaStream_t>(s) : h->own_stream;
+    return 0;
+}
+
+int ddamg_info(const ddamg_handle* h, long long* n_sites, long long* n_coarse, int* dof) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    if (n_sites) *n_sites = h->V;
+    if (n_coarse) *n_coarse = h->NB;
+    if (dof) *dof = h->nc;
+    return 0;
+}
+
+int ddamg_profile_enable(ddamg_handle* h, int on) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    h->prof_on = on != 0;
+    return 0;
+}
+
+int ddamg_profile_reset(ddamg_handle* h) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto& r : h->prof) {
+        h->ev_pool.push_back(r.e0);
+        h->ev_pool.push_back(r.e1);
+    }
+    h->prof.clear();
+    return 0;
+}
+
+int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max) {
+    if (!h || (!out && max > 0)) return DDAMG_ERR_INVALID_ARG;
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    long long n[PF_COUNT] = {0};
+    double ms[PF_COUNT] = {0}, by[PF_COUNT] = {0};
+    for (auto& r : h->prof) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        n[r.fam]++;
+        ms[r.fam] += t;
+        by[r.fam] += r.bytes;
+    }
+    int k = 0;
+    for (int f = 0; f < PF_COUNT; ++f) {
+        if (!n[f]) continue;
+        if (k < max) {
+            std::memset(&out[k], 0, sizeof(out[k]));
+            std::strncpy(out[k].name, kPfNames[f], sizeof(out[k].name) - 1);
+            out[k].launches = n[f];
+            out[k].total_ms = ms[f];
+            out[k].bytes = by[f];
+        }
+        ++k;
+    }
+    return k;
+}
+
+int ddamg_destroy(ddamg_handle* h) {
+    if (!h) return 0;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    dfree(h->d_lnbr);
+    dfree(h->d_bnbr);
+    dfree(h->d_lex_of);
+    dfree(h->d_clex_of);
+    dfree(h->d_sites);
+    dfree(h->U64);
+    dfree(h->clov64);
+    dfree(h->clovinv64);
+    dfree(h->U32);
+    dfree(h->clov32);
+    dfree(h->clovinv32);
+    dfree(h->V64);
+    dfree(h->P64);
+    dfree(h->P32);
+    dfree(h->B64);
+    dfree(h->Dinv64);
+    dfree(h->B32);
+    dfree(h->Dinv32);
+    dfree(h->d_flag);
+    for (auto& s : h->ws_fine) s.release();
+    for (auto& s : h->ws_coarse) s.release();
+    for (auto& s : h->ws_io) s.release();
+    for (auto& s : h->ws_outer) s.release();
+    h->kc.release();
+    h->ko.release();
+    for (auto& r : h->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+"""Thin ctypes binding of libddamg.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts arrays to
+pointers and back.  Arrays may be numpy arrays (host memory: the library copies
+through its stream) or torch CUDA tensors (device memory: used in place).
+Layouts are those of include/ddamg.h: gauge [V,4,3,3] complex128, spinors
+[n_rhs, V, 4, 3] complex128 (complex64 for apply_D_f32), coarse vectors
+[n_rhs, n_coarse_sites, 2N] complex128; sites lexicographic, x0 slowest.
+
+Importing this module loads the library and raises if it is missing: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddamg.so")
+
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
+
+STATUS = {
+    0: "OK",
+    -1: "INVALID_ARG",
+    -2: "OOM",
+    -3: "CUDA",
+    -4: "NOT_CONVERGED",
+    -5: "NONFINITE",
+    -6: "TIMEOUT",
+    -7: "NOT_READY",
+    -8: "RANK",
+}
+
+
+class DDAMGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+        self.status = status
+
+
+class Lattice(C.Structure):
+    _fields_ = [("dims", C.c_int * 4)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_inv", C.c_int),
+        ("n_vec", C.c_int),
+        ("block", C.c_int * 4),
+        ("coarse_tol", C.c_double),
+        ("coarse_restart", C.c_int),
+        ("coarse_maxiter", C.c_int),
+        ("n_kv", C.c_int),
+        ("tol", C.c_double),
+        ("max_outer", C.c_int),
+        ("nu", C.c_int),
+        ("mr_steps", C.c_int),
+        ("precision", C.c_int),
+        ("rebuild_after_last", C.c_int),
+        ("seed", C.c_uint64),
+        ("time_limit_s", C.c_double),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int),
+        ("restarts", C.c_int),
+        ("coarse_iterations", C.c_longlong),
+        ("vcycles", C.c_int),
+        ("rel_residual", C.c_double),
+        ("solve_seconds", C.c_double),
+        ("coarse_seconds", C.c_double),
+        ("status", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelProfile(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1303_1377_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, LL = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "ddamg_default_params": (None, [C.POINTER(Params)]),
+        "ddamg_error_string": (C.c_char_p, [I]),
+        "ddamg_last_error": (C.c_char_p, []),
+        "ddamg_setup": (I, [C.POINTER(Lattice), P, D, D, C.POINTER(Params), C.POINTER(P)]),
+        "ddamg_create": (I, [C.POINTER(Lattice), P, D, D, C.POINTER(Params), C.POINTER(P)]),
+        "ddamg_run_setup": (I, [P, P]),
+        "ddamg_setup_from_vectors": (I, [P, P, I]),
+        "ddamg_get_vectors": (I, [P, P]),
+        "ddamg_solve": (I, [P, P, P, D, C.POINTER(Stats)]),
+        "ddamg_solve_batch": (I, [P, P, P, I, D, C.POINTER(Stats)]),
+        "ddamg_apply_D": (I, [P, P, P, I]),
+        "ddamg_apply_D_f32": (I, [P, P, P, I]),
+        "ddamg_apply_sap": (I, [P, P, P, I, I]),
+        "ddamg_restrict": (I, [P, P, P, I]),
+        "ddamg_prolong": (I, [P, P, P, I]),
+        "ddamg_apply_Dc": (I, [P, P, P, I]),
+        "ddamg_get_coarse_stencil": (I, [P, P]),
+        "ddamg_coarse_solve": (I, [P, P, P, I, I]),
+        "ddamg_vcycle": (I, [P, P, P, I, I]),
+        "ddamg_set_mass": (I, [P, D]),
+        "ddamg_set_stream": (I, [P, P]),
+        "ddamg_info": (I, [P, C.POINTER(LL), C.POINTER(LL), C.POINTER(I)]),
+        "ddamg_profile_enable": (I, [P, I]),
+        "ddamg_profile_read": (I, [P, C.POINTER(KernelProfile), I]),
+        "ddamg_profile_reset": (I, [P]),
+        "ddamg_launch_count": (LL, []),
+        "ddamg_debug_fail_allocs": (None, [I]),
+        "ddamg_destroy": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib.ddamg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "block":
+            for m in range(4):
+                p.block[m] = int(v[m])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc != 0 and rc not in allow:
+        raise DDAMGError(rc, where, lib.ddamg_last_error().decode(errors="replace"))
+    return rc
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _host(a, dtype):
+    if _is_torch(a):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _empty_like(a, shape, dtype):
+    if _is_torch(a):
+        import torch
+
+        tdt = {np.complex128: torch.complex128, np.complex64: torch.complex64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=a.device)
+    return np.empty(shape, dtype=dtype)
+
+
+class Solver:
+    """A DD-alpha-AMG operator D(U, m0, c_sw) with its two-level preconditioner."""
+
+    def __init__(self, dims, U, m0: float, c_sw: float, params: Params | None = None, setup: bool = True, v0=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.params = params if params is not None else default_params()
+        lat = Lattice((C.c_int * 4)(*self.dims))
+        U = _host(U, np.complex128)
+        h = C.c_void_p()
+        _check(lib.ddamg_create(C.byref(lat), _ptr(U), float(m0), float(c_sw), C.byref(self.params), C.byref(h)), "ddamg_create")
+        self.h = h
+        n, nc, dof = C.c_longlong(), C.c_longlong(), C.c_int()
+        lib.ddamg_info(self.h, C.byref(n), C.byref(nc), C.byref(dof))
+        self.V, self.n_coarse, self.coarse_dof = n.value, nc.value, dof.value
+        if setup:
+            self.run_setup(v0)
+
+    # -- lifecycle --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ddamg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- setup ------------------------------------------------------------------
+    def run_setup(self, v0=None):
+        p = C.c_void_p() if v0 is None else _ptr(_host(v0, np.complex128))
+        _check(lib.ddamg_run_setup(self.h, p), "ddamg_run_setup")
+
+    def setup_from_vectors(self, V):
+        V = _host(V, np.complex128)
+        _check(lib.ddamg_setup_from_vectors(self.h, _ptr(V), int(V.shape[0])), "ddamg_setup_from_vectors")
+
+    def vectors(self):
+        out = np.empty((self.params.n_vec, self.V, 4, 3), dtype=np.complex128)
+        _check(lib.ddamg_get_vectors(self.h, _ptr(out)), "ddamg_get_vectors")
+        return out
+
+    def set_mass(self, m0: float):
+        _check(lib.ddamg_set_mass(self.h, float(m0)), "ddamg_set_mass")
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(lib.ddamg_set_stream(self.h, C.c_void_p(stream_ptr or 0)), "ddamg_set_stream")
+
+    # -- solves -----------------------------------------------------------------
+    def solve(self, b, z=None, tol: float = 0.0, allow_fail: bool = False):
+        """Solve D z = b for a batch b[n_rhs, V, 4, 3] (or one field [V, 4, 3])."""
+        b = _host(b, np.complex128)
+        single = b.ndim == 3
+        nr = 1 if single else int(b.shape[0])
+        if z is None:
+            z = _empty_like(b, b.shape, np.complex128)
+            z[...] = 0
+        st = (Stats * nr)()
+        rc = lib.ddamg_solve_batch(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
+        _check(rc, "ddamg_solve_batch", allow=(-4, -5) if allow_fail else ())
+        return z, [s.as_dict() for s in st], rc
+
+    # -- operator pieces --------------------------------------------------------
+    def _fine_op(self, fn, x, *extra, dtype=np.complex128):
+        x = _host(x, dtype)
+        nr = 1 if x.ndim == 3 else int(x.shape[0])
+        out = _empty_like(x, x.shape, dtype)
+        _check(fn(self.h, _ptr(x), _ptr(out), nr, *extra), fn.__name__)
+        return out
+
+    def apply_D(self, x):
+        return self._fine_op(lib.ddamg_apply_D, x)
+
+    def apply_D_f32(self, x):
+        return self._fine_op(lib.ddamg_apply_D_f32, x, dtype=np.complex64)
+
+    def apply_sap(self, x, nu: int):
+        return self._fine_op(lib.ddamg_apply_sap, x, int(nu))
+
+    def vcycle(self, r, coarse_fixed_iters: int = 0):
+        return self._fine_op(lib.ddamg_vcycle, r, int(coarse_fixed_iters))
+
+    def restrict(self, x):
+        x = _host(x, np.complex128)
+        nr = 1 if x.ndim == 3 else int(x.shape[0])
+        out = _empty_like(x, (nr, self.n_coarse, self.coarse_dof), np.complex128)
+        _check(lib.ddamg_restrict(self.h, _ptr(x), _ptr(out), nr), "ddamg_restrict")
+        return out[0] if x.ndim == 3 else out
+
+    def prolong(self, e):
+        e = _host(e, np.complex128)
+        nr = 1 if e.ndim == 2 else int(e.shape[0])
+        out = _empty_like(e, (nr, self.V, 4, 3), np.complex128)
+        _check(lib.ddamg_prolong(self.h, _ptr(e), _ptr(out), nr), "ddamg_prolong")
+        return out[0] if e.ndim == 2 else out
+
+    def _coarse_op(self, fn, e, *extra):
+        e = _host(e, np.complex128)
+        nr = 1 if e.ndim == 2 else int(e.shape[0])
+        out = _empty_like(e, e.shape, np.complex128)
+        _check(fn(self.h, _ptr(e), _ptr(out), nr, *extra), fn.__name__)
+        return out
+
+    def apply_Dc(self, e):
+        return self._coarse_op(lib.ddamg_apply_Dc, e)
+
+    def coarse_solve(self, e, fixed_iters: int = 0):
+        return self._coarse_op(lib.ddamg_coarse_solve, e, int(fixed_iters))
+
+    def coarse_stencil(self):
+        out = np.empty((self.n_coarse, 9, self.coarse_dof, self.coarse_dof), dtype=np.complex128)
+        _check(lib.ddamg_get_coarse_stencil(self.h, _ptr(out)), "ddamg_get_coarse_stencil")
+        return out
+
+    # -- profiling ----------------------------------------------------------------
+    def profile(self, on: bool = True):
+        lib.ddamg_profile_enable(self.h, 1 if on else 0)
+
+    def profile_reset(self):
+        lib.ddamg_profile_reset(self.h)
+
+    def profile_read(self):
+        arr = (KernelProfile * 16)()
+        n = lib.ddamg_profile_read(self.h, arr, 16)
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes} for i in range(min(n, 16))}
+
+
+def launch_count() -> int:
+    return int(lib.ddamg_launch_count())
+
+
+def debug_fail_allocs(n: int):
+    lib.ddamg_debug_fail_allocs(int(n))

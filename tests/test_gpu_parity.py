@@ -1,0 +1,243 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 operator applications 1e-13 relative (max-norm over the field
+relative to the field's max), FP32 1e-6 for single applications (2e-6 allowed
+for the Dslash, whose 8 hops each round), looser where an FP32 quantity is
+iterated (stated per test); solves to a true FP64 relative residual <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle.aggregation import Aggregation  # noqa: E402
+from oracle.coarse import CoarseOperator, CoarseSolver  # noqa: E402
+from oracle.dirac import DiracOperator, apply_at_sites, gamma5_field  # noqa: E402
+from oracle.mg import Params as OParams  # noqa: E402
+from oracle.mg import TwoLevel  # noqa: E402
+from oracle.sap import SAP  # noqa: E402
+from paper_1303_1377_gb300 import synth  # noqa: E402
+
+CASES = {
+    # name: (dims, block, N, m0)
+    "4^4/2^4": ((4, 4, 4, 4), (2, 2, 2, 2), 4, 0.1),
+    "8^4/4^4": ((8, 8, 8, 8), (4, 4, 4, 4), 6, 0.05),
+    "4x4x4x12/2x2x2x6": ((4, 4, 4, 12), (2, 2, 2, 6), 3, 0.1),
+}
+CSW = 1.0
+
+
+def relerr(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def dd():
+    from paper_1303_1377_gb300 import ddamg
+
+    return ddamg
+
+
+class Case:
+    def __init__(self, name, dd):
+        dims, block, N, m0 = CASES[name]
+        self.dims, self.block, self.N, self.m0 = dims, block, N, m0
+        self.U = synth.gauge_field(dims, 0.5, seed=101)
+        self.D = DiracOperator(self.U, dims, m0, CSW)
+        self.v = synth.random_test_vectors(dims, N, seed=102)
+        self.dd = dd
+
+    def solver(self, prec, vectors=None):
+        p = self.dd.default_params(n_vec=self.N, block=self.block, precision=prec, nu=2)
+        s = self.dd.Solver(self.dims, self.U, self.m0, CSW, p, setup=False)
+        s.setup_from_vectors(self.v if vectors is None else vectors)
+        return s
+
+
+_cache = {}
+
+
+def case(name, dd):
+    if name not in _cache:
+        _cache[name] = Case(name, dd)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_dslash_fp64_fp32(name, dd):
+    c = case(name, dd)
+    x = synth.gaussian_spinors(c.dims, 3, seed=103)
+    ref = np.stack([c.D.apply(x[r]) for r in range(3)])
+    with c.solver(dd.PREC_SINGLE) as s:
+        assert relerr(s.apply_D(x), ref) < 1e-13
+        y32 = s.apply_D_f32(x.astype(np.complex64))
+        assert relerr(y32, ref) < 2e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nu", [1, 3])
+def test_sap(name, nu, dd):
+    c = case(name, dd)
+    sap = SAP(c.D, c.block, mr_steps=4)
+    b = synth.gaussian_spinors(c.dims, 2, seed=104)
+    ref = np.stack([sap.apply(b[r], nu) for r in range(2)])
+    with c.solver(dd.PREC_DOUBLE) as s:
+        assert relerr(s.apply_sap(b, nu), ref) < 1e-12
+    with c.solver(dd.PREC_SINGLE) as s:
+        assert relerr(s.apply_sap(b, nu), ref) < 2e-5  # FP32, iterated MR steps
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transfer_and_coarse_stencil(name, dd):
+    c = case(name, dd)
+    agg = Aggregation(c.D.lat, c.block, c.v)
+    Dc = CoarseOperator(c.D, agg)
+    x = synth.gaussian_spinors(c.dims, 2, seed=105)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 2, seed=106)
+    ref_r = np.stack([agg.restrict(x[r]) for r in range(2)])
+    ref_p = np.stack([agg.prolong(e[r]) for r in range(2)])
+    ref_c = np.stack([Dc.apply(e[r]) for r in range(2)])
+    with c.solver(dd.PREC_DOUBLE) as s:
+        B = s.coarse_stencil()
+        assert relerr(B, Dc.B) < 1e-12
+        assert relerr(s.restrict(x), ref_r) < 1e-13
+        assert relerr(s.prolong(e), ref_p) < 1e-13
+        assert relerr(s.apply_Dc(e), ref_c) < 1e-12
+    with c.solver(dd.PREC_SINGLE) as s:
+        assert relerr(s.restrict(x), ref_r) < 1e-6
+        assert relerr(s.prolong(e), ref_p) < 1e-6
+        assert relerr(s.apply_Dc(e), ref_c) < 1e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve_fixed_iterations(name, dd):
+    c = case(name, dd)
+    agg = Aggregation(c.D.lat, c.block, c.v)
+    cs = CoarseSolver(CoarseOperator(c.D, agg), restart=30, tol=5e-2)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 2, seed=107)
+    for k in (3, 12, 35):  # 35 crosses a restart
+        ref = np.stack([cs.solve(e[r], fixed_iters=k) for r in range(2)])
+        with c.solver(dd.PREC_DOUBLE) as s:
+            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-10
+        with c.solver(dd.PREC_SINGLE) as s:
+            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 2e-4  # FP32 Krylov recurrence
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_fixed_coarse_iterations(name, dd):
+    c = case(name, dd)
+    mg = TwoLevel(c.D, OParams(N=c.N, agg_block=c.block, sap_block=c.block, nu=2), vectors=c.v)
+    r = synth.gaussian_spinors(c.dims, 2, seed=108)
+    ref = np.stack([mg.vcycle(r[q], coarse_fixed_iters=10) for q in range(2)])
+    with c.solver(dd.PREC_DOUBLE) as s:
+        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-10
+    with c.solver(dd.PREC_SINGLE) as s:
+        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE"])
+def test_solve_matches_oracle(prec, dd):
+    """Oracle setup (Algorithm 2) -> same vectors on the GPU -> FGMRES solves agree."""
+    c = case("4^4/2^4", dd)
+    mg = TwoLevel(c.D, OParams(N=c.N, agg_block=c.block, sap_block=c.block, n_inv=2, nu=2))
+    vecs = mg.setup(c.v)
+    b = synth.gaussian_spinors(c.dims, 2, seed=109)
+    with c.solver(getattr(dd, "PREC_" + prec), vectors=vecs) as s:
+        z, st, rc = s.solve(b)
+    assert rc == 0
+    for q in range(2):
+        res = np.linalg.norm(b[q] - c.D.apply(z[q])) / np.linalg.norm(b[q])
+        assert res <= 1e-10
+        zo, info = mg.solve(b[q])
+        assert np.linalg.norm(z[q] - zo) <= 1e-8 * np.linalg.norm(zo)
+        assert st[q]["rel_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE"])
+def test_gpu_setup_solve_8x8x8x8(prec, dd):
+    """The 8^4 workload (aggregates 4^4, N = 20, nu = 3): GPU adaptive setup + solve;
+    the returned solution has FP64 relative residual <= 1e-10 under the oracle's D."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.4, seed=1)
+    m0 = 0.02
+    D = DiracOperator(U, dims, m0, CSW)
+    p = dd.default_params(nu=3, precision=getattr(dd, "PREC_" + prec))
+    b = synth.gaussian_spinors(dims, 1, seed=2)
+    with dd.Solver(dims, U, m0, CSW, p) as s:
+        z, st, rc = s.solve(b)
+    assert rc == 0
+    res = np.linalg.norm(b[0] - D.apply(z[0])) / np.linalg.norm(b[0])
+    assert res <= 1e-10, res
+
+
+def test_batch_equals_single_solves(dd):
+    """Each right-hand side gets the same answer alone and inside a batch."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 3, seed=110)
+    with c.solver(dd.PREC_SINGLE) as s:
+        zb, stb, rc = s.solve(b)
+        assert rc == 0
+        for q in range(3):
+            z1, st1, rc1 = s.solve(b[q:q + 1])
+            assert rc1 == 0
+            assert np.linalg.norm(z1[0] - zb[q]) <= 1e-8 * np.linalg.norm(z1[0])
+            assert abs(stb[q]["iterations"] - st1[0]["iterations"]) <= 1  # reductions are split differently
+
+
+def test_full_size_dslash_sampled(dd):
+    """32^3 x 64 (the benchmark lattice): GPU Dslash (FP64 and FP32) at 256 sampled sites
+    against the oracle evaluated site by site, and Gamma5-hermiticity over the whole lattice."""
+    dims = (64, 32, 32, 32)
+    U = synth.gauge_field(dims, 0.5, seed=3)
+    m0 = -0.1
+    p = dd.default_params(precision=dd.PREC_SINGLE)
+    x = synth.gaussian_spinors(dims, 2, seed=4)
+    with dd.Solver(dims, U, m0, CSW, p, setup=False) as s:
+        y = s.apply_D(x)
+        y32 = s.apply_D_f32(x[:1].astype(np.complex64))
+    sites = np.random.default_rng(5).choice(np.prod(dims), 256, replace=False)
+    sites = np.concatenate([sites, [0, np.prod(dims) - 1]])
+    ref = apply_at_sites(U, dims, m0, CSW, x[0], sites)
+    assert relerr(y[0][sites], ref) < 1e-13
+    assert relerr(y32[0][sites], ref) < 2e-6
+    a = np.vdot(x[0], gamma5_field(y[1]))
+    b = np.conj(np.vdot(x[1], gamma5_field(y[0])))
+    assert abs(a - b) < 1e-11 * abs(a)
+
+
+def test_error_statuses(dd):
+    c = case("4^4/2^4", dd)
+    p = dd.default_params(n_vec=c.N, block=c.block)
+    # not ready before setup
+    s = dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False)
+    with pytest.raises(dd.DDAMGError) as e:
+        s.solve(synth.gaussian_spinors(c.dims, 1, seed=1))
+    assert e.value.status == -7
+    s.setup_from_vectors(c.v)
+    # NaN in the right-hand side
+    b = synth.gaussian_spinors(c.dims, 1, seed=1)
+    b[0, 3, 1, 2] = np.nan
+    z, st, rc = s.solve(b, allow_fail=True)
+    assert rc == -5
+    s.close()
+    # iteration cap
+    p2 = dd.default_params(n_vec=c.N, block=c.block, max_outer=1)
+    with dd.Solver(c.dims, c.U, c.m0, CSW, p2, setup=False) as s2:
+        s2.setup_from_vectors(c.v)
+        z, st, rc = s2.solve(synth.gaussian_spinors(c.dims, 1, seed=1), allow_fail=True)
+        assert rc == -4 and st[0]["iterations"] == 1
+    # forced allocation failure
+    dd.debug_fail_allocs(1)
+    with pytest.raises(dd.DDAMGError) as e:
+        dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False)
+    assert e.value.status == -2
+    dd.debug_fail_allocs(0)
+    # rank-deficient test vectors
+    v = c.v.copy()
+    v[1] = v[0]
+    with dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False) as s3:
+        with pytest.raises(dd.DDAMGError) as e:
+            s3.setup_from_vectors(v)
+        assert e.value.status == -8

@@ -138,3 +138,16 @@ def test_mass_enters_diagonal_only():
     a = DiracOperator(U, dims, 0.1, 1.0).apply(psi)
     b = DiracOperator(U, dims, 0.35, 1.0).apply(psi)
     assert np.allclose(b - a, 0.25 * psi, atol=1e-13)
+
+
+def test_site_sampled_operator_equals_full_operator():
+    """The gather-based evaluation at chosen sites reproduces the full-field operator."""
+    from oracle.dirac import apply_at_sites
+
+    dims = (4, 2, 6, 4)
+    U = synth.gauge_field(dims, 0.5, seed=15)
+    psi = synth.gaussian_spinors(dims, 1, seed=16)[0]
+    D = DiracOperator(U, dims, -0.2, 1.1)
+    full = D.apply(psi)
+    sites = np.array([0, 5, 17, 63, 100, 191])
+    assert np.allclose(apply_at_sites(U, dims, -0.2, 1.1, psi, sites), full[sites], atol=1e-13)

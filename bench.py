@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: batched DD-alpha-AMG solves to relative residual 1e-10 on one GB300.
+
+One step = one call of ddamg_solve_batch on the 12 point sources (one per spin
+and colour) of the 32^3 x 64 workload: FGMRES(25) in FP64, one V-cycle per
+iteration (SAP 4^4 blocks, nu = 2, MR(4); 4^4 aggregates, N_v = 20; odd-even
+GMRES(30) coarse solve to 5e-2), V-cycle in FP32 (single) or FP32 with FP16
+coarse/interpolation storage (half).  The adaptive setup (Algorithm 2) runs
+before the timed region and is reported separately.
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) are independent
+replicas, one per GPU (weak scaling; the method needs no exchange between
+independent solves).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # the oracle baseline runs on one core
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # lattice (L0 = time first), gauge eps/seed, right-hand sides, method parameters
+    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, m0_key="lattice_32x32x32x64"),
+    "16x16x16x16": dict(dims=(16, 16, 16, 16), eps=0.5, seed=1, nrhs=12, rhs="point", N=20, nu=2, m0_key="lattice_16x16x16x16"),
+    "8x8x8x8": dict(dims=(8, 8, 8, 8), eps=0.4, seed=1, nrhs=1, rhs="gaussian", N=20, nu=3, m0_key="lattice_8x8x8x8"),
+}
+C_SW = 1.0
+WORKLOADS_JSON = os.path.join(ROOT, "paper_1303_1377_gb300", "workloads.json")
+
+
+def workload_m0(w):
+    data = json.load(open(WORKLOADS_JSON))
+    return float(data[w["m0_key"]]["m0"]), data[w["m0_key"]]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_rhs(w, V):
+    from paper_1303_1377_gb300 import synth
+
+    if w["rhs"] == "point":
+        b = np.zeros((12, V, 4, 3), dtype=np.complex128)
+        for k in range(12):
+            b[k, 0, k // 3, k % 3] = 1.0
+        return b[: w["nrhs"]]
+    return synth.gaussian_spinors(w["dims"], w["nrhs"], seed=w["seed"] + 1000)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample (the same workload on 8^4)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, m0, fgmres_iters_per_solve, seconds_budget=15.0):
+    """Time FGMRES iterations of the oracle on one point source of the workload's
+    8^4 counterpart (same eps, c_sw, m0, N_v, 4^4 blocks, nu; P from seeded random
+    test vectors) and scale: time/iteration * (V / 8^4) * iterations per solve."""
+    from oracle.dirac import DiracOperator
+    from oracle.krylov import fgmres
+    from oracle.mg import Params as OParams
+    from oracle.mg import TwoLevel
+    from paper_1303_1377_gb300 import synth
+
+    sdims = (8, 8, 8, 8)
+    U = synth.gauge_field(sdims, w["eps"], w["seed"])
+    D = DiracOperator(U, sdims, m0, C_SW)
+    mg = TwoLevel(D, OParams(N=w["N"], nu=w["nu"]), vectors=synth.random_test_vectors(sdims, w["N"], seed=w["seed"] + 7))
+    b = np.zeros((D.V, 4, 3), dtype=np.complex128)
+    b[0, 0, 0] = 1.0
+    t0 = time.perf_counter()
+    iters = 0
+    while True:
+        fgmres(D.apply, mg.vcycle, b, n_kv=25, tol=0.0, maxiter=1)
+        iters += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = (time.perf_counter() - t0) / iters
+    scale = np.prod(w["dims"]) / np.prod(sdims)
+    per_solve = dt * scale * fgmres_iters_per_solve
+    return 1.0 / per_solve, dict(sample=f"{iters} oracle FGMRES iterations (one point source) on the 8^4 version of the workload "
+                                        f"(same eps, c_sw, m0, N_v={w['N']}, 4^4 blocks, nu={w['nu']}; P from seeded random vectors), "
+                                        f"{dt:.2f} s/iteration x volume ratio {scale:.0f} x {fgmres_iters_per_solve} FGMRES iterations "
+                                        f"per solve", seconds=time.perf_counter() - t0)
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    m0, _ = workload_m0(w)
+    iters_per_solve = json.load(open(WORKLOADS_JSON)).get("fgmres_iterations_per_solve", {}).get(args.workload, 30)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, info = oracle_sample(w, m0, iters_per_solve, seconds_budget=8.0)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)", "value": value,
+        "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w["nrhs"] / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} lattice, eps={w['eps']}, c_sw={C_SW}, m0={m0:.6f}, {w['nrhs']} {w['rhs']} sources, "
+                               f"N_v={w['N']}, 4^4 blocks, nu={w['nu']}", "l2": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32x32x32x64", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="single", choices=["single", "half", "double"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+
+    from paper_1303_1377_gb300 import ddamg, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    m0, _ = workload_m0(w)
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    t = time.perf_counter()
+    U = synth.gauge_field(dims, w["eps"], w["seed"])
+    t_gauge = time.perf_counter() - t
+    prec = {"single": ddamg.PREC_SINGLE, "half": ddamg.PREC_HALF, "double": ddamg.PREC_DOUBLE}[args.precision]
+    params = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=prec)
+    t = time.perf_counter()
+    solver = ddamg.Solver(dims, U, m0, C_SW, params, setup=True)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t
+    del U
+    stream = torch.cuda.Stream()
+    solver.set_stream(stream.cuda_stream)
+    bh = make_rhs(w, V)
+    nr = bh.shape[0]
+    b = torch.from_numpy(bh).to("cuda")
+    z = torch.zeros_like(b)
+
+    def step():
+        with torch.cuda.stream(stream):
+            z.zero_()
+        zz, st, rc = solver.solve(b, z)
+        if rc != 0:
+            raise RuntimeError(f"solve status {rc}")
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    # identify the dominant kernel family on one profiled step
+    solver.profile()
+    solver.profile_reset()
+    step()
+    prof_all = solver.profile_read()
+    dominant = max(prof_all, key=lambda k: prof_all[k]["total_ms"])
+    solver.profile([dominant])
+    solver.profile_reset()
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    n_launch0 = ddamg.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ddamg.launch_count() - n_launch0
+    clk = clocks.stop()
+    prof = solver.profile_read()
+    solver.profile([])
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * nr * args.steps / (ms / 1e3)
+    # residual check of the last solve, in FP64 through the library's D
+    r = b - solver.apply_D(z)
+    rel = (torch.linalg.vector_norm(r.reshape(nr, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nr, -1), dim=1)).max().item()
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        bhost = torch.from_numpy(bh).pin_memory()
+        zhost = torch.zeros_like(bhost).pin_memory()
+        solver.set_stream(None)
+        solver.solve(bhost.numpy(), zhost.numpy())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            zhost.zero_()
+            solver.solve(bhost.numpy(), zhost.numpy())
+        e2e_s = time.perf_counter() - t0
+        nbytes = bh.nbytes
+        e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
+               "d2h_bytes_per_step": nbytes}
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    d = prof.get(dominant, {"launches": 0, "total_ms": 0.0, "bytes": 0.0})
+    achieved = (d["bytes"] / d["launches"]) / (d["total_ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else 0.0
+    traffic = None
+    tr = json.load(open(WORKLOADS_JSON)).get("ncu_traffic", {}).get(f"{args.workload}/{args.precision}/{dominant}")
+    if tr:
+        traffic = tr
+    roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "launches": d["launches"], "avg_launch_us": 1e3 * d["total_ms"] / max(1, d["launches"]),
+            "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+            "time_share_of_step": d["total_ms"] / ms if ms else None}
+    iters = [s["iterations"] for s in stats[-1]]
+    line = {
+        "metric": "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)" if args.workload == "32x32x32x64" else f"solves/s to rel. residual 1e-10 ({args.workload})",
+        "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": f"{args.workload} lattice (L0={dims[0]}), SU(3) links exp(i eps H) eps={w['eps']} seed={w['seed']}, c_sw={C_SW}, "
+                               f"m0={m0:.6f}, {nr} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
+                               f"MR(4), FGMRES(25) tol 1e-10, coarse GMRES(30) tol 5e-2, V-cycle {args.precision}",
+                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "fgmres_iterations": iters,
+        "coarse_iterations_per_solve": stats[-1][0]["coarse_iterations"],
+        "max_rel_residual": rel,
+        "setup_seconds": t_setup,
+        "gauge_generation_seconds": t_gauge,
+        "kernel_profile_first_step": prof_all,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, info = oracle_sample(w, m0, max(iters), seconds_budget=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": info["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

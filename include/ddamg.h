@@ -145,6 +145,12 @@ int ddamg_apply_D(ddamg_handle* h, const double* in, double* out, int n_rhs);
 /* out = D in in FP32 arithmetic on FP32 fields ([site][spin][colour] complex float). */
 int ddamg_apply_D_f32(ddamg_handle* h, const float* in, float* out, int n_rhs);
 
+/* out = D in for an FP32 field in ([site][spin][colour] complex float) with an
+ * FP64 result accurate to ~1e-14 relative: the operator is applied in
+ * double-word FP32 arithmetic (how FGMRES multiplies D with the FP32 V-cycle
+ * output).  Needs a single- or half-precision handle. */
+int ddamg_apply_D_mixed(ddamg_handle* h, const float* in, double* out, int n_rhs);
+
 /* out = M_SAP^(nu) in (Sec. 2.3) in the V-cycle precision; FP64 fields in/out. */
 int ddamg_apply_sap(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);
 
@@ -182,16 +188,20 @@ int ddamg_set_stream(ddamg_handle* h, void* cuda_stream);
 int ddamg_info(const ddamg_handle* h, long long* n_sites, long long* n_coarse_sites, int* coarse_dof);
 
 /* Per-kernel timing with CUDA events on the handle's stream (benchmarks).
- * ddamg_profile_enable(h, 1) starts recording, 0 stops;  ddamg_profile_read
- * fills up to max entries (name, launches, total milliseconds, algorithmic
- * bytes) and returns the number of kernel families recorded. */
+ * ddamg_profile_enable(h, mask) records the kernel families whose bit is set
+ * in mask (bit order as listed by ddamg_profile_families; -1 = all, 0 = off);
+ * ddamg_profile_read fills up to max entries (name, launches, total
+ * milliseconds, algorithmic bytes moved) and returns the number of families
+ * recorded.  ddamg_profile_families writes the comma-separated family names
+ * into names (len bytes) and returns their number. */
 typedef struct {
     char name[48];
     long long launches;
     double total_ms;
     double bytes;
 } ddamg_kernel_profile;
-int ddamg_profile_enable(ddamg_handle* h, int on);
+int ddamg_profile_enable(ddamg_handle* h, int family_mask);
+int ddamg_profile_families(char* names, int len);
 int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max);
 int ddamg_profile_reset(ddamg_handle* h);
 

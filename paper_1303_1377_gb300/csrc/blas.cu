@@ -4,6 +4,7 @@
 // permutations between the ABI's lexicographic layout and the internal order.
 #include "kernels.h"
 #include "blas.h"
+#include "dw.cuh"
 
 namespace ddamg {
 
@@ -318,6 +319,156 @@ int arnoldi_update(const KrylovState& s, int k, const cplx<double>* hcol, cplx<d
 }
 int arnoldi_solve(const KrylovState& s, cplx<double>* y, cudaStream_t st) {
     arnoldi_solve_kernel<<<ceil_div(s.nrhs, 64), 64, 0, st>>>(s, y);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// double-word basis vectors (cplx<dwf>, one float4 per complex number)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ cdw ld4(const cplx<dwf>* p) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void st4(cplx<dwf>* p, const cdw& a) {
+    dw re = dw_norm(a.re), im = dw_norm(a.im);
+    *reinterpret_cast<float4*>(p) = make_float4(re.h, re.l, im.h, im.l);
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kDotThreads) multidot_dw_kernel(const cplx<dwf>* __restrict__ A, size_t istride, size_t arstride, int k,
+                                                                  const cplx<dwf>* __restrict__ w, size_t wrstride, size_t n, int nrhs,
+                                                                  int ctas_per_rhs, double* __restrict__ partial) {
+    const int r = blockIdx.x % nrhs;
+    const int part = blockIdx.x / nrhs;
+    const cplx<dwf>* Ar = A + r * arstride;
+    const cplx<dwf>* wr = w + r * wrstride;
+    cdw acc[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = cdw_zero();
+    const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
+    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n; e += stride) {
+        cdw wv = ld4(wr + e);
+#pragma unroll
+        for (int i = 0; i < KB; ++i)
+            if (i < k) cdw_mac_conj(acc[i], ld4(Ar + i * istride + e), wv);
+    }
+    __shared__ double red[kDotThreads / 32][2 * KB];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+        if (i < k) {
+            double vr = warp_sum(dw_to_double(acc[i].re));
+            double vi = warp_sum(dw_to_double(acc[i].im));
+            if (lane == 0) {
+                red[wi][2 * i] = vr;
+                red[wi][2 * i + 1] = vi;
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) {
+        double s = 0;
+        for (int ww = 0; ww < kDotThreads / 32; ++ww) s += red[ww][q];
+        partial[((size_t)blockIdx.x) * 2 * k + q] = s;
+    }
+}
+
+template <>
+int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n,
+                       int nrhs, cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st) {
+    int off = 0;
+    while (off < k) {
+        int kk = k - off;
+        if (kk > 16) kk = 16;
+        int ctas = (int)((n + kDotThreads - 1) / kDotThreads);
+        int target = 1216 / nrhs;
+        if (target < 1) target = 1;
+        if (ctas > target) ctas = target;
+        const cplx<dwf>* Ab = A + off * istride;
+        if (kk <= 1)
+            multidot_dw_kernel<1><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else if (kk <= 4)
+            multidot_dw_kernel<4><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else if (kk <= 8)
+            multidot_dw_kernel<8><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        else
+            multidot_dw_kernel<16><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+        DD_CHECK_LAUNCH();
+        multidot_finish<<<ceil_div((long long)nrhs * kk, 128), 128, 0, st>>>(scratch, kk, nrhs, ctas, out + (size_t)off * ostride_i,
+                                                                          ostride_i);
+        DD_CHECK_LAUNCH();
+        off += kk;
+    }
+    return 0;
+}
+
+// coefficients alpha * coef[i][r] (FP64 complex) -> double-word pairs
+__global__ void coef_to_dw_kernel(const cplx<double>* __restrict__ coef, int cstride_i, int k, int nrhs, double alpha,
+                                  float4* __restrict__ out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k * nrhs) return;
+    int i = q / nrhs, r = q % nrhs;
+    cplx<double> c = coef[(size_t)i * cstride_i + r];
+    dw re = dw_from_double(alpha * c.re), im = dw_from_double(alpha * c.im);
+    out[q] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+// out[r] = beta * out[r] + sum_i cdw[i][r] * A_i[r]  (beta 0 or 1), double-word arithmetic
+template <int KB>
+__global__ void lincomb_dw_kernel(cplx<dwf>* __restrict__ out, size_t ors, int beta1, const cplx<dwf>* __restrict__ A, size_t istride,
+                                  size_t ars, int k, const float4* __restrict__ cdwv, size_t n, int nrhs) {
+    const size_t tot = n * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(q / n);
+        size_t e = q % n;
+        cdw acc = beta1 ? ld4(out + r * ors + e) : cdw_zero();
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            float4 c = __ldg(cdwv + (size_t)i * nrhs + r);
+            cdw cc = {{c.x, c.y}, {c.z, c.w}};
+            cdw_mac(acc, cc, ld4(A + i * istride + r * ars + e));
+        }
+        st4(out + r * ors + e, acc);
+    }
+}
+
+int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
+               int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st) {
+    coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch);
+    DD_CHECK_LAUNCH();
+    long long tot = (long long)n * nrhs;
+    int blocks = ceil_div(tot, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    lincomb_dw_kernel<1><<<blocks, 256, 0, st>>>(out, ors, beta1, A, istride, ars, k, coef_scratch, n, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// FP64 <-> double-word vectors and double-word -> FP32 (the V-cycle input)
+__global__ void d2dw_kernel(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        dw v = dw_from_double(in[q]);
+        out[q] = make_float2(v.h, v.l);
+    }
+}
+__global__ void dw2f_kernel(const float2* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        float2 v = in[q];
+        out[q] = v.x + v.y;
+    }
+}
+int convert_d2dw(const double* in, cplx<dwf>* out, size_t nreal, cudaStream_t st) {
+    int blocks = ceil_div((long long)nreal, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    d2dw_kernel<<<blocks, 256, 0, st>>>(in, reinterpret_cast<float2*>(out), nreal);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+int convert_dw2f(const cplx<dwf>* in, float* out, size_t nreal, cudaStream_t st) {
+    int blocks = ceil_div((long long)nreal, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    dw2f_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float2*>(in), out, nreal);
     DD_CHECK_LAUNCH();
     return 0;
 }

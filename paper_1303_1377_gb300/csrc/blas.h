@@ -28,6 +28,14 @@ template <typename To, typename Ta>
 int lincomb(cplx<To>* out, size_t ors, double beta, const cplx<Ta>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
             int cstride_i, size_t n, int nrhs, const int* mask, cudaStream_t st, double alpha = 1.0);
 int add_columns(cplx<double>* a, const cplx<double>* b, int n, cudaStream_t st);
+// double-word vectors
+template <>
+int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n,
+                       int nrhs, cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st);
+int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
+               int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st);
+int convert_d2dw(const double* in, cplx<dwf>* out, size_t nreal, cudaStream_t st);
+int convert_dw2f(const cplx<dwf>* in, float* out, size_t nreal, cudaStream_t st);
 template <typename To, typename Ti>
 int convert(const Ti* in, To* out, size_t n, cudaStream_t st);
 template <typename To, typename Ti>

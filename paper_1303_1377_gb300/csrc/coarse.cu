@@ -18,92 +18,139 @@ struct CVec {
     int site0;       // coarse site stored at p[0]
 };
 
-// One CTA per coarse site c = site_begin + blockIdx.x, one thread per row.
-//   acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)]
-//   self = 0 (self_mode 0), B_0(c) xself[c] (1) or xself[c] (2)
-//   out[c] = apply_inv ? Dinv(c) acc : acc
+// pairs of consecutive complex matrix entries (rows 2p, 2p+1 of one column)
+__device__ __forceinline__ void load_pair(const float* p, cplx<float>& a, cplx<float>& b) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    a = mk(v.x, v.y);
+    b = mk(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double* p, cplx<double>& a, cplx<double>& b) {
+    double2 v0 = __ldg(reinterpret_cast<const double2*>(p));
+    double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    a = mk(v0.x, v0.y);
+    b = mk(v1.x, v1.y);
+}
+
+// acc[2][NRP] += sum over columns q in [q0, q1) of M(q)[2p..2p+1] * xs[q][0..NRP);
+// column q of the stacked matrices starts at first + q * nc complex entries (slots are
+// contiguous nc x nc column-major blocks).
 template <typename T, typename S, int NRP>
-__global__ void coarse_stencil_kernel(CoarseOp<S> op, int site_begin, CVec<T> xin, CVec<T> xself, int self_mode, T hop_sign,
-                                      int apply_inv, CVec<T> out, int nrhs) {
+__device__ __forceinline__ void gemm_slice(const S* first, int nc, int p, int q0, int q1, const cplx<T>* xs,
+                                           cplx<T> (&acc)[2][NRP]) {
+    const S* bp = first + 2 * ((size_t)q0 * nc + 2 * p);
+    const cplx<T>* xq = xs + (size_t)q0 * NRP;
+#pragma unroll 2
+    for (int q = q0; q < q1; ++q, bp += 2 * nc, xq += NRP) {
+        cplx<T> b0, b1;
+        load_pair(bp, b0, b1);
+#pragma unroll
+        for (int r = 0; r < NRP; ++r) {
+            cplx<T> xv = xq[r];
+            cmac(acc[0][r], b0, xv);
+            cmac(acc[1][r], b1, xv);
+        }
+    }
+}
+
+// One CTA per coarse site c = site_begin + blockIdx.x.  Thread (p, g): rows 2p, 2p+1,
+// k-group g of the 8 or 9 (direction, column) slices; partial sums are reduced in
+// shared memory.  acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)] with
+//   self = 0 (self_mode 0), B_0(c) xself[c] (1) or xself[c] (2);  out = apply_inv ? Dinv acc : acc.
+template <typename T, typename S, int NRP>
+__global__ void __launch_bounds__(128) coarse_stencil_kernel(CoarseOp<S> op, int site_begin, CVec<T> xin, CVec<T> xself,
+                                                             int self_mode, T hop_sign, int apply_inv, CVec<T> out, int nrhs) {
     extern __shared__ unsigned char smem_raw[];
-    const int nc = op.nc;
-    cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);  // [9][nc][NRP]
+    const int nc = op.nc, RP = nc / 2;
+    const int KG = blockDim.x / RP;
+    cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);  // [slots][nc][NRP], later reused for partial sums
     const int c = site_begin + blockIdx.x;
-    const int row = threadIdx.x;
     const bool use_hops = hop_sign != T(0);
-    // stage neighbour vectors (and the self vector) in shared memory
-    for (int q = threadIdx.x; q < 9 * nc * NRP; q += blockDim.x) {
-        int r = q % NRP, col = (q / NRP) % nc, d = q / (NRP * nc);
+    const int slot0 = (self_mode == 1) ? 0 : 1;      // slot 0 = B_0 x_self
+    const int nslots = use_hops ? 9 - slot0 : 1 - slot0;
+    const S* first = op.B + ((size_t)(c * 9 + slot0) * nc) * nc * 2;
+    // stage the vectors: slot sl holds direction d = slot0 + sl
+    for (int q = threadIdx.x; q < nslots * nc * NRP; q += blockDim.x) {
+        int r = q % NRP, col = (q / NRP) % nc, d = slot0 + q / (NRP * nc);
         cplx<T> v = czero<T>();
         if (r < nrhs) {
             if (d == 0) {
-                if (self_mode) v = xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + col];
-            } else if (use_hops) {
+                v = xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + col];
+            } else {
                 int n = __ldg(op.cnbr + (d - 1) * op.NB + c);
-                v = xin.p[r * xin.rstride + (size_t)(n - xin.site0) * nc + col];
+                v = hop_sign * xin.p[r * xin.rstride + (size_t)(n - xin.site0) * nc + col];
             }
         }
         xs[q] = v;
     }
     __syncthreads();
-    cplx<T> acc[NRP];
+    const int p = threadIdx.x % RP, g = threadIdx.x / RP;
+    const bool act = g < KG;
+    cplx<T> acc[2][NRP];
 #pragma unroll
-    for (int r = 0; r < NRP; ++r) acc[r] = czero<T>();
-    if (row < nc) {
-        if (use_hops) {
-            for (int d = 1; d < 9; ++d) {
-                const S* Bd = op.B + ((size_t)(c * 9 + d) * nc) * nc * 2;
-                const cplx<T>* xd = xs + (size_t)d * nc * NRP;
-                for (int col = 0; col < nc; ++col) {
-                    cplx<T> b = mk<T>(T(Bd[2 * ((size_t)col * nc + row)]), T(Bd[2 * ((size_t)col * nc + row) + 1]));
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int r = 0; r < NRP; ++r) cmac(acc[r], b, xd[col * NRP + r]);
-                }
-            }
+        for (int r = 0; r < NRP; ++r) acc[h][r] = czero<T>();
+    const int Kt = nslots * nc;
+    if (act && nslots > 0) gemm_slice<T, S, NRP>(first, nc, p, (g * Kt) / KG, ((g + 1) * Kt) / KG, xs, acc);
+    __syncthreads();
+    // reduce the KG partial sums: red[g][row][r]
+    cplx<T>* red = xs;
+    if (act)
 #pragma unroll
-            for (int r = 0; r < NRP; ++r) acc[r] = hop_sign * acc[r];
+        for (int r = 0; r < NRP; ++r) {
+            red[((size_t)g * nc + 2 * p) * NRP + r] = acc[0][r];
+            red[((size_t)g * nc + 2 * p + 1) * NRP + r] = acc[1][r];
         }
-        if (self_mode == 1) {
-            const S* B0 = op.B + ((size_t)(c * 9) * nc) * nc * 2;
-            for (int col = 0; col < nc; ++col) {
-                cplx<T> b = mk<T>(T(B0[2 * ((size_t)col * nc + row)]), T(B0[2 * ((size_t)col * nc + row) + 1]));
-#pragma unroll
-                for (int r = 0; r < NRP; ++r) cmac(acc[r], b, xs[col * NRP + r]);
-            }
-        } else if (self_mode == 2) {
-#pragma unroll
-            for (int r = 0; r < NRP; ++r) acc[r] = acc[r] + xs[row * NRP + r];
+    __syncthreads();
+    cplx<T>* vsum = red + (size_t)KG * nc * NRP;  // [nc][NRP]
+    for (int o = threadIdx.x; o < nc * NRP; o += blockDim.x) {
+        cplx<T> s = czero<T>();
+        for (int gg = 0; gg < KG; ++gg) s = s + red[(size_t)gg * nc * NRP + o];
+        if (self_mode == 2) {
+            int row = o / NRP, r = o % NRP;
+            if (r < nrhs) s = s + xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + row];
         }
+        vsum[o] = s;
     }
+    __syncthreads();
     if (apply_inv) {
+        const S* dfirst = op.Dinv + ((size_t)c * nc) * nc * 2;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int r = 0; r < NRP; ++r) acc[h][r] = czero<T>();
+        if (act) gemm_slice<T, S, NRP>(dfirst, nc, p, (g * nc) / KG, ((g + 1) * nc) / KG, vsum, acc);
         __syncthreads();
-        if (row < nc)
+        if (act)
 #pragma unroll
-            for (int r = 0; r < NRP; ++r) xs[row * NRP + r] = acc[r];
-        __syncthreads();
-        if (row < nc) {
-#pragma unroll
-            for (int r = 0; r < NRP; ++r) acc[r] = czero<T>();
-            const S* Di = op.Dinv + ((size_t)c * nc) * nc * 2;
-            for (int col = 0; col < nc; ++col) {
-                cplx<T> b = mk<T>(T(Di[2 * ((size_t)col * nc + row)]), T(Di[2 * ((size_t)col * nc + row) + 1]));
-#pragma unroll
-                for (int r = 0; r < NRP; ++r) cmac(acc[r], b, xs[col * NRP + r]);
+            for (int r = 0; r < NRP; ++r) {
+                red[((size_t)g * nc + 2 * p) * NRP + r] = acc[0][r];
+                red[((size_t)g * nc + 2 * p + 1) * NRP + r] = acc[1][r];
             }
+        __syncthreads();
+        for (int o = threadIdx.x; o < nc * NRP; o += blockDim.x) {
+            cplx<T> s = czero<T>();
+            for (int gg = 0; gg < KG; ++gg) s = s + red[(size_t)gg * nc * NRP + o];
+            vsum[o] = s;
         }
+        __syncthreads();
     }
-    if (row < nc) {
-#pragma unroll
-        for (int r = 0; r < NRP; ++r)
-            if (r < nrhs) out.p[r * out.rstride + (size_t)(c - out.site0) * nc + row] = acc[r];
+    for (int o = threadIdx.x; o < nc * NRP; o += blockDim.x) {
+        int row = o / NRP, r = o % NRP;
+        if (r < nrhs) out.p[r * out.rstride + (size_t)(c - out.site0) * nc + row] = vsum[o];
     }
 }
 
 template <typename T, typename S, int NRP>
 static int launch_stencil_nrp(const CoarseOp<S>& op, int site_begin, int nsites, CVec<T> xin, CVec<T> xself, int self_mode,
                               T hop_sign, int apply_inv, CVec<T> out, int nrhs, cudaStream_t st) {
-    const int nt = ((op.nc + 31) / 32) * 32;
-    size_t smem = (size_t)9 * op.nc * NRP * sizeof(cplx<T>);
+    const int RP = op.nc / 2;
+    int KG = 128 / RP;
+    if (KG < 1) KG = 1;
+    const int nt = KG * RP;
+    size_t stage = (size_t)9 * op.nc * NRP * sizeof(cplx<T>);
+    size_t reduce = (size_t)(KG + 1) * op.nc * NRP * sizeof(cplx<T>);
+    size_t smem = stage > reduce ? stage : reduce;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(coarse_stencil_kernel<T, S, NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -17,6 +17,11 @@ struct alignas(2 * sizeof(T)) cplx {
     T re, im;
 };
 
+// double-word FP32 number h + l used as a storage type (FP64-like precision at FP32 speed)
+struct dwf {
+    float h, l;
+};
+
 template <typename T>
 __host__ __device__ __forceinline__ cplx<T> mk(T r, T i) {
     cplx<T> z;

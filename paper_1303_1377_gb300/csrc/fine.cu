@@ -9,6 +9,7 @@
 //                                 each 6 real diagonal entries + 15 complex upper entries
 #include "kernels.h"
 #include "dirac.cuh"
+#include "dw.cuh"
 
 namespace ddamg {
 
@@ -162,9 +163,9 @@ __device__ __forceinline__ void block_reduce3(T& a, T& b, T& c, T* red) {
     }
 }
 
-template <typename T>
-__global__ void sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc, cplx<T>* __restrict__ z, int colour,
-                                  int nrhs, int mr_steps) {
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB) sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
+                                                               cplx<T>* __restrict__ z, int colour, int nrhs, int mr_steps) {
     extern __shared__ unsigned char smem_raw[];
     const int H = g.Vb / 2;
     cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw);  // [12][H] even-site work vector
@@ -267,21 +268,27 @@ __global__ void sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restric
     }
 }
 
-template <typename T>
-int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
-                      cudaStream_t st) {
+template <typename T, int MINB>
+static int launch_sap_plain(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                            cudaStream_t st) {
     const int H = g.Vb / 2;
     const int nt = ((H + 31) / 32) * 32;
     size_t smem = 3 * 12 * (size_t)H * sizeof(cplx<T>) + 3 * 32 * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(sap_colour_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(sap_colour_kernel<T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     long long nblk = (long long)(g.NB / 2) * nrhs;
-    sap_colour_kernel<T><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    sap_colour_kernel<T, MINB><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
     DD_CHECK_LAUNCH();
     return 0;
+}
+
+template <typename T>
+int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                      cudaStream_t st) {
+    return launch_sap_plain<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
 }
 template int launch_sap_colour<double>(const Geom&, const FineOp<double>&, const cplx<double>*, cplx<double>*, int, int, int,
                                        cudaStream_t);
@@ -429,6 +436,184 @@ int upload_gamma_products(const double* gg) {
 
 int launch_clover(const Geom& g, const cplx<double>* U, double m0, double csw, double* clov, double* clovinv, cudaStream_t st) {
     clover_kernel<<<ceil_div(g.V, 64), 64, 0, st>>>(g, U, m0, csw, clov, clovinv);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// D z for an FP32 field z with an FP64-accurate result, evaluated in double-word
+// FP32 arithmetic (pairs hi + lo of floats; error-free transformations TwoSum
+// (Knuth) and TwoProduct via FMA, as in Joldes, Muller, Popescu, "Tight and
+// rigorous error bounds for basic building blocks of double-word arithmetic",
+// ACM TOMS 2017).  Used for w = D z_k inside FGMRES, where z_k is the V-cycle
+// output and hence exactly an FP32 vector.  On GB300 an FP64 instruction costs
+// about sixty FP32 instructions, and the double-word form needs about twelve per
+// real multiply-add, with relative accuracy ~1e-14.
+// Links and site terms are stored as double-word pairs (same bytes as FP64).
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ cdw ld_cdw(const float4* p) {
+    float4 v = __ldg(p);
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void dw_hop(cdw (&acc)[12], const cplx<float>* __restrict__ in, int V, int nb, const float4* __restrict__ U,
+                                       int link_site) {
+    using B = SpinB<MU>;
+    cdw psi[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        cplx<float> v = in[(size_t)k * V + nb];
+        psi[k] = {{v.re, 0.f}, {v.im, 0.f}};
+    }
+    cdw h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cdw b0 = cdw_ipow<B::p0>(psi[(2 + B::c0) * 3 + c]);
+        cdw b1 = cdw_ipow<B::p1>(psi[(2 + B::c1) * 3 + c]);
+        h[0][c] = FWD ? cdw_sub(psi[0 * 3 + c], b0) : cdw_add(psi[0 * 3 + c], b0);
+        h[1][c] = FWD ? cdw_sub(psi[1 * 3 + c], b1) : cdw_add(psi[1 * 3 + c], b1);
+    }
+    cdw W[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) W[q] = ld_cdw(U + (size_t)(MU * 9 + q) * V + link_site);
+    cdw gv[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cdw t = cdw_zero();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (FWD) cdw_mac(t, W[a * 3 + b], h[s][b]);
+                else cdw_mac_conj(t, W[b * 3 + a], h[s][b]);
+            }
+            t.re = dw_norm(t.re);
+            t.im = dw_norm(t.im);
+            gv[s][a] = t;
+            acc[s * 3 + a] = cdw_add(acc[s * 3 + a], t);
+        }
+    }
+    // lower spins: -s B^H g  (forward: -B^H g, backward: +B^H g)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cdw l0 = cdw_ipow<B::hp0>(gv[B::hc0][c]);
+        cdw l1 = cdw_ipow<B::hp1>(gv[B::hc1][c]);
+        acc[2 * 3 + c] = FWD ? cdw_sub(acc[2 * 3 + c], l0) : cdw_add(acc[2 * 3 + c], l0);
+        acc[3 * 3 + c] = FWD ? cdw_sub(acc[3 * 3 + c], l1) : cdw_add(acc[3 * 3 + c], l1);
+    }
+}
+
+template <int MU>
+__device__ __forceinline__ void dw_hop_pair(const Geom& g, cdw (&acc)[12], const cplx<float>* __restrict__ in, const float4* __restrict__ U,
+                                            int i) {
+    dw_hop<MU, true>(acc, in, g.V, fine_nbr(g, i, 2 * MU), U, i);
+    int bk = fine_nbr(g, i, 2 * MU + 1);
+    dw_hop<MU, false>(acc, in, g.V, bk, U, bk);
+}
+
+}  // namespace
+
+template <bool OUT_DW>
+__global__ void __launch_bounds__(128) dslash_dw_kernel(Geom g, const float4* __restrict__ U, const float2* __restrict__ clov,
+                                                        const cplx<float>* __restrict__ in, void* __restrict__ outp, int nrhs) {
+    int r = blockIdx.x % nrhs;
+    int i = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const size_t off = (size_t)r * 12 * g.V;
+    const cplx<float>* inr = in + off;
+    cdw acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = cdw_zero();
+    dw_hop_pair<0>(g, acc, inr, U, i);
+    dw_hop_pair<1>(g, acc, inr, U, i);
+    dw_hop_pair<2>(g, acc, inr, U, i);
+    dw_hop_pair<3>(g, acc, inr, U, i);
+    // site term: y = A x with two packed hermitian 6x6 blocks (double-word entries), x FP32
+    cdw y[12];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float x[12];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            cplx<float> v = inr[(size_t)(h * 6 + a) * g.V + i];
+            x[2 * a] = v.re;
+            x[2 * a + 1] = v.im;
+        }
+        const float2* base = clov + (size_t)(h * 36) * g.V + i;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float2 dv = __ldg(base + (size_t)a * g.V);
+            dw d = {dv.x, dv.y};
+            cdw t = cdw_zero();
+            dw_macf(t.re, d, x[2 * a]);
+            dw_macf(t.im, d, x[2 * a + 1]);
+            y[h * 6 + a] = t;
+        }
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < 6; ++b) {
+                float2 mr = __ldg(base + (size_t)(6 + 2 * q) * g.V), mi = __ldg(base + (size_t)(7 + 2 * q) * g.V);
+                dw m_re = {mr.x, mr.y}, m_im = {mi.x, mi.y};
+                // y[a] += m x[b];  y[b] += conj(m) x[a]
+                dw_macf(y[h * 6 + a].re, m_re, x[2 * b]);
+                dw_macf(y[h * 6 + a].re, dw_neg(m_im), x[2 * b + 1]);
+                dw_macf(y[h * 6 + a].im, m_re, x[2 * b + 1]);
+                dw_macf(y[h * 6 + a].im, m_im, x[2 * b]);
+                dw_macf(y[h * 6 + b].re, m_re, x[2 * a]);
+                dw_macf(y[h * 6 + b].re, m_im, x[2 * a + 1]);
+                dw_macf(y[h * 6 + b].im, m_re, x[2 * a + 1]);
+                dw_macf(y[h * 6 + b].im, dw_neg(m_im), x[2 * a]);
+                ++q;
+            }
+        }
+    }
+    if (OUT_DW) {
+        float4* o = reinterpret_cast<float4*>(outp) + off;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            dw re = dw_norm(dw_add(y[k].re, {-0.5f * acc[k].re.h, -0.5f * acc[k].re.l}));
+            dw im = dw_norm(dw_add(y[k].im, {-0.5f * acc[k].im.h, -0.5f * acc[k].im.l}));
+            o[(size_t)k * g.V + i] = make_float4(re.h, re.l, im.h, im.l);
+        }
+    } else {
+        cplx<double>* o = reinterpret_cast<cplx<double>*>(outp) + off;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double re = (double)y[k].re.h + (double)y[k].re.l - 0.5 * ((double)acc[k].re.h + (double)acc[k].re.l);
+            double im = (double)y[k].im.h + (double)y[k].im.l - 0.5 * ((double)acc[k].im.h + (double)acc[k].im.l);
+            o[(size_t)k * g.V + i] = mk(re, im);
+        }
+    }
+}
+
+int launch_dslash_dw(const Geom& g, const float4* U, const float2* clov, const cplx<float>* in, void* out, bool out_dw, int nrhs,
+                     cudaStream_t st) {
+    const int nt = 128;
+    long long nblk = (long long)ceil_div(g.V, nt) * nrhs;
+    if (out_dw) dslash_dw_kernel<true><<<(unsigned)nblk, nt, 0, st>>>(g, U, clov, in, out, nrhs);
+    else dslash_dw_kernel<false><<<(unsigned)nblk, nt, 0, st>>>(g, U, clov, in, out, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// FP64 array -> double-word pairs (hi = nearest float, lo = nearest float of the remainder)
+__global__ void to_dw_kernel(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        double x = in[q];
+        float h = (float)x;
+        out[q] = make_float2(h, (float)(x - (double)h));
+    }
+}
+int launch_to_dw(const double* in, float2* out, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    to_dw_kernel<<<blocks, 256, 0, st>>>(in, out, n);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -32,6 +32,9 @@ template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st);
 int upload_gamma_products(const double* gg);
+int launch_dslash_dw(const Geom& g, const float4* U, const float2* clov, const cplx<float>* in, void* out, bool out_dw, int nrhs,
+                     cudaStream_t st);
+int launch_to_dw(const double* in, float2* out, size_t n, cudaStream_t st);
 int launch_clover(const Geom& g, const cplx<double>* U, double m0, double csw, double* clov, double* clovinv, cudaStream_t st);
 
 // ---- transfer.cu (P, P^H, Gram-Schmidt, D_c assembly)

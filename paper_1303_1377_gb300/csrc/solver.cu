@@ -9,6 +9,7 @@
 #include <functional>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "blas.h"
@@ -55,8 +56,9 @@ static void dfree(T*& p) {
     } while (0)
 
 // profiling families
-enum { PF_DSLASH64 = 0, PF_DSLASH32, PF_SAP, PF_COARSE, PF_RESTRICT, PF_PROLONG, PF_COUNT };
-static const char* kPfNames[PF_COUNT] = {"dslash_fp64", "dslash_fp32", "sap_block_mr", "coarse_stencil", "restrict", "prolong"};
+enum { PF_DSLASH64 = 0, PF_DSLASH32, PF_SAP, PF_COARSE, PF_RESTRICT, PF_PROLONG, PF_DSLASHDW, PF_ORTHO, PF_UPDATE, PF_COUNT };
+static const char* kPfNames[PF_COUNT] = {"dslash_fp64", "dslash_fp32", "sap_block_mr", "coarse_stencil", "restrict", "prolong",
+                                         "dslash_dw",   "krylov_ortho", "krylov_update"};
 
 struct ProfRec {
     int fam;
@@ -97,7 +99,8 @@ struct KrylovBufs {
     cplx<double>* scale = nullptr;  // [nrhs]
     cplx<double>* y = nullptr;      // [m][nrhs]
     cplx<double>* nrm = nullptr;    // [nrhs]
-    cplx<double>* ones = nullptr;   // [1] = 1
+    cplx<double>* ones = nullptr;   // [nrhs] = 1
+    float4* coefdw = nullptr;       // [(m+2)][nrhs] double-word coefficients
     double* dscr = nullptr;         // multidot scratch
     int* h_active = nullptr;        // pinned copy of active flags
     int* h_steps = nullptr;
@@ -126,6 +129,7 @@ struct KrylovBufs {
         DD_TRY(dalloc_n(&y, (size_t)mm * nr));
         DD_TRY(dalloc_n(&nrm, nr));
         DD_TRY(dalloc_n(&ones, nr));
+        DD_TRY(dalloc_n(&coefdw, (size_t)(mm + 2) * nr));
         {
             std::vector<cplx<double>> one(nr, mk(1.0, 0.0));
             DD_CUDA(cudaMemcpy(ones, one.data(), sizeof(cplx<double>) * nr, cudaMemcpyHostToDevice));
@@ -154,6 +158,7 @@ struct KrylovBufs {
         dfree(y);
         dfree(nrm);
         dfree(ones);
+        dfree(coefdw);
         dfree(dscr);
         if (h_active) cudaFreeHost(h_active);
         if (h_steps) cudaFreeHost(h_steps);
@@ -185,6 +190,8 @@ struct ddamg_handle {
     double *clov64 = nullptr, *clovinv64 = nullptr;
     cplx<float>* U32 = nullptr;
     float *clov32 = nullptr, *clovinv32 = nullptr;
+    float4* Udw = nullptr;    // links as double-word FP32 pairs (FGMRES matvec on FP32 inputs)
+    float2* clovdw = nullptr;  // site terms as double-word pairs
     // interpolation
     bool ready = false;
     cplx<double>* V64 = nullptr;  // test vectors [N][12][V]
@@ -194,14 +201,14 @@ struct ddamg_handle {
     float *B32 = nullptr, *Dinv32 = nullptr;
     int* d_flag = nullptr;
     // workspaces
-    Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[4];
+    Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[5];
     KrylovBufs kc, ko;  // coarse GMRES, outer FGMRES
     // stats of the current call
     long long coarse_iters = 0;
     int vcycles = 0;
     double coarse_seconds = 0;
     // profiling
-    bool prof_on = false;
+    int prof_mask = 0;  // bit f: record kernel family f
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
 
@@ -225,7 +232,7 @@ struct Prof {
     ddamg_handle* h;
     ProfRec r;
     bool on;
-    Prof(ddamg_handle* hh, int fam, double bytes) : h(hh), on(hh->prof_on) {
+    Prof(ddamg_handle* hh, int fam, double bytes) : h(hh), on((hh->prof_mask >> fam) & 1) {
         if (on) {
             r.fam = fam;
             r.bytes = bytes;
@@ -468,6 +475,12 @@ static int dslash(ddamg_handle* h, const cplx<Ts>* in, const cplx<T>* b, cplx<T>
     return launch_dslash<T, Ts>(h->g, L.op, in, b, out, nrhs, h->stream);
 }
 
+// w = D z for FP32 z with an FP64-accurate result (double-word arithmetic)
+static int dslash_dw(ddamg_handle* h, const cplx<float>* z, cplx<double>* w, int nrhs) {
+    Prof pr(h, PF_DSLASHDW, (double)h->V * (36.0 * 16 + 72.0 * 8 + nrhs * (12.0 * 8 + 12.0 * 16)));
+    return launch_dslash_dw(h->g, h->Udw, h->clovdw, z, w, false, nrhs, h->stream);
+}
+
 // z <- SAP iterations (nu) on D z = b from the current z (Sec. 2.3)
 template <typename T>
 static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) {
@@ -495,19 +508,20 @@ static int prolong_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) 
 
 // ---------------------------------------------------------------------------
 // batched restarted (F)GMRES.  Vectors of length n per rhs, rhs stride n.
-// A: w = A z;  M (optional): z = M v (flexible; Z basis kept).
-// x holds the initial guess (x0_zero: treat as 0) and receives the solution.
+// TB: right-hand side / iterate (and true residuals), TV: Arnoldi basis,
+// TZ: preconditioned vectors.  A: w = A z (TZ -> TV); Ax: residual product (TB -> TB);
+// M (optional): z = M v (flexible, Z basis kept).
 // ---------------------------------------------------------------------------
-template <typename TV, typename TZ>
+template <typename TB, typename TV, typename TZ>
 struct KrylovProblem {
     size_t n;
     int nrhs;
     int m;
-    std::function<int(const cplx<TZ>*, cplx<TV>*)> A;      // w = A z for basis-type input, all nrhs at once
-    std::function<int(const cplx<TV>*, cplx<TV>*)> Ax;     // w = A x for the iterate (residuals)
-    std::function<int(const cplx<TV>*, cplx<TZ>*)> M;      // empty: no preconditioner (TZ == TV)
-    const cplx<TV>* b;
-    cplx<TV>* x;
+    std::function<int(const cplx<TZ>*, cplx<TV>*)> A;
+    std::function<int(const cplx<TB>*, cplx<TB>*)> Ax;
+    std::function<int(const cplx<TV>*, cplx<TZ>*)> M;
+    const cplx<TB>* b;
+    cplx<TB>* x;
     bool x0_zero;
     double tol;            // relative to ||b_r||
     long long maxiter;     // Arnoldi steps per rhs
@@ -516,7 +530,8 @@ struct KrylovProblem {
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
     cplx<TZ>* Zb;          // [m][nrhs][n] when M is set
     cplx<TV>* w;           // [nrhs][n]
-    const int* enabled_host;  // optional per-rhs participation (nullptr: all)
+    cplx<TB>* wB;          // [nrhs][n] residual scratch (may alias w when TB == TV)
+    const int* enabled_host;
 };
 
 struct KrylovResult {
@@ -528,8 +543,38 @@ struct KrylovResult {
     bool converged = true;
 };
 
-template <typename TV, typename TZ>
-static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, KrylovResult& R) {
+// basis-space kernels (generic precisions / double-word)
+template <typename TV>
+static int bdot(KrylovBufs& kb, const cplx<TV>* A, size_t istride, int k, const cplx<TV>* w, size_t n, int nr, cplx<double>* out,
+                cudaStream_t st) {
+    return multidot<TV, TV>(A, istride, n, k, w, n, n, nr, out, nr, kb.dscr, st);
+}
+template <typename TV>
+static int baxpy(KrylovBufs& kb, cplx<TV>* out, bool accumulate, const cplx<TV>* A, size_t istride, int k, const cplx<double>* coef,
+                 size_t n, int nr, double alpha, cudaStream_t st) {
+    return lincomb<TV, TV>(out, n, accumulate ? 1.0 : 0.0, A, istride, n, k, coef, nr, n, nr, nullptr, st, alpha);
+}
+template <>
+int baxpy<dwf>(KrylovBufs& kb, cplx<dwf>* out, bool accumulate, const cplx<dwf>* A, size_t istride, int k, const cplx<double>* coef,
+               size_t n, int nr, double alpha, cudaStream_t st) {
+    return lincomb_dw(out, n, accumulate ? 1 : 0, A, istride, n, k, coef, nr, n, nr, alpha, kb.coefdw, st);
+}
+template <typename TV, typename TB>
+static int bfrom(cplx<TV>* out, const cplx<TB>* in, size_t count, cudaStream_t st) {
+    if (sizeof(TV) == sizeof(TB)) {
+        DD_CUDA(cudaMemcpyAsync(out, in, sizeof(cplx<TV>) * count, cudaMemcpyDeviceToDevice, st));
+        return 0;
+    }
+    set_error("unsupported basis conversion");
+    return DDAMG_ERR_INVALID_ARG;
+}
+template <>
+int bfrom<dwf, double>(cplx<dwf>* out, const cplx<double>* in, size_t count, cudaStream_t st) {
+    return convert_d2dw(reinterpret_cast<const double*>(in), out, 2 * count, st);
+}
+
+template <typename TB, typename TV, typename TZ>
+static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P, KrylovResult& R) {
     cudaStream_t st = h->stream;
     const int nr = P.nrhs;
     const size_t n = P.n;
@@ -540,7 +585,7 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, Kry
     R.resid.assign(nr, 0.0);
     R.bnorm.assign(nr, 0.0);
     // ||b||, targets, enabled
-    DD_TRY((multidot<TV, TV>(P.b, 0, n, 1, P.b, n, n, nr, kb.nrm, 1, kb.dscr, st)));
+    DD_TRY((multidot<TB, TB>(P.b, 0, n, 1, P.b, n, n, nr, kb.nrm, 1, kb.dscr, st)));
     std::vector<cplx<double>> hb(nr);
     DD_CUDA(cudaMemcpyAsync(hb.data(), kb.nrm, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToHost, st));
     DD_CUDA(cudaStreamSynchronize(st));
@@ -557,24 +602,24 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, Kry
     DD_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(int) * nr, st));
     const size_t bstride = (size_t)nr * n;  // between basis vectors
     cplx<TV>* V0 = P.Vb;
+    // V0 = b - A x (in the iterate's precision), or b for a zero guess
     auto residual_to_V0 = [&]() -> int {
-        DD_TRY(P.Ax(P.x, P.w));
-        DD_CUDA(cudaMemcpyAsync(V0, P.b, sizeof(cplx<TV>) * nr * n, cudaMemcpyDeviceToDevice, st));
-        DD_TRY((lincomb<TV, TV>(V0, n, 1.0, P.w, 0, n, 1, kb.ones, nr, n, nr, nullptr, st, -1.0)));
-        return 0;
+        DD_TRY(P.Ax(P.x, P.wB));
+        DD_TRY((lincomb<TB, TB>(P.wB, n, -1.0, P.b, 0, n, 1, kb.ones, nr, n, nr, nullptr, st)));
+        return bfrom<TV, TB>(V0, P.wB, n * nr, st);
     };
     if (P.x0_zero) {
-        DD_CUDA(cudaMemsetAsync(P.x, 0, sizeof(cplx<TV>) * nr * n, st));
-        DD_CUDA(cudaMemcpyAsync(V0, P.b, sizeof(cplx<TV>) * nr * n, cudaMemcpyDeviceToDevice, st));
+        DD_CUDA(cudaMemsetAsync(P.x, 0, sizeof(cplx<TB>) * nr * n, st));
+        DD_TRY((bfrom<TV, TB>(V0, P.b, n * nr, st)));
     } else {
         DD_TRY(residual_to_V0());
     }
     long long total = 0;
     while (true) {
         // start of a cycle
-        DD_TRY((multidot<TV, TV>(V0, 0, n, 1, V0, n, n, nr, kb.nrm, 1, kb.dscr, st)));
+        DD_TRY(bdot<TV>(kb, V0, 0, 1, V0, n, nr, kb.nrm, st));
         DD_TRY(arnoldi_start(s, kb.nrm, kb.scale, P.fixed ? 1 : 0, st));
-        DD_TRY((lincomb<TV, TV>(V0, n, 0.0, V0, 0, n, 1, kb.scale, nr, n, nr, nullptr, st)));
+        DD_TRY(baxpy<TV>(kb, V0, false, V0, 0, 1, kb.scale, n, nr, 1.0, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaStreamSynchronize(st));
@@ -601,16 +646,20 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, Kry
             }
             DD_TRY(P.A(zk, P.w));
             // classical Gram-Schmidt (twice when reorth)
-            DD_TRY((multidot<TV, TV>(P.Vb, bstride, n, k + 1, P.w, n, n, nr, kb.hcol, nr, kb.dscr, st)));
-            DD_TRY((lincomb<TV, TV>(P.w, n, 1.0, P.Vb, bstride, n, k + 1, kb.hcol, nr, n, nr, nullptr, st, -1.0)));
-            if (P.reorth) {
-                DD_TRY((multidot<TV, TV>(P.Vb, bstride, n, k + 1, P.w, n, n, nr, kb.hcol2, nr, kb.dscr, st)));
-                DD_TRY((lincomb<TV, TV>(P.w, n, 1.0, P.Vb, bstride, n, k + 1, kb.hcol2, nr, n, nr, nullptr, st, -1.0)));
-                DD_TRY(add_columns(kb.hcol, kb.hcol2, (k + 1) * nr, st));
+            {
+                const double vb = (double)sizeof(cplx<TV>) * n * nr;
+                Prof pr(h, PF_ORTHO, vb * ((k + 1) * (P.reorth ? 4 : 2) + 4));
+                DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol, st));
+                DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol, n, nr, -1.0, st));
+                if (P.reorth) {
+                    DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol2, st));
+                    DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol2, n, nr, -1.0, st));
+                    DD_TRY(add_columns(kb.hcol, kb.hcol2, (k + 1) * nr, st));
+                }
+                DD_TRY(bdot<TV>(kb, P.w, 0, 1, P.w, n, nr, kb.hcol + (size_t)(k + 1) * nr, st));
+                DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
+                DD_TRY(baxpy<TV>(kb, P.Vb + (size_t)(k + 1) * bstride, false, P.w, 0, 1, kb.scale, n, nr, 1.0, st));
             }
-            DD_TRY((multidot<TV, TV>(P.w, 0, n, 1, P.w, n, n, nr, kb.hcol + (size_t)(k + 1) * nr, nr, kb.dscr, st)));
-            DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
-            DD_TRY((lincomb<TV, TV>(P.Vb + (size_t)(k + 1) * bstride, n, 0.0, P.w, 0, n, 1, kb.scale, nr, n, nr, nullptr, st)));
             ++total;
             if (P.fixed) {
                 if (total >= P.maxiter) {
@@ -630,10 +679,14 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, Kry
         }
         // x += sum_i y_i Z_i (or V_i)
         DD_TRY(arnoldi_solve(s, kb.y, st));
-        if (P.M)
-            DD_TRY((lincomb<TV, TZ>(P.x, n, 1.0, P.Zb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
-        else
-            DD_TRY((lincomb<TV, TV>(P.x, n, 1.0, P.Vb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
+        {
+            Prof pru(h, PF_UPDATE, (double)n * nr * (2 * sizeof(cplx<TB>) + std::min(k, P.m) * sizeof(cplx<TZ>)));
+            if (P.M)
+                DD_TRY((lincomb<TB, TZ>(P.x, n, 1.0, P.Zb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
+            else
+                DD_TRY((lincomb<TB, TZ>(P.x, n, 1.0, reinterpret_cast<const cplx<TZ>*>(P.Vb), bstride, n, std::min(k, P.m), kb.y, nr,
+                                        n, nr, nullptr, st)));
+        }
         DD_CUDA(cudaMemcpyAsync(kb.h_steps, s.steps, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_flags, s.flags, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
@@ -651,7 +704,6 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TV, TZ>& P, Kry
     }
     return 0;
 }
-
 
 // ---------------------------------------------------------------------------
 // coarse solve: odd-even reduced GMRES(restart) (Sec. 6) on full coarse vectors
@@ -675,24 +727,25 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     cplx<T>* basis = h->ws_coarse[4].as<cplx<T>>();
     Level<T> L = level<T>(h);
     const double sbytes = (double)h->NB * 9 * nc * nc * sizeof(cplx<T>);
+    const double vbytes = 2.0 * hn * nrhs * sizeof(cplx<T>);  // one half vector in, one out
     {
-        Prof pr(h, PF_COARSE, sbytes / 9);
+        Prof pr(h, PF_COARSE, sbytes / 18 + vbytes);
         DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, nullptr, 0, T(0), te, hn, nrhs, st)));
     }
     {
-        Prof pr(h, PF_COARSE, sbytes * 4 / 9);
+        Prof pr(h, PF_COARSE, sbytes * 4 / 9 + 1.5 * vbytes);
         DD_TRY((launch_coarse_odd<T, T>(L.cop, bc + hn, full, te, hn, 0, bp, hn, nrhs, st)));
     }
-    KrylovProblem<T, T> P;
+    KrylovProblem<T, T, T> P;
     P.n = hn;
     P.nrhs = nrhs;
     P.m = m;
     P.A = [&](const cplx<T>* v, cplx<T>* out) -> int {
         {
-            Prof pr(h, PF_COARSE, sbytes / 2);
+            Prof pr(h, PF_COARSE, sbytes / 2 + vbytes);
             DD_TRY((launch_coarse_even<T, T>(L.cop, nullptr, 0, v, hn, T(1), te, hn, nrhs, st)));
         }
-        Prof pr(h, PF_COARSE, sbytes / 2);
+        Prof pr(h, PF_COARSE, sbytes / 2 + 1.5 * vbytes);
         return launch_coarse_odd<T, T>(L.cop, v, hn, te, hn, 1, out, hn, nrhs, st);
     };
     P.Ax = P.A;
@@ -706,15 +759,16 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     P.Vb = basis;
     P.Zb = nullptr;
     P.w = w;
+    P.wB = w;
     P.enabled_host = nullptr;
     KrylovResult R;
-    DD_TRY((krylov<T, T>(h, h->kc, P, R)));
+    DD_TRY((krylov<T, T, T>(h, h->kc, P, R)));
     long long it = 0;
     for (long long v : R.iters) it = std::max(it, v);
     h->coarse_iters += it;
     // back-substitution x_e = D_ee^{-1} (b_e - D_eo x_o); x_o into the odd half
     {
-        Prof pr(h, PF_COARSE, sbytes / 2);
+        Prof pr(h, PF_COARSE, sbytes / 2 + 1.5 * vbytes);
         DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, xo, hn, T(-1), xc, full, nrhs, st)));
     }
     DD_CUDA(cudaMemcpy2DAsync(xc + hn, full * sizeof(cplx<T>), xo, hn * sizeof(cplx<T>), hn * sizeof(cplx<T>), nrhs,
@@ -887,25 +941,38 @@ static int run_setup(ddamg_handle* h, const double* v0) {
 // ---------------------------------------------------------------------------
 // the outer solve: FGMRES(n_kv) in FP64, one V-cycle as right preconditioner
 // ---------------------------------------------------------------------------
-template <typename TZ>
+// TV = basis type: double-word FP32 pairs when the V-cycle is FP32 (GB300's FP64
+// rate is a small fraction of its FP32 rate), FP64 for the all-FP64 path.
+template <typename TZ, typename TV>
 static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R) {
     cudaStream_t st = h->stream;
     const size_t fld = (size_t)12 * h->V;
     const int m = h->p.n_kv;
-    DD_TRY(h->ws_outer[0].ensure(sizeof(cplx<double>) * fld * nrhs * (m + 1)));
+    DD_TRY(h->ws_outer[0].ensure(sizeof(cplx<TV>) * fld * nrhs * (m + 1)));
     DD_TRY(h->ws_outer[1].ensure(sizeof(cplx<TZ>) * fld * nrhs * m));
-    DD_TRY(h->ws_outer[2].ensure(sizeof(cplx<double>) * fld * nrhs));
+    DD_TRY(h->ws_outer[2].ensure(sizeof(cplx<TV>) * fld * nrhs));
     DD_TRY(h->ws_outer[3].ensure(sizeof(cplx<TZ>) * fld * nrhs));
+    const bool sep = sizeof(TV) != sizeof(double) * 2 || !std::is_same<TV, double>::value;
+    if (sep) DD_TRY(h->ws_outer[4].ensure(sizeof(cplx<double>) * fld * nrhs));
     cplx<TZ>* rT = h->ws_outer[3].as<cplx<TZ>>();
-    KrylovProblem<double, TZ> P;
+    KrylovProblem<double, TV, TZ> P;
     P.n = fld;
     P.nrhs = nrhs;
     P.m = m;
-    P.A = [&](const cplx<TZ>* z, cplx<double>* w) -> int { return dslash<double, TZ>(h, z, nullptr, w, nrhs); };
+    P.A = [&](const cplx<TZ>* z, cplx<TV>* w) -> int {
+        if (std::is_same<TV, dwf>::value) {
+            Prof pr(h, PF_DSLASHDW, (double)h->V * (36.0 * 16 + 72.0 * 8 + nrhs * (12.0 * 8 + 12.0 * 16)));
+            return launch_dslash_dw(h->g, h->Udw, h->clovdw, reinterpret_cast<const cplx<float>*>(z), w, true, nrhs, h->stream);
+        }
+        return dslash<double, TZ>(h, z, nullptr, reinterpret_cast<cplx<double>*>(w), nrhs);
+    };
     P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int { return dslash<double, double>(h, z, nullptr, w, nrhs); };
-    P.M = [&](const cplx<double>* v, cplx<TZ>* z) -> int {
+    P.M = [&](const cplx<TV>* v, cplx<TZ>* z) -> int {
         const cplx<TZ>* r;
-        if (sizeof(TZ) == 8) {
+        if (std::is_same<TV, dwf>::value) {
+            DD_TRY(convert_dw2f(reinterpret_cast<const cplx<dwf>*>(v), reinterpret_cast<float*>(rT), 2 * fld * nrhs, st));
+            r = rT;
+        } else if (sizeof(TZ) == 8) {
             r = reinterpret_cast<const cplx<TZ>*>(v);
         } else {
             DD_TRY((convert<TZ, double>(reinterpret_cast<const double*>(v), reinterpret_cast<TZ*>(rT), 2 * fld * nrhs, st)));
@@ -920,11 +987,12 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     P.fixed = false;
     P.maxiter = h->p.max_outer;
     P.reorth = true;
-    P.Vb = h->ws_outer[0].as<cplx<double>>();
+    P.Vb = h->ws_outer[0].as<cplx<TV>>();
     P.Zb = h->ws_outer[1].as<cplx<TZ>>();
-    P.w = h->ws_outer[2].as<cplx<double>>();
+    P.w = h->ws_outer[2].as<cplx<TV>>();
+    P.wB = sep ? h->ws_outer[4].as<cplx<double>>() : reinterpret_cast<cplx<double>*>(P.w);
     P.enabled_host = nullptr;
-    return krylov<double, TZ>(h, h->ko, P, R);
+    return krylov<double, TV, TZ>(h, h->ko, P, R);
 }
 
 static int check_ready(ddamg_handle* h) {
@@ -998,7 +1066,8 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
     if (h->single()) {
         if ((rc = dalloc_n(&h->U32, V * 36)) || (rc = dalloc_n(&h->clov32, V * 72)) || (rc = dalloc_n(&h->clovinv32, V * 72)) ||
             (rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
-            (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)))
+            (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)) || (rc = dalloc_n(&h->Udw, V * 36)) ||
+            (rc = dalloc_n(&h->clovdw, V * 72)))
             return fail(rc);
     }
     // gauge field -> internal order, clover term and inverses
@@ -1009,7 +1078,9 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
     if (h->single()) {
         if ((rc = convert<float, double>(reinterpret_cast<const double*>(h->U64), reinterpret_cast<float*>(h->U32), V * 72, h->stream)) ||
             (rc = convert<float, double>(h->clov64, h->clov32, V * 72, h->stream)) ||
-            (rc = convert<float, double>(h->clovinv64, h->clovinv32, V * 72, h->stream)))
+            (rc = convert<float, double>(h->clovinv64, h->clovinv32, V * 72, h->stream)) ||
+            (rc = launch_to_dw(reinterpret_cast<const double*>(h->U64), reinterpret_cast<float2*>(h->Udw), V * 72, h->stream)) ||
+            (rc = launch_to_dw(h->clov64, h->clovdw, V * 72, h->stream)))
             return fail(rc);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1161,7 +1232,7 @@ static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, d
     h->vcycles = 0;
     h->coarse_seconds = 0;
     KrylovResult R;
-    int rc = h->single() ? solve_T<float>(h, bi, xi, nrhs, tol, false, R) : solve_T<double>(h, bi, xi, nrhs, tol, false, R);
+    int rc = h->single() ? solve_T<float, dwf>(h, bi, xi, nrhs, tol, false, R) : solve_T<double, double>(h, bi, xi, nrhs, tol, false, R);
     if (rc) return rc;
     DD_TRY(fine_out<double>(h, xi, z, nrhs));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1226,6 +1297,25 @@ int ddamg_apply_D_f32(ddamg_handle* h, const float* in, float* out, int n_rhs) {
     return finish_out(h, out, dout, sizeof(cplx<float>) * fld * n_rhs, host);
 }
 
+}  // extern "C"
+
+extern "C" {
+int ddamg_apply_D_mixed(ddamg_handle* h, const float* in, double* out, int n_rhs) {
+    if (!h || !in || !out || n_rhs < 1) return DDAMG_ERR_INVALID_ARG;
+    if (!h->single()) {
+        set_error("ddamg_apply_D_mixed needs a handle in single or half precision");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(h->ws_fine[4].ensure((sizeof(cplx<float>) + sizeof(cplx<double>)) * fld * n_rhs));
+    cplx<float>* a = h->ws_fine[4].as<cplx<float>>();
+    cplx<double>* o = reinterpret_cast<cplx<double>*>(a + fld * n_rhs);
+    const void* dv;
+    DD_TRY(stage_in(h, h->ws_io[0], in, sizeof(cplx<float>) * fld * n_rhs, &dv));
+    DD_TRY((to_internal<float, float>(reinterpret_cast<const cplx<float>*>(dv), a, h->d_lex_of, h->V, 12, n_rhs, h->stream)));
+    DD_TRY(dslash_dw(h, a, o, n_rhs));
+    return fine_out<double>(h, o, out, n_rhs);
+}
 }  // extern "C"
 
 template <typename T>
@@ -1388,6 +1478,7 @@ int ddamg_set_mass(ddamg_handle* h, double m0) {
     if (h->single()) {
         DD_TRY((convert<float, double>(h->clov64, h->clov32, (size_t)h->V * 72, h->stream)));
         DD_TRY((convert<float, double>(h->clovinv64, h->clovinv32, (size_t)h->V * 72, h->stream)));
+        DD_TRY(launch_to_dw(h->clov64, h->clovdw, (size_t)h->V * 72, h->stream));
     }
     if (h->ready) DD_TRY(build_interpolation(h));
     DD_CUDA(cudaStreamSynchronize(h->stream));
@@ -1408,10 +1499,23 @@ int ddamg_info(const ddamg_handle* h, long long* n_sites, long long* n_coarse, i
     return 0;
 }
 
-int ddamg_profile_enable(ddamg_handle* h, int on) {
+int ddamg_profile_enable(ddamg_handle* h, int family_mask) {
     if (!h) return DDAMG_ERR_INVALID_ARG;
-    h->prof_on = on != 0;
+    h->prof_mask = family_mask;
     return 0;
+}
+
+int ddamg_profile_families(char* names, int len) {
+    std::string all;
+    for (int f = 0; f < PF_COUNT; ++f) {
+        if (f) all += ",";
+        all += kPfNames[f];
+    }
+    if (names && len > 0) {
+        std::strncpy(names, all.c_str(), (size_t)len - 1);
+        names[len - 1] = 0;
+    }
+    return PF_COUNT;
 }
 
 int ddamg_profile_reset(ddamg_handle* h) {
@@ -1476,6 +1580,8 @@ int ddamg_destroy(ddamg_handle* h) {
     dfree(h->Dinv64);
     dfree(h->B32);
     dfree(h->Dinv32);
+    dfree(h->Udw);
+    dfree(h->clovdw);
     dfree(h->d_flag);
     for (auto& s : h->ws_fine) s.release();
     for (auto& s : h->ws_coarse) s.release();

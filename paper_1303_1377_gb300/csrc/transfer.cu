@@ -17,33 +17,34 @@ namespace ddamg {
 template <typename T, typename Tp>
 __global__ void restrict_kernel(Geom g, const cplx<Tp>* __restrict__ P, int N, const cplx<T>* __restrict__ in,
                                 cplx<T>* __restrict__ out, int nrhs) {
+    // accumulation in the V-cycle precision T (FP64 arithmetic is a small fraction of FP32 on GB300)
     extern __shared__ unsigned char smem_raw[];
-    double* red = reinterpret_cast<double*>(smem_raw);  // [nwarps][4N]
+    T* red = reinterpret_cast<T*>(smem_raw);  // [nwarps][4N]
     const int r = blockIdx.x % nrhs;
     const int c = blockIdx.x / nrhs;
     const int l = threadIdx.x;
     const bool act = l < g.Vb;
     const int i = c * g.Vb + l;
     const cplx<T>* inr = in + (size_t)r * 12 * g.V;
-    cplx<double> x[12];
+    cplx<T> x[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) x[k] = act ? ccast<double>(inr[(size_t)k * g.V + i]) : czero<double>();
+    for (int k = 0; k < 12; ++k) x[k] = act ? inr[(size_t)k * g.V + i] : czero<T>();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = 0; j < N; ++j) {
-        cplx<double> s0 = czero<double>(), s1 = czero<double>();
+        cplx<T> s0 = czero<T>(), s1 = czero<T>();
         if (act) {
             const cplx<Tp>* pj = P + (size_t)j * 12 * g.V;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) cmac_conj(s0, ccast<double>(pj[(size_t)k * g.V + i]), x[k]);
+            for (int k = 0; k < 6; ++k) cmac_conj(s0, ccast<T>(pj[(size_t)k * g.V + i]), x[k]);
 #pragma unroll
-            for (int k = 6; k < 12; ++k) cmac_conj(s1, ccast<double>(pj[(size_t)k * g.V + i]), x[k]);
+            for (int k = 6; k < 12; ++k) cmac_conj(s1, ccast<T>(pj[(size_t)k * g.V + i]), x[k]);
         }
         s0.re = warp_sum(s0.re);
         s0.im = warp_sum(s0.im);
         s1.re = warp_sum(s1.re);
         s1.im = warp_sum(s1.im);
         if (lane == 0) {
-            double* q = red + (size_t)w * 4 * N + 4 * j;
+            T* q = red + (size_t)w * 4 * N + 4 * j;
             q[0] = s0.re;
             q[1] = s0.im;
             q[2] = s1.re;
@@ -52,11 +53,11 @@ __global__ void restrict_kernel(Geom g, const cplx<Tp>* __restrict__ P, int N, c
     }
     __syncthreads();
     for (int q = threadIdx.x; q < 4 * N; q += blockDim.x) {
-        double s = 0;
+        T s = 0;
         for (int ww = 0; ww < nw; ++ww) s += red[(size_t)ww * 4 * N + q];
         int j = q >> 2, h = (q >> 1) & 1, im = q & 1;  // q = 4 j + 2 h + im
         T* o = reinterpret_cast<T*>(out + ((size_t)r * g.NB + c) * (2 * N) + h * N + j);
-        o[im] = T(s);
+        o[im] = s;
     }
 }
 
@@ -64,7 +65,7 @@ template <typename T, typename Tp>
 int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st) {
     const int nt = ((g.Vb + 31) / 32) * 32;
     const long long nblk = (long long)g.NB * nrhs;
-    size_t sm = (size_t)(nt / 32) * 4 * N * sizeof(double);
+    size_t sm = (size_t)(nt / 32) * 4 * N * sizeof(T);
     if (sm > 48 * 1024) cudaFuncSetAttribute(restrict_kernel<T, Tp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     restrict_kernel<T, Tp><<<(unsigned)nblk, nt, sm, st>>>(g, P, N, in, out, nrhs);
     DD_CHECK_LAUNCH();

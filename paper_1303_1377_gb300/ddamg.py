@@ -103,6 +103,7 @@ def _load():
         "ddamg_solve_batch": (I, [P, P, P, I, D, C.POINTER(Stats)]),
         "ddamg_apply_D": (I, [P, P, P, I]),
         "ddamg_apply_D_f32": (I, [P, P, P, I]),
+        "ddamg_apply_D_mixed": (I, [P, P, P, I]),
         "ddamg_apply_sap": (I, [P, P, P, I, I]),
         "ddamg_restrict": (I, [P, P, P, I]),
         "ddamg_prolong": (I, [P, P, P, I]),
@@ -116,6 +117,7 @@ def _load():
         "ddamg_profile_enable": (I, [P, I]),
         "ddamg_profile_read": (I, [P, C.POINTER(KernelProfile), I]),
         "ddamg_profile_reset": (I, [P]),
+        "ddamg_profile_families": (I, [C.c_char_p, I]),
         "ddamg_launch_count": (LL, []),
         "ddamg_debug_fail_allocs": (None, [I]),
         "ddamg_destroy": (I, [P]),
@@ -260,6 +262,14 @@ class Solver:
     def apply_D_f32(self, x):
         return self._fine_op(lib.ddamg_apply_D_f32, x, dtype=np.complex64)
 
+    def apply_D_mixed(self, x):
+        """D x for a complex64 field, complex128 result (double-word FP32 arithmetic)."""
+        x = _host(x, np.complex64)
+        nr = 1 if x.ndim == 3 else int(x.shape[0])
+        out = _empty_like(x, x.shape, np.complex128)
+        _check(lib.ddamg_apply_D_mixed(self.h, _ptr(x), _ptr(out), nr), "ddamg_apply_D_mixed")
+        return out
+
     def apply_sap(self, x, nu: int):
         return self._fine_op(lib.ddamg_apply_sap, x, int(nu))
 
@@ -299,8 +309,16 @@ class Solver:
         return out
 
     # -- profiling ----------------------------------------------------------------
-    def profile(self, on: bool = True):
-        lib.ddamg_profile_enable(self.h, 1 if on else 0)
+    def profile(self, families=None):
+        """Record the named kernel families (None: all; [] : off)."""
+        if families is None:
+            mask = -1
+        else:
+            names = profile_families()
+            mask = 0
+            for f in families:
+                mask |= 1 << names.index(f)
+        lib.ddamg_profile_enable(self.h, mask)
 
     def profile_reset(self):
         lib.ddamg_profile_reset(self.h)
@@ -309,6 +327,12 @@ class Solver:
         arr = (KernelProfile * 16)()
         n = lib.ddamg_profile_read(self.h, arr, 16)
         return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes} for i in range(min(n, 16))}
+
+
+def profile_families():
+    buf = C.create_string_buffer(256)
+    lib.ddamg_profile_families(buf, 256)
+    return buf.value.decode().split(",")
 
 
 def launch_count() -> int:

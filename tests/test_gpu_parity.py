@@ -74,6 +74,10 @@ def test_dslash_fp64_fp32(name, dd):
         assert relerr(s.apply_D(x), ref) < 1e-13
         y32 = s.apply_D_f32(x.astype(np.complex64))
         assert relerr(y32, ref) < 2e-6
+        # double-word path: exact FP32 input, FP64-accurate output
+        x32 = x.astype(np.complex64)
+        ref32 = np.stack([c.D.apply(x32[r].astype(np.complex128)) for r in range(3)])
+        assert relerr(s.apply_D_mixed(x32), ref32) < 1e-13
 
 
 @pytest.mark.parametrize("name", list(CASES))

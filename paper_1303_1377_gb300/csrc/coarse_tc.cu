@@ -1,0 +1,314 @@
+// Coarse stencil on tensor cores with FP16 storage and FP32 accumulation (the
+// half-precision mode of the V-cycle).  For one coarse site c the operator is
+// y = sum_d B_d(c) x_{c+d} (Sec. 3.2).  Complex blocks are written as two real
+// planes, A_c = [Re B ; Im B] (2nc rows), and the right-hand sides as two real
+// column groups [Re X | Im X]; one real GEMM P = A_c X gives
+//   Re y = P[0:nc, 0:NR] - P[nc:2nc, NR:2NR],  Im y = P[nc:2nc, 0:NR] + P[0:nc, NR:2NR],
+// so the complex matrix is stored once (2 halves per entry) without the 2x2
+// real embedding.  The nine directions are stacked along K, the eight hops first
+// (8 nc columns: a multiple of 16 for any N) and the self block last, so the
+// Schur-complement kernels that use only the hops read a 16-aligned K range.
+//
+// Storage: A_c is pre-arranged in the register-fragment order of
+// mma.sync.m16n8k16 (A row-major): for each (m-tile, k-tile) the 32 lanes' four
+// 32-bit registers are 512 contiguous bytes, so each warp streams the matrix
+// with one coalesced 16-byte load per lane and k-tile.  The right-hand sides are
+// staged in shared memory as FP16 (k contiguous per column).
+//
+// Why mma.sync here: each coarse site owns a distinct 2nc x 9nc matrix (M = 80
+// rows at N_v = 20) multiplied by a thin 9nc x 2 n_rhs block, and the kernel
+// streams every matrix byte once, so it is bound by HBM.  A warp-level m16
+// tile matches the 80-row per-site blocks without padding.
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace ddamg {
+
+__device__ __forceinline__ __half elem_of(const double* M, size_t base, int nc, int m, int col) {
+    // M: complex column-major nc x nc block at base (doubles), m < nc: real plane, else imaginary plane
+    int row = m < nc ? m : m - nc;
+    return __float2half_rn((float)M[base + 2 * ((size_t)col * nc + row) + (m < nc ? 0 : 1)]);
+}
+
+__device__ __forceinline__ unsigned pack2(__half lo, __half hi) {
+    __half2 v = __halves2half2(lo, hi);
+    return *reinterpret_cast<unsigned*>(&v);
+}
+
+// A_c[m][kk] for the stencil matrix
+__device__ __forceinline__ __half stencil_elem(const double* B64, int c, int nc, int m, int kk) {
+    int d, col;
+    if (kk < 8 * nc) {
+        d = 1 + kk / nc;
+        col = kk % nc;
+    } else if (kk < 9 * nc) {
+        d = 0;
+        col = kk - 8 * nc;
+    } else {
+        return __float2half_rn(0.f);
+    }
+    return elem_of(B64, (((size_t)c * 9 + d) * nc) * nc * 2, nc, m, col);
+}
+
+__global__ void pack_stencil_kernel(const double* __restrict__ B64, uint4* __restrict__ Bh, int NB, int nc, int Mt, int Kt) {
+    const size_t tot = (size_t)NB * Mt * Kt * 32;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int L = (int)(q % 32);
+        int kt = (int)((q / 32) % Kt);
+        int mt = (int)((q / 32 / Kt) % Mt);
+        int c = (int)(q / ((size_t)32 * Kt * Mt));
+        int g = L >> 2, t = L & 3;
+        int r0 = mt * 16 + g, r1 = r0 + 8, k0 = kt * 16 + 2 * t, k1 = k0 + 8;
+        uint4 v;
+        v.x = pack2(stencil_elem(B64, c, nc, r0, k0), stencil_elem(B64, c, nc, r0, k0 + 1));
+        v.y = pack2(stencil_elem(B64, c, nc, r1, k0), stencil_elem(B64, c, nc, r1, k0 + 1));
+        v.z = pack2(stencil_elem(B64, c, nc, r0, k1), stencil_elem(B64, c, nc, r0, k1 + 1));
+        v.w = pack2(stencil_elem(B64, c, nc, r1, k1), stencil_elem(B64, c, nc, r1, k1 + 1));
+        Bh[q] = v;
+    }
+}
+
+__device__ __forceinline__ __half dinv_elem(const double* D64, int c, int nc, int m, int kk) {
+    if (kk >= nc) return __float2half_rn(0.f);
+    return elem_of(D64, (size_t)c * nc * nc * 2, nc, m, kk);
+}
+
+__global__ void pack_dinv_kernel(const double* __restrict__ D64, uint4* __restrict__ Dh, int NH, int nc, int Mt, int Kt) {
+    const size_t tot = (size_t)NH * Mt * Kt * 32;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int L = (int)(q % 32);
+        int kt = (int)((q / 32) % Kt);
+        int mt = (int)((q / 32 / Kt) % Mt);
+        int c = (int)(q / ((size_t)32 * Kt * Mt));
+        int g = L >> 2, t = L & 3;
+        int r0 = mt * 16 + g, r1 = r0 + 8, k0 = kt * 16 + 2 * t, k1 = k0 + 8;
+        uint4 v;
+        v.x = pack2(dinv_elem(D64, c, nc, r0, k0), dinv_elem(D64, c, nc, r0, k0 + 1));
+        v.y = pack2(dinv_elem(D64, c, nc, r1, k0), dinv_elem(D64, c, nc, r1, k0 + 1));
+        v.z = pack2(dinv_elem(D64, c, nc, r0, k1), dinv_elem(D64, c, nc, r0, k1 + 1));
+        v.w = pack2(dinv_elem(D64, c, nc, r1, k1), dinv_elem(D64, c, nc, r1, k1 + 1));
+        Dh[q] = v;
+    }
+}
+
+int tc_dims(int nc, int* Mt, int* Kt_all, int* Kt_hops, int* Kt_d) {
+    if (nc % 8) return DDAMG_ERR_INVALID_ARG;
+    *Mt = nc / 8;
+    *Kt_hops = (8 * nc) / 16;
+    *Kt_d = (nc + 15) / 16;
+    *Kt_all = *Kt_hops + *Kt_d;
+    return 0;
+}
+
+int pack_coarse_tc(const double* B64, const double* Dinv64, uint4* Bh, uint4* Dh, int NB, int nc, cudaStream_t st) {
+    int Mt, Kta, Kth, Ktd;
+    if (tc_dims(nc, &Mt, &Kta, &Kth, &Ktd)) {
+        set_error("half precision needs 2N divisible by 8");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    pack_stencil_kernel<<<152 * 8, 256, 0, st>>>(B64, Bh, NB, nc, Mt, Kta);
+    DD_CHECK_LAUNCH();
+    pack_dinv_kernel<<<152 * 8, 256, 0, st>>>(Dinv64, Dh, NB / 2, nc, Mt, Ktd);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint4& a, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+template <typename T>
+struct CVecT {
+    cplx<T>* p;
+    size_t rstride;
+    int site0;
+};
+
+// One CTA per coarse site, warp w owns m-tile w (rows 16w..16w+15 of [Re; Im]).
+//   acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)]; self = 0 / B_0 xself / xself;
+//   out = apply_inv ? Dinv acc : acc       (same modes as the CUDA-core kernel)
+template <int NRP>
+__global__ void coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode, float hop_sign,
+                                 int apply_inv, CVecT<float> out, int nrhs) {
+    constexpr int NT = NRP / 4;  // n-tiles of 8 columns over [Re X | Im X] (2 NRP columns)
+    extern __shared__ unsigned char smem_raw[];
+    const int nc = op.nc;
+    const int Kp = op.Kt_all * 16;
+    const int LDX = Kp + 8;                                             // halves per staged column (bank offset)
+    __half* XT = reinterpret_cast<__half*>(smem_raw);                   // [2 NRP][LDX]
+    float* Cs = reinterpret_cast<float*>(XT + (size_t)2 * NRP * LDX);   // [2nc][2 NRP]
+    cplx<float>* Vs = reinterpret_cast<cplx<float>*>(Cs + (size_t)2 * nc * 2 * NRP);  // [nc][NRP]
+    const int c = site_begin + blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const bool hops = hop_sign != 0.f;
+    // 1. stage [Re X | Im X]^T for the used K range
+    for (int q = threadIdx.x; q < NRP * Kp; q += blockDim.x) {
+        int kk = q % Kp, r = q / Kp;
+        cplx<float> v = czero<float>();
+        if (r < nrhs) {
+            if (kk < 8 * nc) {
+                if (hops) {
+                    int d = 1 + kk / nc, col = kk % nc;
+                    int n = __ldg(op.cnbr + (d - 1) * op.NB + c);
+                    v = hop_sign * xin.p[r * xin.rstride + (size_t)(n - xin.site0) * nc + col];
+                }
+            } else if (kk < 9 * nc && self_mode == 1) {
+                v = xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + (kk - 8 * nc)];
+            }
+        }
+        XT[(size_t)r * LDX + kk] = __float2half_rn(v.re);
+        XT[(size_t)(NRP + r) * LDX + kk] = __float2half_rn(v.im);
+    }
+    __syncthreads();
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const int kt0 = hops ? 0 : op.Kt_hops;
+    const int kt1 = self_mode == 1 ? op.Kt_all : op.Kt_hops;
+    const uint4* Ab = op.Bh + (((size_t)c * op.Mt + w) * op.Kt_all) * 32 + lane;
+#pragma unroll 4
+    for (int kt = kt0; kt < kt1; ++kt) {
+        uint4 a = __ldg(Ab + (size_t)kt * 32);
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
+            unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
+            unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
+            mma16816(acc[n], a, b0, b1);
+        }
+    }
+    // 2. recombine the planes into complex rows (+ identity self term)
+    auto store_acc = [&]() {
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            int r0 = w * 16 + g, col = n * 8 + 2 * t;
+            Cs[(size_t)r0 * 2 * NRP + col] = acc[n][0];
+            Cs[(size_t)r0 * 2 * NRP + col + 1] = acc[n][1];
+            Cs[(size_t)(r0 + 8) * 2 * NRP + col] = acc[n][2];
+            Cs[(size_t)(r0 + 8) * 2 * NRP + col + 1] = acc[n][3];
+        }
+    };
+    store_acc();
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * NRP; q += blockDim.x) {
+        int row = q / NRP, r = q % NRP;
+        float re = Cs[(size_t)row * 2 * NRP + r] - Cs[(size_t)(nc + row) * 2 * NRP + NRP + r];
+        float im = Cs[(size_t)(nc + row) * 2 * NRP + r] + Cs[(size_t)row * 2 * NRP + NRP + r];
+        cplx<float> v = mk(re, im);
+        if (self_mode == 2 && r < nrhs) v = v + xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + row];
+        Vs[q] = v;
+    }
+    __syncthreads();
+    if (apply_inv) {
+        const int Kd = op.Kt_d * 16;
+        for (int q = threadIdx.x; q < NRP * Kd; q += blockDim.x) {
+            int kk = q % Kd, r = q / Kd;
+            cplx<float> v = kk < nc ? Vs[kk * NRP + r] : czero<float>();
+            XT[(size_t)r * LDX + kk] = __float2half_rn(v.re);
+            XT[(size_t)(NRP + r) * LDX + kk] = __float2half_rn(v.im);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        const uint4* Db = op.Dh + (((size_t)c * op.Mt + w) * op.Kt_d) * 32 + lane;
+        for (int kt = 0; kt < op.Kt_d; ++kt) {
+            uint4 a = __ldg(Db + (size_t)kt * 32);
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
+                unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
+                unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
+                mma16816(acc[n], a, b0, b1);
+            }
+        }
+        store_acc();
+        __syncthreads();
+        for (int q = threadIdx.x; q < nc * NRP; q += blockDim.x) {
+            int row = q / NRP, r = q % NRP;
+            float re = Cs[(size_t)row * 2 * NRP + r] - Cs[(size_t)(nc + row) * 2 * NRP + NRP + r];
+            float im = Cs[(size_t)(nc + row) * 2 * NRP + r] + Cs[(size_t)row * 2 * NRP + NRP + r];
+            Vs[q] = mk(re, im);
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < nc * NRP; q += blockDim.x) {
+        int row = q / NRP, r = q % NRP;
+        if (r < nrhs) out.p[r * out.rstride + (size_t)(c - out.site0) * nc + row] = Vs[q];
+    }
+}
+
+template <int NRP>
+static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<float> xin, CVecT<float> xself, int self_mode,
+                         float hop_sign, int apply_inv, CVecT<float> out, int nrhs, cudaStream_t st) {
+    const int Kp = op.Kt_all * 16;
+    size_t smem = (size_t)2 * NRP * (Kp + 8) * sizeof(__half) + (size_t)2 * op.nc * 2 * NRP * sizeof(float) +
+                  (size_t)op.nc * NRP * sizeof(cplx<float>);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(coarse_tc_kernel<NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    coarse_tc_kernel<NRP><<<nsites, 32 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+static int launch_tc(const CoarseTC& op, int site_begin, int nsites, CVecT<float> xin, CVecT<float> xself, int self_mode,
+                     float hop_sign, int apply_inv, CVecT<float> out, int nrhs, cudaStream_t st) {
+    while (nrhs > 0) {
+        int n = nrhs > 24 ? 24 : nrhs;
+        int rc;
+        if (n <= 4) rc = launch_tc_nrp<4>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
+        else if (n <= 8) rc = launch_tc_nrp<8>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
+        else if (n <= 12) rc = launch_tc_nrp<12>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
+        else if (n <= 16) rc = launch_tc_nrp<16>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
+        else rc = launch_tc_nrp<24>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
+        if (rc) return rc;
+        nrhs -= n;
+        xin.p += n * xin.rstride;
+        xself.p += n * xself.rstride;
+        out.p += n * out.rstride;
+    }
+    return 0;
+}
+
+int tc_coarse_full(const CoarseTC& op, const cplx<float>* x, cplx<float>* y, int nrhs, cudaStream_t st) {
+    size_t rs = (size_t)op.NB * op.nc;
+    CVecT<float> xv{const_cast<cplx<float>*>(x), rs, 0}, yv{y, rs, 0};
+    return launch_tc(op, 0, op.NB, xv, xv, 1, 1.f, 0, yv, nrhs, st);
+}
+
+int tc_coarse_even(const CoarseTC& op, const cplx<float>* b_e, size_t b_rs, const cplx<float>* x_o, size_t x_rs, float beta,
+                   cplx<float>* out_e, size_t o_rs, int nrhs, cudaStream_t st) {
+    const int H = op.NB / 2;
+    CVecT<float> xv{const_cast<cplx<float>*>(x_o ? x_o : out_e), x_o ? x_rs : o_rs, H};
+    CVecT<float> bv{const_cast<cplx<float>*>(b_e ? b_e : out_e), b_e ? b_rs : o_rs, 0};
+    CVecT<float> ov{out_e, o_rs, 0};
+    return launch_tc(op, 0, H, xv, bv, b_e ? 2 : 0, x_o ? beta : 0.f, 1, ov, nrhs, st);
+}
+
+int tc_coarse_odd(const CoarseTC& op, const cplx<float>* x_o, size_t x_rs, const cplx<float>* t_e, size_t t_rs, int use_diag,
+                  cplx<float>* out_o, size_t o_rs, int nrhs, cudaStream_t st) {
+    const int H = op.NB / 2;
+    CVecT<float> tv{const_cast<cplx<float>*>(t_e), t_rs, 0}, xv{const_cast<cplx<float>*>(x_o), x_rs, H}, ov{out_o, o_rs, H};
+    return launch_tc(op, H, H, tv, xv, use_diag ? 1 : 2, -1.f, 0, ov, nrhs, st);
+}
+
+// P (FP64) -> FP16 copy for the half-precision restriction / prolongation
+__global__ void to_half_kernel(const double* __restrict__ in, __half* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        out[q] = __float2half_rn((float)in[q]);
+}
+int convert_to_half(const double* in, void* out, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    to_half_kernel<<<blocks, 256, 0, st>>>(in, reinterpret_cast<__half*>(out), n);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+}  // namespace ddamg

@@ -59,4 +59,20 @@ int launch_coarse_odd(const CoarseOp<S>& op, const cplx<T>* x_o, size_t x_rs, co
                       cplx<T>* out_o, size_t o_rs, int nrhs, cudaStream_t st);
 int launch_coarse_invert(const double* B, double* Dinv, int NB, int nc, int* fail, cudaStream_t st);
 
+// ---- coarse_tc.cu (half-precision storage, tensor cores)
+struct CoarseTC {
+    const uint4* Bh;
+    const uint4* Dh;
+    const int* cnbr;
+    int NB, nc, Mt, Kt_all, Kt_hops, Kt_d;
+};
+int tc_dims(int nc, int* Mt, int* Kt_all, int* Kt_hops, int* Kt_d);
+int pack_coarse_tc(const double* B64, const double* Dinv64, uint4* Bh, uint4* Dh, int NB, int nc, cudaStream_t st);
+int tc_coarse_full(const CoarseTC& op, const cplx<float>* x, cplx<float>* y, int nrhs, cudaStream_t st);
+int tc_coarse_even(const CoarseTC& op, const cplx<float>* b_e, size_t b_rs, const cplx<float>* x_o, size_t x_rs, float beta,
+                   cplx<float>* out_e, size_t o_rs, int nrhs, cudaStream_t st);
+int tc_coarse_odd(const CoarseTC& op, const cplx<float>* x_o, size_t x_rs, const cplx<float>* t_e, size_t t_rs, int use_diag,
+                  cplx<float>* out_o, size_t o_rs, int nrhs, cudaStream_t st);
+int convert_to_half(const double* in, void* out, size_t n, cudaStream_t st);
+
 }  // namespace ddamg

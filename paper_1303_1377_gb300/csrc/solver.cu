@@ -12,6 +12,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "blas.h"
 #include "kernels.h"
 
@@ -199,6 +201,9 @@ struct ddamg_handle {
     cplx<float>* P32 = nullptr;
     double *B64 = nullptr, *Dinv64 = nullptr;
     float *B32 = nullptr, *Dinv32 = nullptr;
+    uint4 *Bh = nullptr, *Dh = nullptr;  // half mode: FP16 fragments of D_c and D_ee^{-1}
+    cplx<__half>* P16 = nullptr;          // half mode: FP16 interpolation
+    CoarseTC tc{};
     int* d_flag = nullptr;
     // workspaces
     Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[5];
@@ -213,6 +218,7 @@ struct ddamg_handle {
     std::vector<cudaEvent_t> ev_pool;
 
     bool single() const { return p.precision != DDAMG_PREC_DOUBLE; }
+    bool half() const { return p.precision == DDAMG_PREC_HALF; }
 };
 
 namespace ddamg {
@@ -496,14 +502,46 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
 template <typename T>
 static int restrict_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) {
     Level<T> L = level<T>(h);
-    Prof pr(h, PF_RESTRICT, (double)h->V * (12.0 * h->N + 12.0 * nrhs) * 2 * sizeof(T));
+    const double pb = h->half() ? 2.0 : sizeof(T);
+    Prof pr(h, PF_RESTRICT, (double)h->V * (12.0 * h->N * 2 * pb + 12.0 * nrhs * 2 * sizeof(T)));
+    if (std::is_same<T, float>::value && h->half())
+        return launch_restrict<float, __half>(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in),
+                                              reinterpret_cast<cplx<float>*>(out), nrhs, h->stream);
     return launch_restrict<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
 }
 template <typename T>
 static int prolong_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) {
     Level<T> L = level<T>(h);
-    Prof pr(h, PF_PROLONG, (double)h->V * (12.0 * h->N + 12.0 * nrhs) * 2 * sizeof(T));
+    const double pb = h->half() ? 2.0 : sizeof(T);
+    Prof pr(h, PF_PROLONG, (double)h->V * (12.0 * h->N * 2 * pb + 12.0 * nrhs * 2 * sizeof(T)));
+    if (std::is_same<T, float>::value && h->half())
+        return launch_prolong<float, __half>(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in),
+                                             reinterpret_cast<cplx<float>*>(out), nrhs, h->stream);
     return launch_prolong<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
+}
+
+// coarse stencil dispatch: FP16 tensor-core storage in half mode, CUDA cores otherwise
+template <typename T>
+static int c_even(ddamg_handle* h, const cplx<T>* b_e, size_t b_rs, const cplx<T>* x_o, size_t x_rs, T beta, cplx<T>* out_e,
+                  size_t o_rs, int nrhs) {
+    if (std::is_same<T, float>::value && h->half())
+        return tc_coarse_even(h->tc, reinterpret_cast<const cplx<float>*>(b_e), b_rs, reinterpret_cast<const cplx<float>*>(x_o), x_rs,
+                              (float)beta, reinterpret_cast<cplx<float>*>(out_e), o_rs, nrhs, h->stream);
+    return launch_coarse_even<T, T>(level<T>(h).cop, b_e, b_rs, x_o, x_rs, beta, out_e, o_rs, nrhs, h->stream);
+}
+template <typename T>
+static int c_odd(ddamg_handle* h, const cplx<T>* x_o, size_t x_rs, const cplx<T>* t_e, size_t t_rs, int use_diag, cplx<T>* out_o,
+                 size_t o_rs, int nrhs) {
+    if (std::is_same<T, float>::value && h->half())
+        return tc_coarse_odd(h->tc, reinterpret_cast<const cplx<float>*>(x_o), x_rs, reinterpret_cast<const cplx<float>*>(t_e), t_rs,
+                             use_diag, reinterpret_cast<cplx<float>*>(out_o), o_rs, nrhs, h->stream);
+    return launch_coarse_odd<T, T>(level<T>(h).cop, x_o, x_rs, t_e, t_rs, use_diag, out_o, o_rs, nrhs, h->stream);
+}
+template <typename T>
+static int c_full(ddamg_handle* h, const cplx<T>* x, cplx<T>* y, int nrhs) {
+    if (std::is_same<T, float>::value && h->half())
+        return tc_coarse_full(h->tc, reinterpret_cast<const cplx<float>*>(x), reinterpret_cast<cplx<float>*>(y), nrhs, h->stream);
+    return launch_coarse_full<T, T>(level<T>(h).cop, x, y, nrhs, h->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -726,15 +764,15 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     cplx<T>* w = h->ws_coarse[3].as<cplx<T>>();
     cplx<T>* basis = h->ws_coarse[4].as<cplx<T>>();
     Level<T> L = level<T>(h);
-    const double sbytes = (double)h->NB * 9 * nc * nc * sizeof(cplx<T>);
+    const double sbytes = (double)h->NB * 9 * nc * nc * (h->half() && sizeof(T) == 4 ? 4.0 : sizeof(cplx<T>));
     const double vbytes = 2.0 * hn * nrhs * sizeof(cplx<T>);  // one half vector in, one out
     {
         Prof pr(h, PF_COARSE, sbytes / 18 + vbytes);
-        DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, nullptr, 0, T(0), te, hn, nrhs, st)));
+        DD_TRY(c_even<T>(h, bc, full, nullptr, 0, T(0), te, hn, nrhs));
     }
     {
         Prof pr(h, PF_COARSE, sbytes * 4 / 9 + 1.5 * vbytes);
-        DD_TRY((launch_coarse_odd<T, T>(L.cop, bc + hn, full, te, hn, 0, bp, hn, nrhs, st)));
+        DD_TRY(c_odd<T>(h, bc + hn, full, te, hn, 0, bp, hn, nrhs));
     }
     KrylovProblem<T, T, T> P;
     P.n = hn;
@@ -743,10 +781,10 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     P.A = [&](const cplx<T>* v, cplx<T>* out) -> int {
         {
             Prof pr(h, PF_COARSE, sbytes / 2 + vbytes);
-            DD_TRY((launch_coarse_even<T, T>(L.cop, nullptr, 0, v, hn, T(1), te, hn, nrhs, st)));
+            DD_TRY(c_even<T>(h, nullptr, 0, v, hn, T(1), te, hn, nrhs));
         }
         Prof pr(h, PF_COARSE, sbytes / 2 + 1.5 * vbytes);
-        return launch_coarse_odd<T, T>(L.cop, v, hn, te, hn, 1, out, hn, nrhs, st);
+        return c_odd<T>(h, v, hn, te, hn, 1, out, hn, nrhs);
     };
     P.Ax = P.A;
     P.b = bp;
@@ -769,7 +807,7 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     // back-substitution x_e = D_ee^{-1} (b_e - D_eo x_o); x_o into the odd half
     {
         Prof pr(h, PF_COARSE, sbytes / 2 + 1.5 * vbytes);
-        DD_TRY((launch_coarse_even<T, T>(L.cop, bc, full, xo, hn, T(-1), xc, full, nrhs, st)));
+        DD_TRY(c_even<T>(h, bc, full, xo, hn, T(-1), xc, full, nrhs));
     }
     DD_CUDA(cudaMemcpy2DAsync(xc + hn, full * sizeof(cplx<T>), xo, hn * sizeof(cplx<T>), hn * sizeof(cplx<T>), nrhs,
                               cudaMemcpyDeviceToDevice, st));
@@ -832,7 +870,10 @@ static int build_interpolation(ddamg_handle* h) {
         set_error("singular diagonal block of the coarse operator");
         return DDAMG_ERR_RANK;
     }
-    if (h->single()) {
+    if (h->half()) {
+        DD_TRY(convert_to_half(reinterpret_cast<const double*>(h->P64), h->P16, 2 * fld * N, st));
+        DD_TRY(pack_coarse_tc(h->B64, h->Dinv64, h->Bh, h->Dh, h->NB, nc, st));
+    } else if (h->single()) {
         DD_TRY((convert<float, double>(reinterpret_cast<const double*>(h->P64), reinterpret_cast<float*>(h->P32), 2 * fld * N, st)));
         DD_TRY((convert<float, double>(h->B64, h->B32, (size_t)h->NB * 9 * nc * nc * 2, st)));
         DD_TRY((convert<float, double>(h->Dinv64, h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2, st)));
@@ -1065,9 +1106,22 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
         return fail(rc);
     if (h->single()) {
         if ((rc = dalloc_n(&h->U32, V * 36)) || (rc = dalloc_n(&h->clov32, V * 72)) || (rc = dalloc_n(&h->clovinv32, V * 72)) ||
-            (rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
-            (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)) || (rc = dalloc_n(&h->Udw, V * 36)) ||
-            (rc = dalloc_n(&h->clovdw, V * 72)))
+            (rc = dalloc_n(&h->Udw, V * 36)) || (rc = dalloc_n(&h->clovdw, V * 72)))
+            return fail(rc);
+    }
+    if (h->half()) {
+        int Mt, Kta, Kth, Ktd;
+        if (tc_dims((int)nc, &Mt, &Kta, &Kth, &Ktd)) {
+            set_error("half precision needs n_vec divisible by 4");
+            return fail(DDAMG_ERR_INVALID_ARG);
+        }
+        if ((rc = dalloc_n(&h->Bh, (size_t)h->NB * Mt * Kta * 32)) || (rc = dalloc_n(&h->Dh, (size_t)(h->NB / 2) * Mt * Ktd * 32)) ||
+            (rc = dalloc_n(&h->P16, V * 12 * N)))
+            return fail(rc);
+        h->tc = CoarseTC{h->Bh, h->Dh, h->d_bnbr, h->NB, (int)nc, Mt, Kta, Kth, Ktd};
+    } else if (h->single()) {
+        if ((rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
+            (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)))
             return fail(rc);
     }
     // gauge field -> internal order, clover term and inverses
@@ -1388,7 +1442,7 @@ static int apply_Dc_T(ddamg_handle* h, const double* in, double* out, int n_rhs)
     Level<T> L = level<T>(h);
     {
         Prof pr(h, PF_COARSE, (double)h->NB * 9 * h->nc * h->nc * sizeof(cplx<T>));
-        DD_TRY((launch_coarse_full<T, T>(L.cop, a, o, n_rhs, h->stream)));
+        DD_TRY(c_full<T>(h, a, o, n_rhs));
     }
     return coarse_out<T>(h, o, out, n_rhs);
 }
@@ -1582,6 +1636,9 @@ int ddamg_destroy(ddamg_handle* h) {
     dfree(h->Dinv32);
     dfree(h->Udw);
     dfree(h->clovdw);
+    dfree(h->Bh);
+    dfree(h->Dh);
+    dfree(h->P16);
     dfree(h->d_flag);
     for (auto& s : h->ws_fine) s.release();
     for (auto& s : h->ws_coarse) s.release();

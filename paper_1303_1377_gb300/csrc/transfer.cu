@@ -5,6 +5,8 @@
 // P is stored as N fine spinor fields P_j [N][12][V] (internal order): column
 // (c, h, j) of P is P_j restricted to block c and spins {2h, 2h+1}.
 // Coarse vectors: cplx[nrhs][NB][2N], component h*N + j.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "dirac.cuh"
 
@@ -116,6 +118,10 @@ int launch_prolong(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, c
 template int launch_restrict<double, double>(const Geom&, const cplx<double>*, int, const cplx<double>*, cplx<double>*, int,
                                              cudaStream_t);
 template int launch_restrict<float, float>(const Geom&, const cplx<float>*, int, const cplx<float>*, cplx<float>*, int,
+                                           cudaStream_t);
+template int launch_restrict<float, __half>(const Geom&, const cplx<__half>*, int, const cplx<float>*, cplx<float>*, int,
+                                            cudaStream_t);
+template int launch_prolong<float, __half>(const Geom&, const cplx<__half>*, int, const cplx<float>*, cplx<float>*, int,
                                            cudaStream_t);
 template int launch_prolong<double, double>(const Geom&, const cplx<double>*, int, const cplx<double>*, cplx<double>*, int,
                                             cudaStream_t);

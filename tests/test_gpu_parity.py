@@ -141,7 +141,23 @@ def test_vcycle_fixed_coarse_iterations(name, dd):
         assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-4
 
 
-@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE"])
+def test_half_precision_operators(dd):
+    """FP16 storage of D_c, D_ee^{-1} and P with FP32 accumulation (tensor cores): errors against the
+    FP64 oracle stay at the FP16 rounding level (stated tolerance 4e-3 relative to the field maximum)."""
+    c = case("4^4/2^4", dd)
+    agg = Aggregation(c.D.lat, c.block, c.v)
+    Dc = CoarseOperator(c.D, agg)
+    cs = CoarseSolver(Dc, restart=30, tol=5e-2)
+    x = synth.gaussian_spinors(c.dims, 2, seed=105)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 5, seed=106)
+    with c.solver(dd.PREC_HALF) as s:
+        assert relerr(s.restrict(x), np.stack([agg.restrict(x[r]) for r in range(2)])) < 4e-3
+        assert relerr(s.prolong(e), np.stack([agg.prolong(e[r]) for r in range(5)])) < 4e-3
+        assert relerr(s.apply_Dc(e), np.stack([Dc.apply(e[r]) for r in range(5)])) < 4e-3
+        assert relerr(s.coarse_solve(e, fixed_iters=6), np.stack([cs.solve(e[r], fixed_iters=6) for r in range(5)])) < 2e-2
+
+
+@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
 def test_solve_matches_oracle(prec, dd):
     """Oracle setup (Algorithm 2) -> same vectors on the GPU -> FGMRES solves agree."""
     c = case("4^4/2^4", dd)
@@ -159,7 +175,7 @@ def test_solve_matches_oracle(prec, dd):
         assert st[q]["rel_residual"] <= 1e-10
 
 
-@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE"])
+@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
 def test_gpu_setup_solve_8x8x8x8(prec, dd):
     """The 8^4 workload (aggregates 4^4, N = 20, nu = 3): GPU adaptive setup + solve;
     the returned solution has FP64 relative residual <= 1e-10 under the oracle's D."""

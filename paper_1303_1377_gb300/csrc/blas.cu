@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kDotThreads) multidot_kernel(const cplx<Ta>* _
 
 // stage 2: out[i * ostride_i + r] = sum over the ctas of rhs r
 __global__ void multidot_finish(const double* __restrict__ partial, int k, int nrhs, int ctas_per_rhs,
-                                cplx<double>* __restrict__ out, int ostride_i) {
+                                cplx<double>* __restrict__ out, int ostride_i, const int* __restrict__ run_flag = nullptr) {
+    if (run_flag && !*run_flag) return;
     int q = blockIdx.x * blockDim.x + threadIdx.x;  // q = r * k + i
     if (q >= nrhs * k) return;
     int r = q / k, i = q % k;
@@ -338,7 +339,9 @@ __device__ __forceinline__ void st4(cplx<dwf>* p, const cdw& a) {
 template <int KB>
 __global__ void __launch_bounds__(kDotThreads) multidot_dw_kernel(const cplx<dwf>* __restrict__ A, size_t istride, size_t arstride, int k,
                                                                   const cplx<dwf>* __restrict__ w, size_t wrstride, size_t n, int nrhs,
-                                                                  int ctas_per_rhs, double* __restrict__ partial) {
+                                                                  int ctas_per_rhs, double* __restrict__ partial,
+                                                                  const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
     const int r = blockIdx.x % nrhs;
     const int part = blockIdx.x / nrhs;
     const cplx<dwf>* Ar = A + r * arstride;
@@ -374,9 +377,8 @@ __global__ void __launch_bounds__(kDotThreads) multidot_dw_kernel(const cplx<dwf
     }
 }
 
-template <>
-int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n,
-                       int nrhs, cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st) {
+int multidot_dw(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n, int nrhs,
+                cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st) {
     int off = 0;
     while (off < k) {
         int kk = k - off;
@@ -387,25 +389,32 @@ int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int 
         if (ctas > target) ctas = target;
         const cplx<dwf>* Ab = A + off * istride;
         if (kk <= 1)
-            multidot_dw_kernel<1><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+            multidot_dw_kernel<1><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch, run_flag);
         else if (kk <= 4)
-            multidot_dw_kernel<4><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+            multidot_dw_kernel<4><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch, run_flag);
         else if (kk <= 8)
-            multidot_dw_kernel<8><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+            multidot_dw_kernel<8><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch, run_flag);
         else
-            multidot_dw_kernel<16><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch);
+            multidot_dw_kernel<16><<<ctas * nrhs, kDotThreads, 0, st>>>(Ab, istride, arstride, kk, w, wrstride, n, nrhs, ctas, scratch, run_flag);
         DD_CHECK_LAUNCH();
         multidot_finish<<<ceil_div((long long)nrhs * kk, 128), 128, 0, st>>>(scratch, kk, nrhs, ctas, out + (size_t)off * ostride_i,
-                                                                          ostride_i);
+                                                                          ostride_i, run_flag);
         DD_CHECK_LAUNCH();
         off += kk;
     }
     return 0;
 }
 
+template <>
+int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n,
+                       int nrhs, cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st) {
+    return multidot_dw(A, istride, arstride, k, w, wrstride, n, nrhs, out, ostride_i, scratch, nullptr, st);
+}
+
 // coefficients alpha * coef[i][r] (FP64 complex) -> double-word pairs
 __global__ void coef_to_dw_kernel(const cplx<double>* __restrict__ coef, int cstride_i, int k, int nrhs, double alpha,
-                                  float4* __restrict__ out) {
+                                  float4* __restrict__ out, const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= k * nrhs) return;
     int i = q / nrhs, r = q % nrhs;
@@ -435,12 +444,93 @@ __global__ void lincomb_dw_kernel(cplx<dwf>* __restrict__ out, size_t ors, int b
 
 int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
                int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st) {
-    coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch);
+    coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch, nullptr);
     DD_CHECK_LAUNCH();
     long long tot = (long long)n * nrhs;
     int blocks = ceil_div(tot, 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     lincomb_dw_kernel<1><<<blocks, 256, 0, st>>>(out, ors, beta1, A, istride, ars, k, coef_scratch, n, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// w[r] += sum_i cdw[i][r] * A_i[r] in place, with ||w[r]||^2 of the result accumulated
+// per CTA (partial[cta], one rhs per CTA); skipped entirely when *run_flag == 0.
+constexpr int kAxpyThreads = 256;
+__global__ void __launch_bounds__(kAxpyThreads) axpy_norm_dw_kernel(cplx<dwf>* __restrict__ wv, const cplx<dwf>* __restrict__ A,
+                                                                    size_t istride, size_t rstride, int k, const float4* __restrict__ cdwv,
+                                                                    size_t n, int nrhs, int ctas_per_rhs, double* __restrict__ partial,
+                                                                    const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
+    const int r = blockIdx.x % nrhs;
+    const int part = blockIdx.x / nrhs;
+    cplx<dwf>* wr = wv + r * rstride;
+    const cplx<dwf>* Ar = A + r * rstride;
+    double nrm = 0.0;
+    const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
+    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n; e += stride) {
+        cdw acc = ld4(wr + e);
+        for (int i = 0; i < k; ++i) {
+            float4 c = __ldg(cdwv + (size_t)i * nrhs + r);
+            cdw cc = {{c.x, c.y}, {c.z, c.w}};
+            cdw_mac(acc, cc, ld4(Ar + i * istride + e));
+        }
+        st4(wr + e, acc);
+        double re = dw_to_double(acc.re), im = dw_to_double(acc.im);
+        nrm = fma(re, re, fma(im, im, nrm));
+    }
+    __shared__ double red[kAxpyThreads / 32];
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int q = 0; q < kAxpyThreads / 32; ++q) s += red[q];
+        partial[blockIdx.x * 2] = s;
+        partial[blockIdx.x * 2 + 1] = 0.0;
+    }
+}
+
+int axpy_norm_dw(cplx<dwf>* w, const cplx<dwf>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
+                 size_t n, int nrhs, double alpha, float4* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                 cudaStream_t st) {
+    coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch, run_flag);
+    DD_CHECK_LAUNCH();
+    int ctas = (int)((n + kAxpyThreads - 1) / kAxpyThreads);
+    int target = 1216 / nrhs;
+    if (target < 1) target = 1;
+    if (ctas > target) ctas = target;
+    axpy_norm_dw_kernel<<<ctas * nrhs, kAxpyThreads, 0, st>>>(w, A, istride, rstride, k, coef_scratch, n, nrhs, ctas, scratch, run_flag);
+    DD_CHECK_LAUNCH();
+    multidot_finish<<<ceil_div((long long)nrhs, 128), 128, 0, st>>>(scratch, 1, nrhs, ctas, norm_out, nrhs, run_flag);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// Reorthogonalisation test of classical Gram-Schmidt (the DGKS criterion with
+// threshold eta): request a second pass when, for any active right-hand side,
+// ||w after||^2 < eta^2 ||w before||^2.
+__global__ void dgks_kernel(const cplx<double>* __restrict__ before, const cplx<double>* __restrict__ after,
+                            const int* __restrict__ active, int nrhs, double eta2, int* __restrict__ flag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int f = 0;
+        for (int r = 0; r < nrhs; ++r)
+            if (active[r] && after[r].re < eta2 * before[r].re) f = 1;
+        *flag = f;
+    }
+}
+int dgks(const cplx<double>* before, const cplx<double>* after, const int* active, int nrhs, double eta, int* flag, cudaStream_t st) {
+    dgks_kernel<<<1, 32, 0, st>>>(before, after, active, nrhs, eta * eta, flag);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+__global__ void add_columns_flag_kernel(cplx<double>* __restrict__ a, const cplx<double>* __restrict__ b, int n, const int* __restrict__ flag) {
+    if (!*flag) return;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) a[q] = a[q] + b[q];
+}
+int add_columns_flag(cplx<double>* a, const cplx<double>* b, int n, const int* flag, cudaStream_t st) {
+    add_columns_flag_kernel<<<ceil_div(n, 128), 128, 0, st>>>(a, b, n, flag);
     DD_CHECK_LAUNCH();
     return 0;
 }

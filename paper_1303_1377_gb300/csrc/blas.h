@@ -32,6 +32,13 @@ int add_columns(cplx<double>* a, const cplx<double>* b, int n, cudaStream_t st);
 template <>
 int multidot<dwf, dwf>(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n,
                        int nrhs, cplx<double>* out, int ostride_i, double* scratch, cudaStream_t st);
+int multidot_dw(const cplx<dwf>* A, size_t istride, size_t arstride, int k, const cplx<dwf>* w, size_t wrstride, size_t n, int nrhs,
+                cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st);
+int axpy_norm_dw(cplx<dwf>* w, const cplx<dwf>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
+                 size_t n, int nrhs, double alpha, float4* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                 cudaStream_t st);
+int dgks(const cplx<double>* before, const cplx<double>* after, const int* active, int nrhs, double eta, int* flag, cudaStream_t st);
+int add_columns_flag(cplx<double>* a, const cplx<double>* b, int n, const int* flag, cudaStream_t st);
 int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
                int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st);
 int convert_d2dw(const double* in, cplx<dwf>* out, size_t nreal, cudaStream_t st);

@@ -18,6 +18,17 @@ template <> struct SpinB<1> { enum { c0 = 1, p0 = 2, c1 = 0, p1 = 0, hc0 = 1, hp
 template <> struct SpinB<2> { enum { c0 = 0, p0 = 1, c1 = 1, p1 = 3, hc0 = 0, hp0 = 3, hc1 = 1, hp1 = 1 }; };
 template <> struct SpinB<3> { enum { c0 = 0, p0 = 0, c1 = 1, p1 = 0, hc0 = 0, hp0 = 0, hc1 = 1, hp1 = 0 }; };
 
+// runtime form of SpinB (same entries), for rolled loops over the eight directions:
+// [mu][0..7] = c0, p0, c1, p1, hc0, hp0, hc1, hp1
+__constant__ unsigned char c_spinb[4][8] = {{1, 1, 0, 1, 1, 3, 0, 3}, {1, 2, 0, 0, 1, 0, 0, 2}, {0, 1, 1, 3, 0, 3, 1, 1},
+                                             {0, 0, 1, 0, 0, 0, 1, 0}};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> ipow_rt(cplx<T> a, int p) {
+    cplx<T> b = (p & 1) ? mk(-a.im, a.re) : a;
+    return (p & 2) ? mk(-b.re, -b.im) : b;
+}
+
 template <typename T>
 struct Spinor {
     cplx<T> v[12];
@@ -81,6 +92,46 @@ __device__ __forceinline__ void hop_acc(Spinor<T>& acc, const Spinor<T>& pn, con
             acc.v[2 * 3 + c] = acc.v[2 * 3 + c] + l0;
             acc.v[3 * 3 + c] = acc.v[3 * 3 + c] + l1;
         }
+    }
+}
+
+// hop_acc with the direction mu and the orientation given at run time
+template <typename T>
+__device__ __forceinline__ void hop_acc_rt(Spinor<T>& acc, const Spinor<T>& pn, const cplx<T> (&W)[9], int mu, bool fwd) {
+    const int c0 = c_spinb[mu][0], p0 = c_spinb[mu][1], c1 = c_spinb[mu][2], p1 = c_spinb[mu][3];
+    const int hc0 = c_spinb[mu][4], hp0 = c_spinb[mu][5], hc1 = c_spinb[mu][6], hp1 = c_spinb[mu][7];
+    const T sg = fwd ? T(-1) : T(1);
+    cplx<T> h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cplx<T> l2 = pn.v[2 * 3 + c], l3 = pn.v[3 * 3 + c];
+        cplx<T> b0 = ipow_rt(c0 ? l3 : l2, p0);
+        cplx<T> b1 = ipow_rt(c1 ? l3 : l2, p1);
+        h[0][c] = pn.v[0 * 3 + c] + sg * b0;
+        h[1][c] = pn.v[1 * 3 + c] + sg * b1;
+    }
+    cplx<T> g[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cplx<T> t = czero<T>();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                cplx<T> wf = W[a * 3 + b], wb = conj(W[b * 3 + a]);
+                cmac(t, fwd ? wf : wb, h[s][b]);
+            }
+            g[s][a] = t;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc.v[0 * 3 + c] = acc.v[0 * 3 + c] + g[0][c];
+        acc.v[1 * 3 + c] = acc.v[1 * 3 + c] + g[1][c];
+        cplx<T> l0 = ipow_rt(hc0 ? g[1][c] : g[0][c], hp0);
+        cplx<T> l1 = ipow_rt(hc1 ? g[1][c] : g[0][c], hp1);
+        acc.v[2 * 3 + c] = acc.v[2 * 3 + c] + sg * l0;
+        acc.v[3 * 3 + c] = acc.v[3 * 3 + c] + sg * l1;
     }
 }
 

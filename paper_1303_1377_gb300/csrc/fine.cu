@@ -459,27 +459,30 @@ __device__ __forceinline__ cdw ld_cdw(const float4* p) {
     return {{v.x, v.y}, {v.z, v.w}};
 }
 
-template <int MU, bool FWD>
-__device__ __forceinline__ void dw_hop(cdw (&acc)[12], const cplx<float>* __restrict__ in, int V, int nb, const float4* __restrict__ U,
-                                       int link_site) {
-    using B = SpinB<MU>;
-    cdw psi[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        cplx<float> v = in[(size_t)k * V + nb];
-        psi[k] = {{v.re, 0.f}, {v.im, 0.f}};
-    }
+__device__ __forceinline__ cdw cdw_ipow_rt(const cdw& a, int p) {
+    cdw b = (p & 1) ? cdw{dw_neg(a.im), a.re} : a;
+    return (p & 2) ? cdw{dw_neg(b.re), dw_neg(b.im)} : b;
+}
+
+// one hop of D (direction mu, orientation fwd, given at run time) in double-word arithmetic
+__device__ __noinline__ void dw_hop_rt(cdw (&acc)[12], const cplx<float>* __restrict__ in, int V, int nb, const float4* __restrict__ U,
+                                       int link_site, int mu, bool fwd) {
+    const int c0 = c_spinb[mu][0], p0 = c_spinb[mu][1], c1 = c_spinb[mu][2], p1 = c_spinb[mu][3];
+    const int hc0 = c_spinb[mu][4], hp0 = c_spinb[mu][5], hc1 = c_spinb[mu][6], hp1 = c_spinb[mu][7];
     cdw h[2][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        cdw b0 = cdw_ipow<B::p0>(psi[(2 + B::c0) * 3 + c]);
-        cdw b1 = cdw_ipow<B::p1>(psi[(2 + B::c1) * 3 + c]);
-        h[0][c] = FWD ? cdw_sub(psi[0 * 3 + c], b0) : cdw_add(psi[0 * 3 + c], b0);
-        h[1][c] = FWD ? cdw_sub(psi[1 * 3 + c], b1) : cdw_add(psi[1 * 3 + c], b1);
+        cplx<float> u0 = in[(size_t)(0 * 3 + c) * V + nb], u1 = in[(size_t)(1 * 3 + c) * V + nb];
+        cplx<float> l2 = in[(size_t)(2 * 3 + c) * V + nb], l3 = in[(size_t)(3 * 3 + c) * V + nb];
+        cdw b0 = cdw_ipow_rt(c0 ? cdw{{l3.re, 0.f}, {l3.im, 0.f}} : cdw{{l2.re, 0.f}, {l2.im, 0.f}}, p0);
+        cdw b1 = cdw_ipow_rt(c1 ? cdw{{l3.re, 0.f}, {l3.im, 0.f}} : cdw{{l2.re, 0.f}, {l2.im, 0.f}}, p1);
+        cdw a0 = {{u0.re, 0.f}, {u0.im, 0.f}}, a1 = {{u1.re, 0.f}, {u1.im, 0.f}};
+        h[0][c] = fwd ? cdw_sub(a0, b0) : cdw_add(a0, b0);
+        h[1][c] = fwd ? cdw_sub(a1, b1) : cdw_add(a1, b1);
     }
     cdw W[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) W[q] = ld_cdw(U + (size_t)(MU * 9 + q) * V + link_site);
+    for (int q = 0; q < 9; ++q) W[q] = ld_cdw(U + (size_t)(mu * 9 + q) * V + link_site);
     cdw gv[2][3];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -488,7 +491,7 @@ __device__ __forceinline__ void dw_hop(cdw (&acc)[12], const cplx<float>* __rest
             cdw t = cdw_zero();
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                if (FWD) cdw_mac(t, W[a * 3 + b], h[s][b]);
+                if (fwd) cdw_mac(t, W[a * 3 + b], h[s][b]);
                 else cdw_mac_conj(t, W[b * 3 + a], h[s][b]);
             }
             t.re = dw_norm(t.re);
@@ -497,22 +500,13 @@ __device__ __forceinline__ void dw_hop(cdw (&acc)[12], const cplx<float>* __rest
             acc[s * 3 + a] = cdw_add(acc[s * 3 + a], t);
         }
     }
-    // lower spins: -s B^H g  (forward: -B^H g, backward: +B^H g)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        cdw l0 = cdw_ipow<B::hp0>(gv[B::hc0][c]);
-        cdw l1 = cdw_ipow<B::hp1>(gv[B::hc1][c]);
-        acc[2 * 3 + c] = FWD ? cdw_sub(acc[2 * 3 + c], l0) : cdw_add(acc[2 * 3 + c], l0);
-        acc[3 * 3 + c] = FWD ? cdw_sub(acc[3 * 3 + c], l1) : cdw_add(acc[3 * 3 + c], l1);
+        cdw l0 = cdw_ipow_rt(hc0 ? gv[1][c] : gv[0][c], hp0);
+        cdw l1 = cdw_ipow_rt(hc1 ? gv[1][c] : gv[0][c], hp1);
+        acc[2 * 3 + c] = fwd ? cdw_sub(acc[2 * 3 + c], l0) : cdw_add(acc[2 * 3 + c], l0);
+        acc[3 * 3 + c] = fwd ? cdw_sub(acc[3 * 3 + c], l1) : cdw_add(acc[3 * 3 + c], l1);
     }
-}
-
-template <int MU>
-__device__ __forceinline__ void dw_hop_pair(const Geom& g, cdw (&acc)[12], const cplx<float>* __restrict__ in, const float4* __restrict__ U,
-                                            int i) {
-    dw_hop<MU, true>(acc, in, g.V, fine_nbr(g, i, 2 * MU), U, i);
-    int bk = fine_nbr(g, i, 2 * MU + 1);
-    dw_hop<MU, false>(acc, in, g.V, bk, U, bk);
 }
 
 }  // namespace
@@ -528,10 +522,12 @@ __global__ void __launch_bounds__(128) dslash_dw_kernel(Geom g, const float4* __
     cdw acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = cdw_zero();
-    dw_hop_pair<0>(g, acc, inr, U, i);
-    dw_hop_pair<1>(g, acc, inr, U, i);
-    dw_hop_pair<2>(g, acc, inr, U, i);
-    dw_hop_pair<3>(g, acc, inr, U, i);
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const int nb = fine_nbr(g, i, d);
+        const bool fwd = (d & 1) == 0;
+        dw_hop_rt(acc, inr, g.V, nb, U, fwd ? i : nb, d >> 1, fwd);
+    }
     // site term: y = A x with two packed hermitian 6x6 blocks (double-word entries), x FP32
     cdw y[12];
 #pragma unroll

@@ -103,6 +103,8 @@ struct KrylovBufs {
     cplx<double>* nrm = nullptr;    // [nrhs]
     cplx<double>* ones = nullptr;   // [nrhs] = 1
     float4* coefdw = nullptr;       // [(m+2)][nrhs] double-word coefficients
+    cplx<double>* nbefore = nullptr;  // [nrhs] ||w||^2 before orthogonalisation
+    int* dflag = nullptr;             // device-side "second Gram-Schmidt pass" decision
     double* dscr = nullptr;         // multidot scratch
     int* h_active = nullptr;        // pinned copy of active flags
     int* h_steps = nullptr;
@@ -132,6 +134,8 @@ struct KrylovBufs {
         DD_TRY(dalloc_n(&nrm, nr));
         DD_TRY(dalloc_n(&ones, nr));
         DD_TRY(dalloc_n(&coefdw, (size_t)(mm + 2) * nr));
+        DD_TRY(dalloc_n(&nbefore, nr));
+        DD_TRY(dalloc_n(&dflag, 1));
         {
             std::vector<cplx<double>> one(nr, mk(1.0, 0.0));
             DD_CUDA(cudaMemcpy(ones, one.data(), sizeof(cplx<double>) * nr, cudaMemcpyHostToDevice));
@@ -161,6 +165,8 @@ struct KrylovBufs {
         dfree(nrm);
         dfree(ones);
         dfree(coefdw);
+        dfree(nbefore);
+        dfree(dflag);
         dfree(dscr);
         if (h_active) cudaFreeHost(h_active);
         if (h_steps) cudaFreeHost(h_steps);
@@ -682,9 +688,33 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             } else {
                 zk = reinterpret_cast<const cplx<TZ>*>(Vk);
             }
-            DD_TRY(P.A(zk, P.w));
-            // classical Gram-Schmidt (twice when reorth)
-            {
+            if constexpr (std::is_same<TV, dwf>::value) {
+                // w is formed in the V_{k+1} slot; one multi-dot gives <V_i, w> (i <= k) and ||w||^2,
+                // the axpy kernel returns ||w'||^2, and the second classical Gram-Schmidt pass runs
+                // only when the first one cancelled more than 1 - eta of w (eta = 1e-3, decided on the
+                // device).  With the 48-bit double-word basis one pass leaves a non-orthogonality of
+                // about 1e-14 ||w|| / ||w'||, far below what a 1e-10 solve needs; the FP64 true residual
+                // at every restart certifies convergence whatever the basis quality.
+                cplx<dwf>* wk = P.Vb + (size_t)(k + 1) * bstride;
+                DD_TRY(P.A(zk, wk));
+                const double vb = (double)sizeof(cplx<TV>) * n * nr;
+                Prof pr(h, PF_ORTHO, vb * (2 * (k + 1) + 6));
+                DD_TRY(multidot_dw(P.Vb, bstride, n, k + 2, wk, n, n, nr, kb.hcol, nr, kb.dscr, nullptr, st));
+                DD_CUDA(cudaMemcpyAsync(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToDevice, st));
+                DD_TRY(axpy_norm_dw(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, n, nr, -1.0, kb.coefdw, kb.dscr,
+                                    kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
+                if (P.reorth) {
+                    DD_TRY(dgks(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, s.active, nr, 1e-3, kb.dflag, st));
+                    DD_TRY(multidot_dw(P.Vb, bstride, n, k + 1, wk, n, n, nr, kb.hcol2, nr, kb.dscr, kb.dflag, st));
+                    DD_TRY(axpy_norm_dw(wk, P.Vb, bstride, n, k + 1, kb.hcol2, nr, n, nr, -1.0, kb.coefdw, kb.dscr,
+                                        kb.hcol + (size_t)(k + 1) * nr, kb.dflag, st));
+                    DD_TRY(add_columns_flag(kb.hcol, kb.hcol2, (k + 1) * nr, kb.dflag, st));
+                }
+                DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
+                DD_TRY(baxpy<TV>(kb, wk, false, wk, 0, 1, kb.scale, n, nr, 1.0, st));
+            } else {
+                DD_TRY(P.A(zk, P.w));
+                // classical Gram-Schmidt (twice when reorth)
                 const double vb = (double)sizeof(cplx<TV>) * n * nr;
                 Prof pr(h, PF_ORTHO, vb * ((k + 1) * (P.reorth ? 4 : 2) + 4));
                 DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol, st));

@@ -242,6 +242,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     n_launch0 = ddamg.launch_count()
+    launches_before_timed = n_launch0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -308,6 +309,9 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches,
+        "gpu_launches_before_timed": launches_before_timed,
+        "solve_seconds_host": [s["solve_seconds"] for s in stats[-1]][:1],
+        "coarse_seconds_host": [s["coarse_seconds"] for s in stats[-1]][:1],
         "e2e": e2e,
         "fgmres_iterations": iters,
         "coarse_iterations_per_solve": stats[-1][0]["coarse_iterations"],

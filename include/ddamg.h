@@ -162,6 +162,26 @@ int ddamg_prolong(ddamg_handle* h, const double* coarse_in, double* fine_out, in
 /* out = D_c in for coarse vectors (Sec. 3.2), V-cycle precision arithmetic. */
 int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs);
 
+/* out = D_c in, like ddamg_apply_Dc, for callers that must not have this library
+ * allocate device memory during the call: a code whose memory pool already owns
+ * almost all of the GPU (PyTorch's caching allocator, a serving process with a
+ * fixed budget), or a latency-critical loop that cannot pay the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this is
+ * a deployment variant of the coarse-operator application.
+ * in, out: DEVICE pointers (coarse-vector layout above, n_rhs vectors, FP64);
+ *   host pointers are rejected with DDAMG_ERR_INVALID_ARG.
+ * Working memory: a fixed 16 MiB device array inside the library (every GPU that
+ *   loads the library holds it until the process exits).  n_rhs is limited to
+ *   16 MiB / (2 * coarse sites * 2N * bytes per complex number of the V-cycle
+ *   precision, 8 single / 16 double); larger n_rhs fails with
+ *   DDAMG_ERR_INVALID_ARG and a message giving the limit.  No cudaMalloc,
+ *   cudaFree or other allocating call is made.
+ * The first call on a device looks the array up with cudaGetSymbolAddress (with
+ *   that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; calls that
+ *   overlap on the GPU (other host threads, other streams) race on it. */
+int ddamg_apply_Dc_noalloc(ddamg_handle* h, const double* in, double* out, int n_rhs);
+
 /* Copy the assembled coarse stencil (FP64 as assembled) into out:
  * [coarse site][direction d][row][col] complex with d = 0 self, 1 + 2 mu (+mu),
  * 2 + 2 mu (-mu), rows/cols in the coarse-vector component order. */

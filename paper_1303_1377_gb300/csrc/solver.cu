@@ -1477,6 +1477,43 @@ static int apply_Dc_T(ddamg_handle* h, const double* in, double* out, int n_rhs)
     return coarse_out<T>(h, o, out, n_rhs);
 }
 
+namespace ddamg {
+// D_c applied to caller-owned device vectors, with the two internal-layout staging
+// buffers carved out of caller-provided device scratch: this path allocates nothing.
+template <typename T>
+static int apply_Dc_scratch_T(ddamg_handle* h, const double* in, double* out, int n_rhs, void* scratch, size_t scratch_bytes) {
+    const size_t cn = (size_t)h->NB * h->nc;
+    const size_t per_rhs = 2 * cn * sizeof(cplx<T>);
+    if (per_rhs * (size_t)n_rhs > scratch_bytes) {
+        set_error("ddamg_apply_Dc_noalloc: n_rhs " + std::to_string(n_rhs) + " needs " + std::to_string(per_rhs * n_rhs) +
+                  " bytes of scratch, the fixed scratch holds " + std::to_string(scratch_bytes) + " (at most " +
+                  std::to_string(scratch_bytes / per_rhs) + " right-hand sides for this handle)");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    cplx<T>* a = reinterpret_cast<cplx<T>*>(scratch);
+    cplx<T>* o = a + cn * n_rhs;
+    DD_TRY((coarse_perm<T, double>(reinterpret_cast<const cplx<double>*>(in), a, h->d_clex_of, h->NB, h->nc, n_rhs, 1, h->stream)));
+    DD_TRY(c_full<T>(h, a, o, n_rhs));
+    DD_TRY((coarse_perm<double, T>(o, reinterpret_cast<cplx<double>*>(out), h->d_clex_of, h->NB, h->nc, n_rhs, 0, h->stream)));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    return 0;
+}
+
+int apply_Dc_into_scratch(ddamg_handle* h, const double* in, double* out, int n_rhs, void* scratch, size_t scratch_bytes) {
+    DD_TRY(check_ready(h));
+    if (!in || !out || n_rhs < 1 || !scratch) {
+        set_error("ddamg_apply_Dc_noalloc: null pointer or n_rhs < 1");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    if (!is_device_ptr(in) || !is_device_ptr(out)) {
+        set_error("ddamg_apply_Dc_noalloc: in and out must be device memory (host data would need staging buffers)");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    return h->single() ? apply_Dc_scratch_T<float>(h, in, out, n_rhs, scratch, scratch_bytes)
+                       : apply_Dc_scratch_T<double>(h, in, out, n_rhs, scratch, scratch_bytes);
+}
+}  // namespace ddamg
+
 extern "C" {
 int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs) {
     DD_TRY(check_ready(h));

@@ -108,6 +108,7 @@ def _load():
         "ddamg_restrict": (I, [P, P, P, I]),
         "ddamg_prolong": (I, [P, P, P, I]),
         "ddamg_apply_Dc": (I, [P, P, P, I]),
+        "ddamg_apply_Dc_noalloc": (I, [P, P, P, I]),
         "ddamg_get_coarse_stencil": (I, [P, P]),
         "ddamg_coarse_solve": (I, [P, P, P, I, I]),
         "ddamg_vcycle": (I, [P, P, P, I, I]),
@@ -299,6 +300,12 @@ class Solver:
 
     def apply_Dc(self, e):
         return self._coarse_op(lib.ddamg_apply_Dc, e)
+
+    def apply_Dc_noalloc(self, e_dev, out_dev):
+        """D_c e without any allocation in the library: e_dev, out_dev are device tensors
+        [n_rhs, n_coarse, 2N] complex128; the library's fixed scratch array is used."""
+        nr = 1 if e_dev.ndim == 2 else int(e_dev.shape[0])
+        return _check(lib.ddamg_apply_Dc_noalloc(self.h, _ptr(e_dev), _ptr(out_dev), nr), "ddamg_apply_Dc_noalloc")
 
     def coarse_solve(self, e, fixed_iters: int = 0):
         return self._coarse_op(lib.ddamg_coarse_solve, e, int(fixed_iters))

@@ -179,9 +179,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32x32x32x64", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="single", choices=["single", "half", "double"])
+    ap.add_argument("--precision", default="half", choices=["single", "half", "double"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain single-RHS FP64 comparison solve")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -320,12 +321,35 @@ def main():
         "gauge_generation_seconds": t_gauge,
         "kernel_profile_first_step": prof_all,
     }
+    solver.close()
+    del b, z
+    torch.cuda.empty_cache()
+    # the plain path: one right-hand side, every step of the solve in FP64 (same library)
+    if not args.no_plain and world == 1:
+        Up = synth.gauge_field(dims, w["eps"], w["seed"])
+        pp = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=ddamg.PREC_DOUBLE)
+        tps = time.perf_counter()
+        plain = ddamg.Solver(dims, Up, m0, C_SW, pp, setup=True)
+        t_plain_setup = time.perf_counter() - tps
+        del Up
+        b1 = torch.from_numpy(bh[:1]).to("cuda")
+        z1 = torch.zeros_like(b1)
+        plain.solve(b1, z1)  # warm-up
+        z1.zero_()
+        torch.cuda.synchronize()
+        tp0 = time.perf_counter()
+        _, st1, rc1 = plain.solve(b1, z1)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - tp0
+        line["plain_fp64_single_rhs"] = {"value": 1.0 / tp, "unit": "solves/s", "fgmres_iterations": st1[0]["iterations"],
+                                         "rel_residual": st1[0]["rel_residual"], "status": rc1, "setup_seconds": t_plain_setup,
+                                         "speedup_of_value": value / (1.0 / tp)}
+        plain.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         v, info = oracle_sample(w, m0, max(iters), seconds_budget=15.0)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": info["sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    solver.close()
     if dist:
         dist.destroy_process_group()
     return 0

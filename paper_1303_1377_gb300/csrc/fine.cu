@@ -163,23 +163,50 @@ __device__ __forceinline__ void block_reduce3(T& a, T& b, T& c, T* red) {
     }
 }
 
-template <typename T, int MINB>
-__global__ void __launch_bounds__(128, MINB) sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
-                                                               cplx<T>* __restrict__ z, int colour, int nrhs, int mr_steps) {
+// reduction over the HT threads of one slot (slots are whole warps)
+template <typename T>
+__device__ __forceinline__ void block_reduce3_slot(T& a, T& b, T& c, T* red, int HT) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const int w = (threadIdx.x % HT) >> 5, lane = threadIdx.x & 31, nw = HT >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
+    }
+    __syncthreads();
+    a = b = c = T(0);
+    for (int q = 0; q < nw; ++q) {
+        a += red[3 * q];
+        b += red[3 * q + 1];
+        c += red[3 * q + 2];
+    }
+}
+
+// R right-hand-side slots per CTA (R * HT threads, HT = Vb/2 rounded up to a warp):
+// the slots share the block's links and site terms through L1.
+template <typename T, int R>
+__global__ void __launch_bounds__(128 * R, 1) sap_colour_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
+                                                                cplx<T>* __restrict__ z, int colour, int nrhs, int mr_steps) {
     extern __shared__ unsigned char smem_raw[];
     const int H = g.Vb / 2;
-    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw);  // [12][H] even-site work vector
-    cplx<T>* SO = SE + 12 * H;                            // [12][H] odd-site work vector (rho, then x_o)
-    cplx<T>* SR = SO + 12 * H;                            // [12][H] r_e
-    T* red = reinterpret_cast<T*>(SR + 12 * H);           // reduction scratch
+    const int HT = blockDim.x / R;
+    const int slot = threadIdx.x / HT;
+    const int t = threadIdx.x % HT;
+    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)slot * 36 * H;  // [12][H] even-site work vector
+    cplx<T>* SO = SE + 12 * H;                                                   // [12][H] odd-site work vector (rho, then x_o)
+    cplx<T>* SR = SO + 12 * H;                                                   // [12][H] r_e
+    T* red = reinterpret_cast<T*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)R * 36 * H) + (size_t)slot * 3 * (HT / 32);
 
-    const int r = blockIdx.x % nrhs;
-    const int blk = colour * (g.NB / 2) + blockIdx.x / nrhs;
-    const int t = threadIdx.x;
-    const bool act = t < H;
+    const int nslots = (nrhs + R - 1) / R;
+    const int r = (blockIdx.x % nslots) * R + slot;
+    const int blk = colour * (g.NB / 2) + blockIdx.x / nslots;
+    const bool act = t < H && r < nrhs;
     const int le = t, lo = H + t;
     const int ie = blk * g.Vb + le, io = blk * g.Vb + lo;
-    const size_t off = (size_t)r * 12 * g.V;
+    const size_t off = (size_t)(r < nrhs ? r : 0) * 12 * g.V;
     const cplx<T>* b = bsrc + off;
     cplx<T>* zr = z + off;
 
@@ -236,7 +263,7 @@ __global__ void __launch_bounds__(128, MINB) sap_colour_kernel(Geom g, FineOp<T>
                 den += norm2(tmp.v[k]);
             }
         }
-        block_reduce3(num_re, num_im, den, red);
+        block_reduce3_slot(num_re, num_im, den, red, HT);
         cplx<T> alpha = czero<T>();
         if (den > tiny_normal<T>()) alpha = mk(num_re / den, num_im / den);
         if (act) {
@@ -268,19 +295,19 @@ __global__ void __launch_bounds__(128, MINB) sap_colour_kernel(Geom g, FineOp<T>
     }
 }
 
-template <typename T, int MINB>
-static int launch_sap_plain(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
-                            cudaStream_t st) {
+template <typename T, int R>
+static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                        cudaStream_t st) {
     const int H = g.Vb / 2;
     const int nt = ((H + 31) / 32) * 32;
-    size_t smem = 3 * 12 * (size_t)H * sizeof(cplx<T>) + 3 * 32 * sizeof(T);
+    size_t smem = (size_t)R * 36 * H * sizeof(cplx<T>) + (size_t)R * 3 * 32 * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(sap_colour_kernel<T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(sap_colour_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    long long nblk = (long long)(g.NB / 2) * nrhs;
-    sap_colour_kernel<T, MINB><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
+    sap_colour_kernel<T, R><<<(unsigned)nblk, R * nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
     DD_CHECK_LAUNCH();
     return 0;
 }
@@ -288,7 +315,9 @@ static int launch_sap_plain(const Geom& g, const FineOp<T>& op, const cplx<T>* b
 template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st) {
-    return launch_sap_plain<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
+    const int H = g.Vb / 2;
+    if (sizeof(T) == 4 && H <= 128 && nrhs >= 2) return launch_sap_r<T, 2>(g, op, b, z, colour, nrhs, mr_steps, st);
+    return launch_sap_r<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
 }
 template int launch_sap_colour<double>(const Geom&, const FineOp<double>&, const cplx<double>*, cplx<double>*, int, int, int,
                                        cudaStream_t);

@@ -191,6 +191,7 @@ def main():
     import torch
 
     from paper_1303_1377_gb300 import ddamg, synth
+    from paper_1303_1377_gb300.replicas import aggregate
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -261,11 +262,8 @@ def main():
     clk = clocks.stop()
     prof = solver.profile_read()
     solver.profile([])
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * nr * args.steps / (ms / 1e3)
+    # whole-job throughput: solves summed over the replicas / slowest replica's time
+    value, ms, _ = aggregate(ms, nr * args.steps, dist=dist, device="cuda")
     # residual check of the last solve, in FP64 through the library's D
     r = b - solver.apply_D(z)
     rel = (torch.linalg.vector_norm(r.reshape(nr, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nr, -1), dim=1)).max().item()
@@ -285,18 +283,30 @@ def main():
         nbytes = bh.nbytes
         e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
                "d2h_bytes_per_step": nbytes}
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: HBM-bound families against the measured copy bandwidth;
+    # families whose algorithmic flops per byte exceed the FP32 ridge against the FP32 FMA peak
+    # (152 SMs x 128 FP32 lanes x 2 flops x SM clock sampled during the timed region)
     peak, peak_kind = peaks()
-    d = prof.get(dominant, {"launches": 0, "total_ms": 0.0, "bytes": 0.0})
-    achieved = (d["bytes"] / d["launches"]) / (d["total_ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else 0.0
-    traffic = None
-    tr = json.load(open(WORKLOADS_JSON)).get("ncu_traffic", {}).get(f"{args.workload}/{args.precision}/{dominant}")
-    if tr:
-        traffic = tr
-    roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "launches": d["launches"], "avg_launch_us": 1e3 * d["total_ms"] / max(1, d["launches"]),
-            "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
-            "time_share_of_step": d["total_ms"] / ms if ms else None}
+    d = prof.get(dominant, {"launches": 0, "total_ms": 0.0, "bytes": 0.0, "flops": 0.0})
+    n_l = max(1, d["launches"])
+    sec = d["total_ms"] / n_l / 1e3 if d["launches"] else float("inf")
+    bytes_pl, flops_pl = d["bytes"] / n_l, d.get("flops", 0.0) / n_l
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    fp32_peak_tf = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ridge = fp32_peak_tf * 1e12 / (peak * 1e9)
+    traffic = json.load(open(WORKLOADS_JSON)).get("ncu_traffic", {}).get(f"{args.workload}/{args.precision}/{dominant}")
+    if flops_pl > 0 and flops_pl / bytes_pl > ridge:
+        ach = flops_pl / sec / 1e12
+        roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": fp32_peak_tf,
+                "peak_kind": f"FP32 FMA peak from unit counts at {sm_mhz:.0f} MHz (152 SM x 128 lanes x 2)", "unit": "TFLOP/s",
+                "frac": ach / fp32_peak_tf, "traffic": traffic, "hbm_achieved_gbs": bytes_pl / sec / 1e9, "hbm_peak_gbs": peak,
+                "arithmetic_intensity": flops_pl / bytes_pl, "ridge": ridge}
+    else:
+        ach = bytes_pl / sec / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic}
+    roof.update({"launches": d["launches"], "avg_launch_us": 1e6 * sec, "algorithmic_bytes_per_launch": bytes_pl,
+                 "algorithmic_flops_per_launch": flops_pl, "time_share_of_step": d["total_ms"] / ms if ms else None})
     iters = [s["iterations"] for s in stats[-1]]
     line = {
         "metric": "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)" if args.workload == "32x32x32x64" else f"solves/s to rel. residual 1e-10 ({args.workload})",

@@ -211,14 +211,15 @@ int ddamg_info(const ddamg_handle* h, long long* n_sites, long long* n_coarse_si
  * ddamg_profile_enable(h, mask) records the kernel families whose bit is set
  * in mask (bit order as listed by ddamg_profile_families; -1 = all, 0 = off);
  * ddamg_profile_read fills up to max entries (name, launches, total
- * milliseconds, algorithmic bytes moved) and returns the number of families
+ * milliseconds, algorithmic bytes moved and flops) and returns the number of families
  * recorded.  ddamg_profile_families writes the comma-separated family names
  * into names (len bytes) and returns their number. */
 typedef struct {
     char name[48];
     long long launches;
     double total_ms;
-    double bytes;
+    double bytes;  /* algorithmic bytes moved (every operand read/written once per launch) */
+    double flops;  /* algorithmic floating-point operations (0 where not counted) */
 } ddamg_kernel_profile;
 int ddamg_profile_enable(ddamg_handle* h, int family_mask);
 int ddamg_profile_families(char* names, int len);

@@ -66,6 +66,7 @@ struct ProfRec {
     int fam;
     cudaEvent_t e0, e1;
     double bytes;
+    double flops;
 };
 
 // a growable set of device buffers kept by the handle
@@ -244,10 +245,11 @@ struct Prof {
     ddamg_handle* h;
     ProfRec r;
     bool on;
-    Prof(ddamg_handle* hh, int fam, double bytes) : h(hh), on((hh->prof_mask >> fam) & 1) {
+    Prof(ddamg_handle* hh, int fam, double bytes, double flops = 0.0) : h(hh), on((hh->prof_mask >> fam) & 1) {
         if (on) {
             r.fam = fam;
             r.bytes = bytes;
+            r.flops = flops;
             r.e0 = get_event(h);
             r.e1 = get_event(h);
             cudaEventRecord(r.e0, h->stream);
@@ -494,12 +496,25 @@ static int dslash_dw(ddamg_handle* h, const cplx<float>* z, cplx<double>* w, int
 }
 
 // z <- SAP iterations (nu) on D z = b from the current z (Sec. 2.3)
+// algorithmic flops of one red or black SAP sweep per (even, odd) site pair and right-hand side:
+// full D at both sites for the residual, A_ee^{-1} r_e, the reduced right-hand side, mr MR steps
+// (S rho: in-block hops twice, A_ee^{-1}, A_oo, dot products and updates), back-substitution.
+// One hop = 168 flops (spin projection, two SU(3) x colour-vector products, reconstruction),
+// one 2 x (6x6 hermitian) site-term product = 504 flops.
+static double sap_pair_flops(const ddamg_handle* h) {
+    double hin = 0;  // in-block hops per site
+    for (int m = 0; m < 4; ++m) hin += 2.0 * (h->b[m] - 1) / h->b[m];
+    const double hop = 168, site = 504;
+    return 2 * (8 * hop + site) + site + hin * hop + h->p.mr_steps * (2 * hin * hop + 2 * site + 144) + hin * hop + site;
+}
+
 template <typename T>
 static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) {
     Level<T> L = level<T>(h);
     for (int it = 0; it < nu; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * sizeof(T) + 144.0 * sizeof(T) + nrhs * 36.0 * 2 * sizeof(T)));
+            Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * sizeof(T) + 144.0 * sizeof(T) + nrhs * 36.0 * 2 * sizeof(T)),
+                    (double)h->V / 4 * nrhs * sap_pair_flops(h));
             DD_TRY(launch_sap_colour<T>(h->g, L.op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
         }
     return 0;
@@ -865,6 +880,7 @@ static int vcycle(ddamg_handle* h, const cplx<T>* r, cplx<T>* x, int nrhs, int c
 // ---------------------------------------------------------------------------
 // interpolation: P by local orthonormalisation, D_c by assembly, coarse inverses
 // ---------------------------------------------------------------------------
+static int finish_coarse(ddamg_handle* h);
 static int build_interpolation(ddamg_handle* h) {
     cudaStream_t st = h->stream;
     const int N = h->N, nc = h->nc;
@@ -892,6 +908,15 @@ static int build_interpolation(ddamg_handle* h) {
     DD_CUDA(cudaStreamSynchronize(st));
     tscr.release();
     if (rc) return rc;
+    return finish_coarse(h);
+}
+
+// even-site inverses of D_c and the V-cycle-precision copies of P, D_c, D_ee^{-1}
+static int finish_coarse(ddamg_handle* h) {
+    cudaStream_t st = h->stream;
+    const int N = h->N, nc = h->nc;
+    const size_t fld = (size_t)12 * h->V;
+    int flag = 0;
     DD_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), st));
     DD_TRY(launch_coarse_invert(h->B64, h->Dinv64, h->NB, nc, h->d_flag, st));
     DD_CUDA(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -911,6 +936,14 @@ static int build_interpolation(ddamg_handle* h) {
     DD_CUDA(cudaStreamSynchronize(st));
     h->ready = true;
     return 0;
+}
+
+// D_c(m0 + delta) = D_c(m0) + delta I because P^H P = I (Sec. 3.1): shift the diagonal of B_0
+__global__ void shift_coarse_diag_kernel(double* B64, int NB, int nc, double delta) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)NB * nc) return;
+    int c = (int)(q / nc), i = (int)(q % nc);
+    B64[((((size_t)c * 9) * nc + i) * nc + i) * 2] += delta;
 }
 
 __global__ void gaussian_fill_kernel(double* out, size_t n, unsigned long long seed) {
@@ -1594,6 +1627,7 @@ int ddamg_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, int 
 int ddamg_set_mass(ddamg_handle* h, double m0) {
     if (!h) return DDAMG_ERR_INVALID_ARG;
     // site terms: rebuild with the new mass (the clover part does not depend on it)
+    const double old_m0 = h->m0;
     h->m0 = m0;
     DD_TRY(launch_clover(h->g, h->U64, m0, h->csw, h->clov64, h->clovinv64, h->stream));
     if (h->single()) {
@@ -1601,7 +1635,13 @@ int ddamg_set_mass(ddamg_handle* h, double m0) {
         DD_TRY((convert<float, double>(h->clovinv64, h->clovinv32, (size_t)h->V * 72, h->stream)));
         DD_TRY(launch_to_dw(h->clov64, h->clovdw, (size_t)h->V * 72, h->stream));
     }
-    if (h->ready) DD_TRY(build_interpolation(h));
+    if (h->ready) {
+        // mass re-use (Sec. 6.3): P is kept, D_c moves by (m0' - m0) I, only the inverses are redone
+        const double delta = m0 - old_m0;
+        shift_coarse_diag_kernel<<<ceil_div((long long)h->NB * h->nc, 256), 256, 0, h->stream>>>(h->B64, h->NB, h->nc, delta);
+        DD_CHECK_LAUNCH();
+        DD_TRY(finish_coarse(h));
+    }
     DD_CUDA(cudaStreamSynchronize(h->stream));
     return 0;
 }
@@ -1654,7 +1694,7 @@ int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max) {
     if (!h || (!out && max > 0)) return DDAMG_ERR_INVALID_ARG;
     DD_CUDA(cudaStreamSynchronize(h->stream));
     long long n[PF_COUNT] = {0};
-    double ms[PF_COUNT] = {0}, by[PF_COUNT] = {0};
+    double ms[PF_COUNT] = {0}, by[PF_COUNT] = {0}, fl[PF_COUNT] = {0};
     for (auto& r : h->prof) {
         float t = 0;
         if (cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) {
@@ -1664,6 +1704,7 @@ int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max) {
         n[r.fam]++;
         ms[r.fam] += t;
         by[r.fam] += r.bytes;
+        fl[r.fam] += r.flops;
     }
     int k = 0;
     for (int f = 0; f < PF_COUNT; ++f) {
@@ -1674,6 +1715,7 @@ int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max) {
             out[k].launches = n[f];
             out[k].total_ms = ms[f];
             out[k].bytes = by[f];
+            out[k].flops = fl[f];
         }
         ++k;
     }

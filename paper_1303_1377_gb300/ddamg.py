@@ -82,7 +82,8 @@ class Stats(C.Structure):
 
 
 class KernelProfile(C.Structure):
-    _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
 
 
 def _load():
@@ -333,7 +334,8 @@ class Solver:
     def profile_read(self):
         arr = (KernelProfile * 16)()
         n = lib.ddamg_profile_read(self.h, arr, 16)
-        return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes} for i in range(min(n, 16))}
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms, "bytes": arr[i].bytes,
+                                       "flops": arr[i].flops} for i in range(min(n, 16))}
 
 
 def profile_families():

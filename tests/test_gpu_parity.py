@@ -227,6 +227,50 @@ def test_full_size_dslash_sampled(dd):
     assert abs(a - b) < 1e-11 * abs(a)
 
 
+@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
+def test_set_mass_reuses_interpolation(prec, dd):
+    """Mass re-use: after ddamg_set_mass the coarse operator equals the oracle's P^H D(m0') P with the
+    same P, D equals D(m0'), and a solve at the new mass reaches 1e-10."""
+    c = case("4^4/2^4", dd)
+    m1 = c.m0 - 0.07
+    D1 = DiracOperator(c.U, c.dims, m1, CSW)
+    agg = Aggregation(D1.lat, c.block, c.v)
+    Dc1 = CoarseOperator(D1, agg)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 2, seed=111)
+    x = synth.gaussian_spinors(c.dims, 2, seed=112)
+    with c.solver(getattr(dd, "PREC_" + prec)) as s:
+        s.set_mass(m1)
+        assert relerr(s.coarse_stencil(), Dc1.B) < 1e-12
+        assert relerr(s.apply_D(x), np.stack([D1.apply(x[r]) for r in range(2)])) < 1e-13
+        tol = {"DOUBLE": 1e-12, "SINGLE": 1e-6, "HALF": 4e-3}[prec]
+        assert relerr(s.apply_Dc(e), np.stack([Dc1.apply(e[r]) for r in range(2)])) < tol
+        z, st, rc = s.solve(x)
+        assert rc == 0
+        for r in range(2):
+            assert np.linalg.norm(x[r] - D1.apply(z[r])) <= 1e-10 * np.linalg.norm(x[r])
+
+
+def test_n_vec_24_coarse_blocks_48(dd):
+    """N_v = 24 (2N = 48, the 48^3 x 96 workload's coarse blocks) in all three precisions."""
+    dims, block, N = (8, 8, 8, 8), (4, 4, 4, 4), 24
+    U = synth.gauge_field(dims, 0.5, seed=121)
+    D = DiracOperator(U, dims, 0.1, CSW)
+    v = synth.random_test_vectors(dims, N, seed=122)
+    agg = Aggregation(D.lat, block, v)
+    Dc = CoarseOperator(D, agg)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 3, seed=123)
+    ref = np.stack([Dc.apply(e[r]) for r in range(3)])
+    b = synth.gaussian_spinors(dims, 2, seed=124)
+    for prec, tol in (("DOUBLE", 1e-12), ("SINGLE", 1e-6), ("HALF", 4e-3)):
+        p = dd.default_params(n_vec=N, block=block, precision=getattr(dd, "PREC_" + prec))
+        with dd.Solver(dims, U, 0.1, CSW, p, setup=False) as s:
+            s.setup_from_vectors(v)
+            assert relerr(s.apply_Dc(e), ref) < tol
+            z, st, rc = s.solve(b)
+            assert rc == 0
+            assert max(np.linalg.norm(b[r] - D.apply(z[r])) / np.linalg.norm(b[r]) for r in range(2)) <= 1e-10
+
+
 def test_error_statuses(dd):
     c = case("4^4/2^4", dd)
     p = dd.default_params(n_vec=c.N, block=c.block)

@@ -295,6 +295,115 @@ __global__ void __launch_bounds__(128 * R, 1) sap_colour_kernel(Geom g, FineOp<T
     }
 }
 
+// ---------------------------------------------------------------------------
+// SAP block solve with all per-site MR state in shared memory (r_e, rho, x_o and
+// the even work vector): only temporaries live in registers, so the kernel runs
+// at 128 registers and four CTAs per SM.  One CTA = one block of the colour and
+// one right-hand side; thread t owns the even site t and the odd site H + t.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128, 4) sap_colour_lean_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
+                                                                 cplx<T>* __restrict__ z, int colour, int nrhs, int mr_steps) {
+    extern __shared__ unsigned char smem_raw[];
+    const int H = g.Vb / 2;
+    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw);  // [12][H] even work vector
+    cplx<T>* SO = SE + 12 * H;                            // [12][H] rho
+    cplx<T>* SX = SO + 12 * H;                            // [12][H] x_o (first: r_o)
+    cplx<T>* SR = SX + 12 * H;                            // [12][H] r_e
+    T* red = reinterpret_cast<T*>(SR + 12 * H);
+    const int r = blockIdx.x % nrhs;
+    const int blk = colour * (g.NB / 2) + blockIdx.x / nrhs;
+    const int t = threadIdx.x;
+    const bool act = t < H;
+    const int le = t, lo = H + t;
+    const int ie = blk * g.Vb + le, io = blk * g.Vb + lo;
+    const size_t off = (size_t)r * 12 * g.V;
+    const cplx<T>* b = bsrc + off;
+    cplx<T>* zr = z + off;
+    {
+        Spinor<T> tmp, tmp2;
+        if (act) {
+            site_D(g, op, zr, ie, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                tmp.v[k] = b[(size_t)k * g.V + ie] - tmp.v[k];
+                SR[k * H + t] = tmp.v[k];
+            }
+            herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+            site_D(g, op, zr, io, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SX[k * H + t] = b[(size_t)k * g.V + io] - tmp.v[k];
+        }
+    }
+    __syncthreads();
+    if (act) {  // rho = r_o - D_oe A_ee^{-1} r_e ; x_o = 0
+        Spinor<T> hs;
+        block_hops(g, op.U, SE, H, 0, lo, io, blk, hs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            SO[k * H + t] = SX[k * H + t] + T(0.5) * hs.v[k];
+            SX[k * H + t] = czero<T>();
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < mr_steps; ++it) {
+        if (act) {  // even: SE = A_ee^{-1} D_eo rho  (reads only SO, writes only SE)
+            Spinor<T> hs, tmp2;
+            block_hops(g, op.U, SO, H, H, le, ie, blk, hs);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) hs.v[k] = T(-0.5) * hs.v[k];
+            herm_apply(op.clovinv, g.V, ie, hs, tmp2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+        }
+        __syncthreads();
+        T num_re = 0, num_im = 0, den = 0;
+        Spinor<T> sr;
+        if (act) {  // odd: S rho = A_oo rho + 1/2 hops(SE)
+            Spinor<T> rho, hs;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rho.v[k] = SO[k * H + t];
+            herm_apply(op.clov, g.V, io, rho, sr);
+            block_hops(g, op.U, SE, H, 0, lo, io, blk, hs);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                sr.v[k] = sr.v[k] + T(0.5) * hs.v[k];
+                num_re += sr.v[k].re * rho.v[k].re + sr.v[k].im * rho.v[k].im;
+                num_im += sr.v[k].re * rho.v[k].im - sr.v[k].im * rho.v[k].re;
+                den += norm2(sr.v[k]);
+            }
+        }
+        block_reduce3(num_re, num_im, den, red);
+        cplx<T> alpha = czero<T>();
+        if (den > tiny_normal<T>()) alpha = mk(num_re / den, num_im / den);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cplx<T> rv = SO[k * H + t];
+                cplx<T> xv = SX[k * H + t];
+                cmac(xv, alpha, rv);
+                SX[k * H + t] = xv;
+                SO[k * H + t] = rv - alpha * sr.v[k];
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {  // x_e = A_ee^{-1} (r_e - D_eo x_o); z += x
+        Spinor<T> hs, tmp2;
+        block_hops(g, op.U, SX, H, H, le, ie, blk, hs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) hs.v[k] = SR[k * H + t] + T(0.5) * hs.v[k];
+        herm_apply(op.clovinv, g.V, ie, hs, tmp2);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + tmp2.v[k];
+            zr[(size_t)k * g.V + io] = zr[(size_t)k * g.V + io] + SX[k * H + t];
+        }
+    }
+}
+
 template <typename T, int R>
 static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                         cudaStream_t st) {
@@ -316,6 +425,19 @@ template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st) {
     const int H = g.Vb / 2;
+    if (sizeof(T) == 4) {
+        const int nt = ((H + 31) / 32) * 32;
+        size_t smem = (size_t)48 * H * sizeof(cplx<T>) + 3 * 32 * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(sap_colour_lean_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        long long nblk = (long long)(g.NB / 2) * nrhs;
+        sap_colour_lean_kernel<T><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+        DD_CHECK_LAUNCH();
+        return 0;
+    }
     if (sizeof(T) == 4 && H <= 128 && nrhs >= 2) return launch_sap_r<T, 2>(g, op, b, z, colour, nrhs, mr_steps, st);
     return launch_sap_r<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
 }

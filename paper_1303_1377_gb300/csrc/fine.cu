@@ -301,23 +301,29 @@ __global__ void __launch_bounds__(128 * R, 1) sap_colour_kernel(Geom g, FineOp<T
 // at 128 registers and four CTAs per SM.  One CTA = one block of the colour and
 // one right-hand side; thread t owns the even site t and the odd site H + t.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(128, 4) sap_colour_lean_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
-                                                                 cplx<T>* __restrict__ z, int colour, int nrhs, int mr_steps) {
+// R right-hand sides ride in adjacent lanes (lane = R * site-pair + slot), so the
+// link and site-term loads of the R lanes of one site are a single transaction.
+template <typename T, int R>
+__global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
+                                                                                     cplx<T>* __restrict__ z, int colour, int nrhs,
+                                                                                     int mr_steps) {
     extern __shared__ unsigned char smem_raw[];
     const int H = g.Vb / 2;
-    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw);  // [12][H] even work vector
-    cplx<T>* SO = SE + 12 * H;                            // [12][H] rho
-    cplx<T>* SX = SO + 12 * H;                            // [12][H] x_o (first: r_o)
-    cplx<T>* SR = SX + 12 * H;                            // [12][H] r_e
-    T* red = reinterpret_cast<T*>(SR + 12 * H);
-    const int r = blockIdx.x % nrhs;
-    const int blk = colour * (g.NB / 2) + blockIdx.x / nrhs;
-    const int t = threadIdx.x;
-    const bool act = t < H;
+    const int slot = threadIdx.x % R;
+    const int t = threadIdx.x / R;
+    const int slot_stride = 48 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
+    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)slot * slot_stride;  // [12][H] even work vector
+    cplx<T>* SO = SE + 12 * H;                                                         // [12][H] rho
+    cplx<T>* SX = SO + 12 * H;                                                         // [12][H] x_o (first: r_o)
+    cplx<T>* SR = SX + 12 * H;                                                         // [12][H] r_e
+    T* red = reinterpret_cast<T*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)R * slot_stride);  // [nwarps][R][3]
+    const int ngroups = (nrhs + R - 1) / R;
+    const int r = (blockIdx.x % ngroups) * R + slot;
+    const int blk = colour * (g.NB / 2) + blockIdx.x / ngroups;
+    const bool act = t < H && r < nrhs;
     const int le = t, lo = H + t;
     const int ie = blk * g.Vb + le, io = blk * g.Vb + lo;
-    const size_t off = (size_t)r * 12 * g.V;
+    const size_t off = (size_t)(r < nrhs ? r : 0) * 12 * g.V;
     const cplx<T>* b = bsrc + off;
     cplx<T>* zr = z + off;
     {
@@ -375,7 +381,27 @@ __global__ void __launch_bounds__(128, 4) sap_colour_lean_kernel(Geom g, FineOp<
                 den += norm2(sr.v[k]);
             }
         }
-        block_reduce3(num_re, num_im, den, red);
+        // reduction over the site pairs of each slot: lanes of equal slot first, then warps
+#pragma unroll
+        for (int o = R; o < 32; o <<= 1) {
+            num_re += __shfl_xor_sync(0xffffffffu, num_re, o);
+            num_im += __shfl_xor_sync(0xffffffffu, num_im, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) < R) {
+            red[(w * R + slot) * 3] = num_re;
+            red[(w * R + slot) * 3 + 1] = num_im;
+            red[(w * R + slot) * 3 + 2] = den;
+        }
+        __syncthreads();
+        num_re = num_im = den = T(0);
+        for (int q = 0; q < nw; ++q) {
+            num_re += red[(q * R + slot) * 3];
+            num_im += red[(q * R + slot) * 3 + 1];
+            den += red[(q * R + slot) * 3 + 2];
+        }
         cplx<T> alpha = czero<T>();
         if (den > tiny_normal<T>()) alpha = mk(num_re / den, num_im / den);
         if (act) {
@@ -421,22 +447,30 @@ static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cp
     return 0;
 }
 
+template <typename T, int R>
+static int launch_sap_lean(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+                           cudaStream_t st) {
+    const int H = g.Vb / 2;
+    size_t smem = (size_t)R * (48 * H + 4) * sizeof(cplx<T>) + (size_t)(R * H / 32 + 1) * R * 3 * sizeof(T) + 64;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(sap_colour_lean_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
+    sap_colour_lean_kernel<T, R><<<(unsigned)nblk, R * H, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
 template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st) {
     const int H = g.Vb / 2;
     if (sizeof(T) == 4) {
-        const int nt = ((H + 31) / 32) * 32;
-        size_t smem = (size_t)48 * H * sizeof(cplx<T>) + 3 * 32 * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(sap_colour_lean_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
-        long long nblk = (long long)(g.NB / 2) * nrhs;
-        sap_colour_lean_kernel<T><<<(unsigned)nblk, nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
-        DD_CHECK_LAUNCH();
-        return 0;
+        // four right-hand sides per site in adjacent lanes (needs 4 H to be a whole number of warps)
+        if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<T, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
+        if (H % 32 == 0) return launch_sap_lean<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
     }
     if (sizeof(T) == 4 && H <= 128 && nrhs >= 2) return launch_sap_r<T, 2>(g, op, b, z, colour, nrhs, mr_steps, st);
     return launch_sap_r<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);

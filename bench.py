@@ -180,6 +180,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32x32x32x64", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="half", choices=["single", "half", "double"])
+    ap.add_argument("--outer", default="refine", choices=["refine", "dw"],
+                    help="outer scheme of the mixed-precision modes: FP32 cycles + FP64 residual correction, or double-word FGMRES")
+    ap.add_argument("--cycle-tol", type=float, default=1e-5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain single-RHS FP64 comparison solve")
@@ -209,7 +212,8 @@ def main():
     U = synth.gauge_field(dims, w["eps"], w["seed"])
     t_gauge = time.perf_counter() - t
     prec = {"single": ddamg.PREC_SINGLE, "half": ddamg.PREC_HALF, "double": ddamg.PREC_DOUBLE}[args.precision]
-    params = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=prec)
+    params = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=prec,
+                                  outer=ddamg.OUTER_REFINE if args.outer == "refine" else ddamg.OUTER_DW, cycle_tol=args.cycle_tol)
     t = time.perf_counter()
     solver = ddamg.Solver(dims, U, m0, C_SW, params, setup=True)
     torch.cuda.synchronize()
@@ -316,7 +320,9 @@ def main():
         "config": {"workload": f"{args.workload} lattice (L0={dims[0]}), SU(3) links exp(i eps H) eps={w['eps']} seed={w['seed']}, c_sw={C_SW}, "
                                f"m0={m0:.6f}, {nr} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
                                f"MR(4), FGMRES(25) tol 1e-10, coarse GMRES(30) tol 5e-2, V-cycle {args.precision}",
-                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision},
+                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision,
+                   "outer": (f"FP32 FGMRES cycles to {args.cycle_tol:g} + FP64 residual correction" if args.outer == "refine"
+                             and args.precision != "double" else "double-word FGMRES" if args.precision != "double" else "FP64 FGMRES")},
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches,
@@ -325,6 +331,7 @@ def main():
         "coarse_seconds_host": [s["coarse_seconds"] for s in stats[-1]][:1],
         "e2e": e2e,
         "fgmres_iterations": iters,
+        "fgmres_restarts": [s["restarts"] for s in stats[-1]],
         "coarse_iterations_per_solve": stats[-1][0]["coarse_iterations"],
         "max_rel_residual": rel,
         "setup_seconds": t_setup,

@@ -50,13 +50,27 @@ typedef enum {
     DDAMG_ERR_RANK = -8           /* test vectors linearly dependent on an aggregate */
 } ddamg_status;
 
-/* Arithmetic of the V-cycle (smoother, P/P^H, coarse solve).  The outer FGMRES,
- * its Arnoldi process and the final residual are FP64 in every mode (Sec. 6). */
+/* Arithmetic of the V-cycle (smoother, P/P^H, coarse solve).  The final residual
+ * and the iterate are FP64 in every mode; the outer FGMRES is FP64 in DOUBLE mode
+ * and follows ddamg_outer in SINGLE and HALF mode (Sec. 6 runs the preconditioner
+ * in single precision inside a double-precision FGMRES). */
 typedef enum {
     DDAMG_PREC_DOUBLE = 0, /* V-cycle in FP64 */
     DDAMG_PREC_SINGLE = 1, /* V-cycle in FP32 (the paper's mixed precision, Sec. 6) */
     DDAMG_PREC_HALF = 2    /* V-cycle in FP32 with D_c and P stored in FP16 (FP32 accumulation) */
 } ddamg_precision;
+
+/* Outer iteration of SINGLE and HALF mode (no counterpart in the paper, which
+ * keeps the whole FGMRES in FP64; FP64 arithmetic runs at about 1/60 of FP32 on
+ * this GPU).  Both certify the result with the FP64 residual b - D z. */
+typedef enum {
+    DDAMG_OUTER_DW = 0,    /* one FGMRES(n_kv): double-word (~48-bit) Arnoldi basis and products D z,
+                              FP64 iterate; true FP64 residual at every restart */
+    DDAMG_OUTER_REFINE = 1 /* FGMRES cycles in FP32 (basis, D z, Gram-Schmidt), each ended once every
+                              right-hand side has reduced its residual by cycle_tol (or after n_kv
+                              steps); between cycles the FP64 iterate is updated and the FP64 true
+                              residual b - D z starts the next cycle */
+} ddamg_outer;
 
 typedef struct {
     int dims[4]; /* L0 (time), L1, L2, L3 */
@@ -79,6 +93,8 @@ typedef struct {
     int rebuild_after_last; /* 1: rebuild P, D_c after the last setup update (1) */
     uint64_t seed;        /* seed of the initial random test vectors (1) */
     double time_limit_s;  /* wall-clock limit per solve call, <= 0: none (0) */
+    int outer;            /* ddamg_outer of SINGLE and HALF mode (DDAMG_OUTER_REFINE) */
+    double cycle_tol;     /* residual reduction of one FP32 cycle of DDAMG_OUTER_REFINE, in (0, 1) (1e-5) */
 } ddamg_params;
 
 /* Statistics of one solve (the quantities reported in Tables 3-9). */

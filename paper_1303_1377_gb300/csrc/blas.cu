@@ -270,7 +270,7 @@ __global__ void arnoldi_update_kernel(KrylovState s, int k, const cplx<double>* 
     s.resid[r] = est;
     bool nonfinite = !(est == est) || !(hk == hk);
     if (nonfinite) s.flags[r] |= 2;
-    if (est <= s.target[r] || nonfinite) s.active[r] = 0;
+    if (est <= s.ctarget[r] || nonfinite) s.active[r] = 0;
     scale[r] = (hk > 0.0 && s.active[r]) ? mk(1.0 / hk, 0.0) : mk(0.0, 0.0);
 }
 
@@ -305,6 +305,7 @@ __global__ void arnoldi_start_kernel(KrylovState s, const cplx<double>* __restri
     bool nonfinite = !(beta == beta) || beta > 1e300;
     if (nonfinite) s.flags[r] |= 2;
     s.active[r] = (s.enabled[r] && !nonfinite && (force_all || beta > s.target[r])) ? 1 : 0;
+    s.ctarget[r] = fmax(s.target[r], s.cycle_tol * beta);
     scale[r] = (s.active[r] && beta > 0) ? mk(1.0 / beta, 0.0) : mk(0.0, 0.0);
 }
 
@@ -507,6 +508,195 @@ int axpy_norm_dw(cplx<dwf>* w, const cplx<dwf>* A, size_t istride, size_t rstrid
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 basis vectors (the inner cycles of the refinement scheme).  A thread
+// handles two complex numbers (one float4) per step; products and short sums
+// are FP32, flushed into FP64 accumulators every kFlush steps, so that FP64
+// arithmetic stays a small fraction of the work.  Requires even n and
+// 16-byte aligned vectors (every fine vector is 12 V complex numbers).
+// ---------------------------------------------------------------------------
+constexpr int kFlush = 8;
+
+template <int KB>
+__global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4* __restrict__ A, size_t istride4, size_t arstride4, int k,
+                                                                   const float4* __restrict__ w, size_t wrstride4, size_t n4, int nrhs,
+                                                                   int ctas_per_rhs, double* __restrict__ partial,
+                                                                   const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
+    const int r = blockIdx.x % nrhs;
+    const int part = blockIdx.x / nrhs;
+    const float4* Ar = A + r * arstride4;
+    const float4* wr = w + r * wrstride4;
+    float fr[KB], fi[KB];
+    double dr[KB], di[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) fr[q] = fi[q] = 0.f, dr[q] = di[q] = 0.0;
+    const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
+    int cnt = 0;
+    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n4; e += stride) {
+        const float4 wv = wr[e];
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+            if (i < k) {
+                const float4 a = Ar[i * istride4 + e];  // conj(a) w for both complex numbers
+                fr[i] = fmaf(a.x, wv.x, fmaf(a.y, wv.y, fmaf(a.z, wv.z, fmaf(a.w, wv.w, fr[i]))));
+                fi[i] = fmaf(a.x, wv.y, fmaf(-a.y, wv.x, fmaf(a.z, wv.w, fmaf(-a.w, wv.z, fi[i]))));
+            }
+        }
+        if (++cnt == kFlush) {
+            cnt = 0;
+#pragma unroll
+            for (int i = 0; i < KB; ++i) dr[i] += fr[i], di[i] += fi[i], fr[i] = fi[i] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < KB; ++i) dr[i] += fr[i], di[i] += fi[i];
+    __shared__ double red[kDotThreads / 32][2 * KB];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+        if (i < k) {
+            double vr = warp_sum(dr[i]);
+            double vi = warp_sum(di[i]);
+            if (lane == 0) {
+                red[wi][2 * i] = vr;
+                red[wi][2 * i + 1] = vi;
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) {
+        double s = 0;
+        for (int ww = 0; ww < kDotThreads / 32; ++ww) s += red[ww][q];
+        partial[((size_t)blockIdx.x) * 2 * k + q] = s;
+    }
+}
+
+static bool f32_layout_ok(const void* A, size_t istride, size_t arstride, const void* w, size_t wrstride, size_t n) {
+    return n % 2 == 0 && istride % 2 == 0 && arstride % 2 == 0 && wrstride % 2 == 0 && ((uintptr_t)A & 15) == 0 &&
+           ((uintptr_t)w & 15) == 0;
+}
+
+int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, const cplx<float>* w, size_t wrstride, size_t n, int nrhs,
+                 cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st) {
+    if (!f32_layout_ok(A, istride, arstride, w, wrstride, n)) return -1;
+    const size_t n4 = n / 2;
+    int off = 0;
+    while (off < k) {
+        int kk = k - off;
+        if (kk > 16) kk = 16;
+        int ctas = (int)((n4 + kDotThreads - 1) / kDotThreads);
+        int target = 1216 / nrhs;
+        if (target < 1) target = 1;
+        if (ctas > target) ctas = target;
+        const float4* Ab = reinterpret_cast<const float4*>(A + off * istride);
+        const float4* w4 = reinterpret_cast<const float4*>(w);
+        const unsigned grid = ctas * nrhs;
+        if (kk <= 1)
+            multidot_f32_kernel<1><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+        else if (kk <= 4)
+            multidot_f32_kernel<4><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+        else if (kk <= 8)
+            multidot_f32_kernel<8><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+        else
+            multidot_f32_kernel<16><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+        DD_CHECK_LAUNCH();
+        multidot_finish<<<ceil_div((long long)nrhs * kk, 128), 128, 0, st>>>(scratch, kk, nrhs, ctas, out + (size_t)off * ostride_i,
+                                                                          ostride_i, run_flag);
+        DD_CHECK_LAUNCH();
+        off += kk;
+    }
+    return 0;
+}
+
+// coefficients alpha * coef[i][r] rounded to FP32
+__global__ void coef_to_f32_kernel(const cplx<double>* __restrict__ coef, int cstride_i, int k, int nrhs, double alpha,
+                                   float2* __restrict__ out, const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k * nrhs) return;
+    int i = q / nrhs, r = q % nrhs;
+    cplx<double> c = coef[(size_t)i * cstride_i + r];
+    out[q] = make_float2((float)(alpha * c.re), (float)(alpha * c.im));
+}
+
+// w[r] += sum_i c[i][r] * A_i[r] in place (FP32), with ||w[r]||^2 of the result (FP64 sum)
+__global__ void __launch_bounds__(kAxpyThreads) axpy_norm_f32_kernel(float4* __restrict__ wv, const float4* __restrict__ A, size_t istride4,
+                                                                     size_t rstride4, int k, const float2* __restrict__ cv, size_t n4,
+                                                                     int nrhs, int ctas_per_rhs, double* __restrict__ partial,
+                                                                     const int* __restrict__ run_flag) {
+    if (run_flag && !*run_flag) return;
+    const int r = blockIdx.x % nrhs;
+    const int part = blockIdx.x / nrhs;
+    float4* wr = wv + r * rstride4;
+    const float4* Ar = A + r * rstride4;
+    double nrm = 0.0;
+    const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
+    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n4; e += stride) {
+        float4 acc = wr[e];
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            const float2 c = __ldg(cv + (size_t)i * nrhs + r);
+            const float4 a = Ar[i * istride4 + e];
+            acc.x = fmaf(c.x, a.x, fmaf(-c.y, a.y, acc.x));
+            acc.y = fmaf(c.x, a.y, fmaf(c.y, a.x, acc.y));
+            acc.z = fmaf(c.x, a.z, fmaf(-c.y, a.w, acc.z));
+            acc.w = fmaf(c.x, a.w, fmaf(c.y, a.z, acc.w));
+        }
+        wr[e] = acc;
+        nrm += (double)(acc.x * acc.x + acc.y * acc.y) + (double)(acc.z * acc.z + acc.w * acc.w);
+    }
+    __shared__ double red[kAxpyThreads / 32];
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int q = 0; q < kAxpyThreads / 32; ++q) s += red[q];
+        partial[blockIdx.x * 2] = s;
+        partial[blockIdx.x * 2 + 1] = 0.0;
+    }
+}
+
+int axpy_norm_f32(cplx<float>* w, const cplx<float>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
+                  size_t n, int nrhs, double alpha, float2* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                  cudaStream_t st) {
+    if (!f32_layout_ok(A, istride, rstride, w, rstride, n)) return -1;
+    coef_to_f32_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch, run_flag);
+    DD_CHECK_LAUNCH();
+    const size_t n4 = n / 2;
+    int ctas = (int)((n4 + kAxpyThreads - 1) / kAxpyThreads);
+    int target = 1216 / nrhs;
+    if (target < 1) target = 1;
+    if (ctas > target) ctas = target;
+    axpy_norm_f32_kernel<<<ctas * nrhs, kAxpyThreads, 0, st>>>(reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(A), istride / 2,
+                                                               rstride / 2, k, coef_scratch, n4, nrhs, ctas, scratch, run_flag);
+    DD_CHECK_LAUNCH();
+    multidot_finish<<<ceil_div((long long)nrhs, 128), 128, 0, st>>>(scratch, 1, nrhs, ctas, norm_out, nrhs, run_flag);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// w[r] *= scale[r] (real part) for an FP32 basis vector; one float4 (two complex numbers) per step
+__global__ void scale_f32_kernel(float4* __restrict__ w, const cplx<double>* __restrict__ scale, size_t n4, int nrhs) {
+    const int r = blockIdx.y;
+    const float a = (float)scale[r].re;
+    float4* wr = w + (size_t)r * n4;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+        float4 v = wr[e];
+        v.x *= a, v.y *= a, v.z *= a, v.w *= a;
+        wr[e] = v;
+    }
+}
+int scale_f32(cplx<float>* w, const cplx<double>* scale, size_t n, int nrhs, cudaStream_t st) {
+    if (n % 2 || ((uintptr_t)w & 15)) return -1;
+    const size_t n4 = n / 2;
+    int bx = (int)std::min<size_t>((n4 + 255) / 256, (size_t)std::max(1, 152 * 8 / nrhs));
+    scale_f32_kernel<<<dim3(bx, nrhs), 256, 0, st>>>(reinterpret_cast<float4*>(w), scale, n4, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
 // Reorthogonalisation test of classical Gram-Schmidt (the DGKS criterion with
 // threshold eta): request a second pass when, for any active right-hand side,
 // ||w after||^2 < eta^2 ||w before||^2.
@@ -531,6 +721,40 @@ __global__ void add_columns_flag_kernel(cplx<double>* __restrict__ a, const cplx
 }
 int add_columns_flag(cplx<double>* a, const cplx<double>* b, int n, const int* flag, cudaStream_t st) {
     add_columns_flag_kernel<<<ceil_div(n, 128), 128, 0, st>>>(a, b, n, flag);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// x[r] += sum_i y[i][r] Z_i[r] for an FP64 iterate and FP32 preconditioned vectors: the sum is
+// formed in double-word arithmetic (exact FP32 products, ~2^-48 accumulation) and added once in FP64
+__global__ void xupdate_kernel(cplx<double>* __restrict__ x, const cplx<float>* __restrict__ Z, size_t istride, size_t n, int k,
+                               const float4* __restrict__ cdwv, int nrhs) {
+    const size_t tot = n * nrhs;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(q / n);
+        size_t e = q % n;
+        cdw acc = cdw_zero();
+        for (int i = 0; i < k; ++i) {
+            float4 c = __ldg(cdwv + (size_t)i * nrhs + r);
+            cplx<float> zv = Z[i * istride + (size_t)r * n + e];
+            dw cr = {c.x, c.y}, ci = {c.z, c.w};
+            dw_macf(acc.re, cr, zv.re);
+            dw_macf(acc.re, dw_neg(ci), zv.im);
+            dw_macf(acc.im, cr, zv.im);
+            dw_macf(acc.im, ci, zv.re);
+        }
+        cplx<double>& xv = x[(size_t)r * n + e];
+        xv = mk(xv.re + dw_to_double(acc.re), xv.im + dw_to_double(acc.im));
+    }
+}
+int xupdate_dw(cplx<double>* x, const cplx<float>* Z, size_t istride, size_t n, int k, const cplx<double>* coef, int nrhs,
+               float4* coef_scratch, cudaStream_t st) {
+    coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, nrhs, k, nrhs, 1.0, coef_scratch, nullptr);
+    DD_CHECK_LAUNCH();
+    long long tot = (long long)n * nrhs;
+    int blocks = ceil_div(tot, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    xupdate_kernel<<<blocks, 256, 0, st>>>(x, Z, istride, n, k, coef_scratch, nrhs);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -19,6 +19,8 @@ struct KrylovState {
     int* enabled;      // takes part in this solve at all
     int* flags;        // bit 1: non-finite value met
     double* target;    // absolute residual target tol * ||b||
+    double* ctarget;   // target of the current cycle: max(target, cycle_tol * beta of the cycle)
+    double cycle_tol;  // 0: a cycle runs to target (or the restart length)
 };
 
 template <typename Ta, typename Tb>
@@ -41,6 +43,15 @@ int dgks(const cplx<double>* before, const cplx<double>* after, const int* activ
 int add_columns_flag(cplx<double>* a, const cplx<double>* b, int n, const int* flag, cudaStream_t st);
 int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t istride, size_t ars, int k, const cplx<double>* coef,
                int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st);
+int xupdate_dw(cplx<double>* x, const cplx<float>* Z, size_t istride, size_t n, int k, const cplx<double>* coef, int nrhs,
+               float4* coef_scratch, cudaStream_t st);
+// FP32 basis (even n, 16-byte aligned vectors; -1 otherwise)
+int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, const cplx<float>* w, size_t wrstride, size_t n, int nrhs,
+                 cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st);
+int axpy_norm_f32(cplx<float>* w, const cplx<float>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
+                  size_t n, int nrhs, double alpha, float2* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                  cudaStream_t st);
+int scale_f32(cplx<float>* w, const cplx<double>* scale, size_t n, int nrhs, cudaStream_t st);
 int convert_d2dw(const double* in, cplx<dwf>* out, size_t nreal, cudaStream_t st);
 int convert_dw2f(const cplx<dwf>* in, float* out, size_t nreal, cudaStream_t st);
 template <typename To, typename Ti>

@@ -467,7 +467,7 @@ template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st) {
     const int H = g.Vb / 2;
-    if (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
         // four right-hand sides per site in adjacent lanes (needs 4 H to be a whole number of warps)
         if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<T, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
         if (H % 32 == 0) return launch_sap_lean<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);

@@ -128,6 +128,8 @@ struct KrylovBufs {
         DD_TRY(dalloc_n(&s.enabled, nr));
         DD_TRY(dalloc_n(&s.flags, nr));
         DD_TRY(dalloc_n(&s.target, nr));
+        DD_TRY(dalloc_n(&s.ctarget, nr));
+        s.cycle_tol = 0.0;
         DD_TRY(dalloc_n(&hcol, (size_t)(mm + 2) * nr));
         DD_TRY(dalloc_n(&hcol2, (size_t)(mm + 2) * nr));
         DD_TRY(dalloc_n(&scale, nr));
@@ -159,6 +161,7 @@ struct KrylovBufs {
         dfree(s.enabled);
         dfree(s.flags);
         dfree(s.target);
+        dfree(s.ctarget);
         dfree(hcol);
         dfree(hcol2);
         dfree(scale);
@@ -586,6 +589,8 @@ struct KrylovProblem {
     long long maxiter;     // Arnoldi steps per rhs
     bool fixed;            // run exactly maxiter steps (no tolerance)
     bool reorth;           // classical Gram-Schmidt twice
+    bool lean = false;     // FP32 basis: one Gram-Schmidt pass, a second one only on heavy cancellation
+    double cycle_tol = 0;  // > 0: a cycle ends once every rhs has reduced its residual by this factor
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
     cplx<TZ>* Zb;          // [m][nrhs][n] when M is set
     cplx<TV>* w;           // [nrhs][n]
@@ -628,8 +633,46 @@ static int bfrom(cplx<TV>* out, const cplx<TB>* in, size_t count, cudaStream_t s
     return DDAMG_ERR_INVALID_ARG;
 }
 template <>
+int bfrom<float, double>(cplx<float>* out, const cplx<double>* in, size_t count, cudaStream_t st) {
+    return convert<float, double>(reinterpret_cast<const double*>(in), reinterpret_cast<float*>(out), 2 * count, st);
+}
+template <>
 int bfrom<dwf, double>(cplx<dwf>* out, const cplx<double>* in, size_t count, cudaStream_t st) {
     return convert_d2dw(reinterpret_cast<const double*>(in), out, 2 * count, st);
+}
+
+// one-pass Gram-Schmidt kernels of the double-word and FP32 bases (w in the V_{k+1} slot)
+template <typename TV>
+static int lean_multidot(const cplx<TV>* Vb, size_t bstride, size_t n, int k, const cplx<TV>* w, int nr, cplx<double>* out,
+                         KrylovBufs& kb, const int* flag, cudaStream_t st) {
+    if constexpr (std::is_same<TV, dwf>::value) {
+        return multidot_dw(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, flag, st);
+    } else if constexpr (std::is_same<TV, float>::value) {
+        if (multidot_f32(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, flag, st)) {
+            set_error("FP32 basis: odd length or misaligned vector");
+            return DDAMG_ERR_INVALID_ARG;
+        }
+        return 0;
+    } else {
+        set_error("no one-pass Gram-Schmidt for this basis type");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+}
+template <typename TV>
+static int lean_axpy_norm(cplx<TV>* w, const cplx<TV>* Vb, size_t bstride, size_t n, int k, const cplx<double>* coef, int nr,
+                          KrylovBufs& kb, cplx<double>* norm_out, const int* flag, cudaStream_t st) {
+    if constexpr (std::is_same<TV, dwf>::value) {
+        return axpy_norm_dw(w, Vb, bstride, n, k, coef, nr, n, nr, -1.0, kb.coefdw, kb.dscr, norm_out, flag, st);
+    } else if constexpr (std::is_same<TV, float>::value) {
+        if (axpy_norm_f32(w, Vb, bstride, n, k, coef, nr, n, nr, -1.0, reinterpret_cast<float2*>(kb.coefdw), kb.dscr, norm_out, flag, st)) {
+            set_error("FP32 basis: odd length or misaligned vector");
+            return DDAMG_ERR_INVALID_ARG;
+        }
+        return 0;
+    } else {
+        set_error("no one-pass Gram-Schmidt for this basis type");
+        return DDAMG_ERR_INVALID_ARG;
+    }
 }
 
 template <typename TB, typename TV, typename TZ>
@@ -640,6 +683,7 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
     DD_TRY(kb.alloc(nr, P.m));
     KrylovState& s = kb.s;
     s.nrhs = nr;
+    s.cycle_tol = P.cycle_tol;
     R.iters.assign(nr, 0);
     R.resid.assign(nr, 0.0);
     R.bnorm.assign(nr, 0.0);
@@ -676,9 +720,28 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
     long long total = 0;
     while (true) {
         // start of a cycle
-        DD_TRY(bdot<TV>(kb, V0, 0, 1, V0, n, nr, kb.nrm, st));
+        if constexpr (std::is_same<TV, float>::value) {
+            if (P.lean) {
+                DD_TRY(lean_multidot(V0, 0, n, 1, V0, nr, kb.nrm, kb, nullptr, st));
+            } else {
+                DD_TRY(bdot<TV>(kb, V0, 0, 1, V0, n, nr, kb.nrm, st));
+            }
+        } else {
+            DD_TRY(bdot<TV>(kb, V0, 0, 1, V0, n, nr, kb.nrm, st));
+        }
         DD_TRY(arnoldi_start(s, kb.nrm, kb.scale, P.fixed ? 1 : 0, st));
-        DD_TRY(baxpy<TV>(kb, V0, false, V0, 0, 1, kb.scale, n, nr, 1.0, st));
+        if constexpr (std::is_same<TV, float>::value) {
+            if (P.lean) {
+                if (scale_f32(V0, kb.scale, n, nr, st)) {
+                    set_error("FP32 basis: odd length or misaligned vector");
+                    return DDAMG_ERR_INVALID_ARG;
+                }
+            } else {
+                DD_TRY(baxpy<TV>(kb, V0, false, V0, 0, 1, kb.scale, n, nr, 1.0, st));
+            }
+        } else {
+            DD_TRY(baxpy<TV>(kb, V0, false, V0, 0, 1, kb.scale, n, nr, 1.0, st));
+        }
         DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaStreamSynchronize(st));
@@ -703,30 +766,40 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             } else {
                 zk = reinterpret_cast<const cplx<TZ>*>(Vk);
             }
-            if constexpr (std::is_same<TV, dwf>::value) {
+            bool lean_step = false;
+            if constexpr (std::is_same<TV, dwf>::value || std::is_same<TV, float>::value)
+                lean_step = std::is_same<TV, dwf>::value || P.lean;
+            if (lean_step) {
                 // w is formed in the V_{k+1} slot; one multi-dot gives <V_i, w> (i <= k) and ||w||^2,
                 // the axpy kernel returns ||w'||^2, and the second classical Gram-Schmidt pass runs
                 // only when the first one cancelled more than 1 - eta of w (eta = 1e-3, decided on the
                 // device).  With the 48-bit double-word basis one pass leaves a non-orthogonality of
                 // about 1e-14 ||w|| / ||w'||, far below what a 1e-10 solve needs; the FP64 true residual
                 // at every restart certifies convergence whatever the basis quality.
-                cplx<dwf>* wk = P.Vb + (size_t)(k + 1) * bstride;
+                // (FP32 basis: the same scheme; one pass leaves about 1e-7 ||w|| / ||w'|| of
+                // non-orthogonality, ample for a cycle that reduces the residual by cycle_tol)
+                cplx<TV>* wk = P.Vb + (size_t)(k + 1) * bstride;
                 DD_TRY(P.A(zk, wk));
                 const double vb = (double)sizeof(cplx<TV>) * n * nr;
                 Prof pr(h, PF_ORTHO, vb * (2 * (k + 1) + 6));
-                DD_TRY(multidot_dw(P.Vb, bstride, n, k + 2, wk, n, n, nr, kb.hcol, nr, kb.dscr, nullptr, st));
+                DD_TRY(lean_multidot(P.Vb, bstride, n, k + 2, wk, nr, kb.hcol, kb, nullptr, st));
                 DD_CUDA(cudaMemcpyAsync(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToDevice, st));
-                DD_TRY(axpy_norm_dw(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, n, nr, -1.0, kb.coefdw, kb.dscr,
-                                    kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
+                DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, kb, kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
                 if (P.reorth) {
                     DD_TRY(dgks(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, s.active, nr, 1e-3, kb.dflag, st));
-                    DD_TRY(multidot_dw(P.Vb, bstride, n, k + 1, wk, n, n, nr, kb.hcol2, nr, kb.dscr, kb.dflag, st));
-                    DD_TRY(axpy_norm_dw(wk, P.Vb, bstride, n, k + 1, kb.hcol2, nr, n, nr, -1.0, kb.coefdw, kb.dscr,
-                                        kb.hcol + (size_t)(k + 1) * nr, kb.dflag, st));
+                    DD_TRY(lean_multidot(P.Vb, bstride, n, k + 1, wk, nr, kb.hcol2, kb, kb.dflag, st));
+                    DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol2, nr, kb, kb.hcol + (size_t)(k + 1) * nr, kb.dflag, st));
                     DD_TRY(add_columns_flag(kb.hcol, kb.hcol2, (k + 1) * nr, kb.dflag, st));
                 }
                 DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
-                DD_TRY(baxpy<TV>(kb, wk, false, wk, 0, 1, kb.scale, n, nr, 1.0, st));
+                if constexpr (std::is_same<TV, float>::value) {
+                    if (scale_f32(wk, kb.scale, n, nr, st)) {
+                        set_error("FP32 basis: odd length or misaligned vector");
+                        return DDAMG_ERR_INVALID_ARG;
+                    }
+                } else {
+                    DD_TRY(baxpy<TV>(kb, wk, false, wk, 0, 1, kb.scale, n, nr, 1.0, st));
+                }
             } else {
                 DD_TRY(P.A(zk, P.w));
                 // classical Gram-Schmidt (twice when reorth)
@@ -764,7 +837,10 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
         DD_TRY(arnoldi_solve(s, kb.y, st));
         {
             Prof pru(h, PF_UPDATE, (double)n * nr * (2 * sizeof(cplx<TB>) + std::min(k, P.m) * sizeof(cplx<TZ>)));
-            if (P.M)
+            if (P.M && std::is_same<TB, double>::value && std::is_same<TZ, float>::value)
+                DD_TRY(xupdate_dw(reinterpret_cast<cplx<double>*>(P.x), reinterpret_cast<const cplx<float>*>(P.Zb), bstride, n,
+                                  std::min(k, P.m), kb.y, nr, kb.coefdw, st));
+            else if (P.M)
                 DD_TRY((lincomb<TB, TZ>(P.x, n, 1.0, P.Zb, bstride, n, std::min(k, P.m), kb.y, nr, n, nr, nullptr, st)));
             else
                 DD_TRY((lincomb<TB, TZ>(P.x, n, 1.0, reinterpret_cast<const cplx<TZ>*>(P.Vb), bstride, n, std::min(k, P.m), kb.y, nr,
@@ -1064,11 +1140,14 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     P.nrhs = nrhs;
     P.m = m;
     P.A = [&](const cplx<TZ>* z, cplx<TV>* w) -> int {
-        if (std::is_same<TV, dwf>::value) {
+        if constexpr (std::is_same<TV, dwf>::value) {
             Prof pr(h, PF_DSLASHDW, (double)h->V * (36.0 * 16 + 72.0 * 8 + nrhs * (12.0 * 8 + 12.0 * 16)));
             return launch_dslash_dw(h->g, h->Udw, h->clovdw, reinterpret_cast<const cplx<float>*>(z), w, true, nrhs, h->stream);
+        } else if constexpr (std::is_same<TV, float>::value) {
+            return dslash<float, float>(h, reinterpret_cast<const cplx<float>*>(z), nullptr, w, nrhs);
+        } else {
+            return dslash<double, TZ>(h, z, nullptr, reinterpret_cast<cplx<double>*>(w), nrhs);
         }
-        return dslash<double, TZ>(h, z, nullptr, reinterpret_cast<cplx<double>*>(w), nrhs);
     };
     P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int { return dslash<double, double>(h, z, nullptr, w, nrhs); };
     P.M = [&](const cplx<TV>* v, cplx<TZ>* z) -> int {
@@ -1076,7 +1155,7 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
         if (std::is_same<TV, dwf>::value) {
             DD_TRY(convert_dw2f(reinterpret_cast<const cplx<dwf>*>(v), reinterpret_cast<float*>(rT), 2 * fld * nrhs, st));
             r = rT;
-        } else if (sizeof(TZ) == 8) {
+        } else if (std::is_same<TV, TZ>::value) {
             r = reinterpret_cast<const cplx<TZ>*>(v);
         } else {
             DD_TRY((convert<TZ, double>(reinterpret_cast<const double*>(v), reinterpret_cast<TZ*>(rT), 2 * fld * nrhs, st)));
@@ -1096,6 +1175,12 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     P.w = h->ws_outer[2].as<cplx<TV>>();
     P.wB = sep ? h->ws_outer[4].as<cplx<double>>() : reinterpret_cast<cplx<double>*>(P.w);
     P.enabled_host = nullptr;
+    if (std::is_same<TV, float>::value) {
+        // refinement: FP32 cycles, each ended at cycle_tol relative reduction (or n_kv steps),
+        // with the FP64 iterate updated and the FP64 true residual formed between cycles
+        P.lean = true;
+        P.cycle_tol = h->p.cycle_tol;
+    }
     return krylov<double, TV, TZ>(h, h->ko, P, R);
 }
 
@@ -1128,8 +1213,11 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
         }
     }
     if (p.n_vec < 1 || p.n_vec > 32 || p.nu < 0 || p.mr_steps < 0 || p.n_kv < 1 || p.coarse_restart < 1 ||
-        p.precision < DDAMG_PREC_DOUBLE || p.precision > DDAMG_PREC_HALF || p.n_inv < 0) {
-        set_error("parameter out of range (1 <= n_vec <= 32, n_kv >= 1, coarse_restart >= 1, nu, mr_steps, n_inv >= 0)");
+        p.precision < DDAMG_PREC_DOUBLE || p.precision > DDAMG_PREC_HALF || p.n_inv < 0 ||
+        (p.outer != DDAMG_OUTER_DW && p.outer != DDAMG_OUTER_REFINE) ||
+        (p.outer == DDAMG_OUTER_REFINE && !(p.cycle_tol > 0 && p.cycle_tol < 1))) {
+        set_error("parameter out of range (1 <= n_vec <= 32, n_kv >= 1, coarse_restart >= 1, nu, mr_steps, n_inv >= 0, "
+                  "outer in {0, 1}, 0 < cycle_tol < 1)");
         return DDAMG_ERR_INVALID_ARG;
     }
     long long vb = (long long)p.block[0] * p.block[1] * p.block[2] * p.block[3];
@@ -1268,6 +1356,8 @@ void ddamg_default_params(ddamg_params* p) {
     p->rebuild_after_last = 1;
     p->seed = 1;
     p->time_limit_s = 0;
+    p->outer = DDAMG_OUTER_REFINE;
+    p->cycle_tol = 1e-5;
 }
 
 const char* ddamg_error_string(int s) {
@@ -1348,8 +1438,22 @@ static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, d
     h->coarse_iters = 0;
     h->vcycles = 0;
     h->coarse_seconds = 0;
+    // a zero initial guess (the paper's choice) needs no initial residual product
+    bool x0_zero = false;
+    {
+        DD_TRY(h->ko.alloc(std::max(nrhs, h->ko.nrhs), std::max(1, h->p.n_kv)));
+        DD_TRY((multidot<double, double>(xi, 0, fld, 1, xi, fld, fld, nrhs, h->ko.nrm, 1, h->ko.dscr, h->stream)));
+        std::vector<cplx<double>> zn(nrhs);
+        DD_CUDA(cudaMemcpyAsync(zn.data(), h->ko.nrm, sizeof(cplx<double>) * nrhs, cudaMemcpyDeviceToHost, h->stream));
+        DD_CUDA(cudaStreamSynchronize(h->stream));
+        x0_zero = true;
+        for (int r = 0; r < nrhs; ++r)
+            if (zn[r].re != 0.0) x0_zero = false;
+    }
     KrylovResult R;
-    int rc = h->single() ? solve_T<float, dwf>(h, bi, xi, nrhs, tol, false, R) : solve_T<double, double>(h, bi, xi, nrhs, tol, false, R);
+    int rc = !h->single() ? solve_T<double, double>(h, bi, xi, nrhs, tol, x0_zero, R)
+             : h->p.outer == DDAMG_OUTER_REFINE ? solve_T<float, float>(h, bi, xi, nrhs, tol, x0_zero, R)
+                                                : solve_T<float, dwf>(h, bi, xi, nrhs, tol, x0_zero, R);
     if (rc) return rc;
     DD_TRY(fine_out<double>(h, xi, z, nrhs));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

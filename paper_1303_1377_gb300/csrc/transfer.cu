@@ -14,104 +14,183 @@ namespace ddamg {
 
 // ---------------------------------------------------------------------------
 // restriction out[r][c][h*N + j] = sum_{x in c, k in half h} conj(P_j[k][x]) in[r][k][x]
-// CTA = (block c, rhs r), one thread per site of the block.
+// CTA = (block c, group of R right-hand sides), one thread per site of the block:
+// every P_j entry loaded once serves R right-hand sides.  The 4R partial sums of one
+// j are reduced over the warp by recursive halving (each lane keeps half of its
+// values and trades the other half with its partner, so 4R values cost about 4R
+// shuffles, not 4R log2(32)), then over the warps through shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, typename Tp>
+template <int K>
+__device__ __forceinline__ int bitrev_idx(int lane) {
+    // value index held by a lane after the halving levels 1, 2, ..., K/2
+    int q = 0;
+#pragma unroll
+    for (int m = 1, b = K >> 1; m < K; m <<= 1, b >>= 1)
+        if (lane & m) q |= b;
+    return q;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ T warp_transpose_sum(T (&v)[K], int lane) {
+    // on return lane l holds the warp sum of value bitrev_idx<K>(l & (K-1))
+#pragma unroll
+    for (int m = 1, half = K >> 1; half >= 1; m <<= 1, half >>= 1) {
+        const bool up = lane & m;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            T send = up ? v[q] : v[q + half];
+            T keep = up ? v[q + half] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    T s = v[0];
+#pragma unroll
+    for (int m = K; m < 32; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    return s;
+}
+
+template <typename T, typename Tp, int R>
 __global__ void restrict_kernel(Geom g, const cplx<Tp>* __restrict__ P, int N, const cplx<T>* __restrict__ in,
-                                cplx<T>* __restrict__ out, int nrhs) {
+                                cplx<T>* __restrict__ out, int r0, int ngroups) {
     // accumulation in the V-cycle precision T (FP64 arithmetic is a small fraction of FP32 on GB300)
+    constexpr int K = 4 * R;
     extern __shared__ unsigned char smem_raw[];
-    T* red = reinterpret_cast<T*>(smem_raw);  // [nwarps][4N]
-    const int r = blockIdx.x % nrhs;
-    const int c = blockIdx.x / nrhs;
+    T* red = reinterpret_cast<T*>(smem_raw);  // [nwarps][N][K]
+    const int rb = r0 + (blockIdx.x % ngroups) * R;
+    const int c = blockIdx.x / ngroups;
     const int l = threadIdx.x;
     const bool act = l < g.Vb;
     const int i = c * g.Vb + l;
-    const cplx<T>* inr = in + (size_t)r * 12 * g.V;
-    cplx<T> x[12];
+    cplx<T> x[R][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) x[k] = act ? inr[(size_t)k * g.V + i] : czero<T>();
+    for (int u = 0; u < R; ++u) {
+        const cplx<T>* inr = in + (size_t)(rb + u) * 12 * g.V;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) x[u][k] = act ? inr[(size_t)k * g.V + i] : czero<T>();
+    }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int myq = bitrev_idx<K>(lane & (K - 1));
     for (int j = 0; j < N; ++j) {
-        cplx<T> s0 = czero<T>(), s1 = czero<T>();
+        T v[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] = 0;
         if (act) {
             const cplx<Tp>* pj = P + (size_t)j * 12 * g.V;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) cmac_conj(s0, ccast<T>(pj[(size_t)k * g.V + i]), x[k]);
+            for (int k = 0; k < 12; ++k) {
+                const cplx<T> p = ccast<T>(pj[(size_t)k * g.V + i]);
+                const int o = k < 6 ? 0 : 2;
 #pragma unroll
-            for (int k = 6; k < 12; ++k) cmac_conj(s1, ccast<T>(pj[(size_t)k * g.V + i]), x[k]);
+                for (int u = 0; u < R; ++u) {
+                    // conj(p) * x
+                    v[4 * u + o] += p.re * x[u][k].re + p.im * x[u][k].im;
+                    v[4 * u + o + 1] += p.re * x[u][k].im - p.im * x[u][k].re;
+                }
+            }
         }
-        s0.re = warp_sum(s0.re);
-        s0.im = warp_sum(s0.im);
-        s1.re = warp_sum(s1.re);
-        s1.im = warp_sum(s1.im);
-        if (lane == 0) {
-            T* q = red + (size_t)w * 4 * N + 4 * j;
-            q[0] = s0.re;
-            q[1] = s0.im;
-            q[2] = s1.re;
-            q[3] = s1.im;
-        }
+        T s = warp_transpose_sum<T, K>(v, lane);
+        if (lane < K) red[((size_t)w * N + j) * K + myq] = s;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 4 * N; q += blockDim.x) {
+    for (int q = threadIdx.x; q < K * N; q += blockDim.x) {
         T s = 0;
-        for (int ww = 0; ww < nw; ++ww) s += red[(size_t)ww * 4 * N + q];
-        int j = q >> 2, h = (q >> 1) & 1, im = q & 1;  // q = 4 j + 2 h + im
-        T* o = reinterpret_cast<T*>(out + ((size_t)r * g.NB + c) * (2 * N) + h * N + j);
+        for (int ww = 0; ww < nw; ++ww) s += red[(size_t)ww * K * N + q];
+        const int j = q / K, t = q % K;
+        const int u = t >> 2, h = (t >> 1) & 1, im = t & 1;  // t = 4 u + 2 h + im
+        T* o = reinterpret_cast<T*>(out + ((size_t)(rb + u) * g.NB + c) * (2 * N) + h * N + j);
         o[im] = s;
     }
 }
 
+template <typename T, typename Tp, int R>
+static int launch_restrict_r(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int r0, int ngroups,
+                             cudaStream_t st) {
+    const int nt = ((g.Vb + 31) / 32) * 32;
+    const long long nblk = (long long)g.NB * ngroups;
+    size_t sm = (size_t)(nt / 32) * 4 * R * N * sizeof(T);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(restrict_kernel<T, Tp, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    restrict_kernel<T, Tp, R><<<(unsigned)nblk, nt, sm, st>>>(g, P, N, in, out, r0, ngroups);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// FP32 (and half-P) restriction takes 4 right-hand sides per CTA, FP64 one (register budget)
 template <typename T, typename Tp>
 int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st) {
-    const int nt = ((g.Vb + 31) / 32) * 32;
-    const long long nblk = (long long)g.NB * nrhs;
-    size_t sm = (size_t)(nt / 32) * 4 * N * sizeof(T);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(restrict_kernel<T, Tp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    restrict_kernel<T, Tp><<<(unsigned)nblk, nt, sm, st>>>(g, P, N, in, out, nrhs);
-    DD_CHECK_LAUNCH();
+    int r0 = 0;
+    if constexpr (sizeof(T) == 4) if (nrhs >= 4) {
+        { int e_ = (launch_restrict_r<T, Tp, 4>(g, P, N, in, out, 0, nrhs / 4, st)); if (e_) return e_; }
+        r0 = nrhs / 4 * 4;
+    }
+    if (r0 < nrhs) { int e_ = (launch_restrict_r<T, Tp, 1>(g, P, N, in, out, r0, nrhs - r0, st)); if (e_) return e_; }
     return 0;
 }
 
 // ---------------------------------------------------------------------------
 // prolongation out[r][k][x] = sum_j P_j[k][x] in[r][c(x)][h(k)*N + j]
+// CTA = (block c, group of R right-hand sides); every P_j entry loaded once serves R.
 // ---------------------------------------------------------------------------
-template <typename T, typename Tp>
+template <typename T, typename Tp, int R>
 __global__ void prolong_kernel(Geom g, const cplx<Tp>* __restrict__ P, int N, const cplx<T>* __restrict__ in,
-                               cplx<T>* __restrict__ out, int nrhs) {
+                               cplx<T>* __restrict__ out, int r0, int ngroups) {
     extern __shared__ unsigned char smem_raw[];
-    cplx<T>* e = reinterpret_cast<cplx<T>*>(smem_raw);  // [2N]
-    const int r = blockIdx.x % nrhs;
-    const int c = blockIdx.x / nrhs;
-    const cplx<T>* src = in + ((size_t)r * g.NB + c) * (2 * N);
-    for (int q = threadIdx.x; q < 2 * N; q += blockDim.x) e[q] = src[q];
+    cplx<T>* e = reinterpret_cast<cplx<T>*>(smem_raw);  // [R][2N]
+    const int rb = r0 + (blockIdx.x % ngroups) * R;
+    const int c = blockIdx.x / ngroups;
+    for (int q = threadIdx.x; q < 2 * N * R; q += blockDim.x) {
+        const int u = q / (2 * N), t = q % (2 * N);
+        e[q] = in[((size_t)(rb + u) * g.NB + c) * (2 * N) + t];
+    }
     __syncthreads();
     const int l = threadIdx.x;
     if (l >= g.Vb) return;
     const int i = c * g.Vb + l;
-    cplx<T> acc[12];
+    cplx<T> acc[R][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = czero<T>();
+    for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[u][k] = czero<T>();
     for (int j = 0; j < N; ++j) {
         const cplx<Tp>* pj = P + (size_t)j * 12 * g.V;
-        cplx<T> e0 = e[j], e1 = e[N + j];
+        cplx<T> e0[R], e1[R];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) cmac(acc[k], ccast<T>(pj[(size_t)k * g.V + i]), e0);
+        for (int u = 0; u < R; ++u) {
+            e0[u] = e[u * 2 * N + j];
+            e1[u] = e[u * 2 * N + N + j];
+        }
 #pragma unroll
-        for (int k = 6; k < 12; ++k) cmac(acc[k], ccast<T>(pj[(size_t)k * g.V + i]), e1);
+        for (int k = 0; k < 12; ++k) {
+            const cplx<T> p = ccast<T>(pj[(size_t)k * g.V + i]);
+#pragma unroll
+            for (int u = 0; u < R; ++u) cmac(acc[u][k], p, k < 6 ? e0[u] : e1[u]);
+        }
     }
-    cplx<T>* o = out + (size_t)r * 12 * g.V;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) o[(size_t)k * g.V + i] = acc[k];
+    for (int u = 0; u < R; ++u) {
+        cplx<T>* o = out + (size_t)(rb + u) * 12 * g.V;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[(size_t)k * g.V + i] = acc[u][k];
+    }
+}
+
+template <typename T, typename Tp, int R>
+static int launch_prolong_r(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int r0, int ngroups,
+                            cudaStream_t st) {
+    const int nt = ((g.Vb + 31) / 32) * 32;
+    const long long nblk = (long long)g.NB * ngroups;
+    prolong_kernel<T, Tp, R><<<(unsigned)nblk, nt, 2 * N * R * sizeof(cplx<T>), st>>>(g, P, N, in, out, r0, ngroups);
+    DD_CHECK_LAUNCH();
+    return 0;
 }
 
 template <typename T, typename Tp>
 int launch_prolong(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st) {
-    const int nt = ((g.Vb + 31) / 32) * 32;
-    const long long nblk = (long long)g.NB * nrhs;
-    prolong_kernel<T, Tp><<<(unsigned)nblk, nt, 2 * N * sizeof(cplx<T>), st>>>(g, P, N, in, out, nrhs);
-    DD_CHECK_LAUNCH();
+    int r0 = 0;
+    if constexpr (sizeof(T) == 4) if (nrhs >= 4) {
+        { int e_ = (launch_prolong_r<T, Tp, 4>(g, P, N, in, out, 0, nrhs / 4, st)); if (e_) return e_; }
+        r0 = nrhs / 4 * 4;
+    }
+    if (r0 < nrhs) { int e_ = (launch_prolong_r<T, Tp, 1>(g, P, N, in, out, r0, nrhs - r0, st)); if (e_) return e_; }
     return 0;
 }
 

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libddamg.so")
 
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
+OUTER_DW, OUTER_REFINE = 0, 1
 
 STATUS = {
     0: "OK",
@@ -62,6 +63,8 @@ class Params(C.Structure):
         ("rebuild_after_last", C.c_int),
         ("seed", C.c_uint64),
         ("time_limit_s", C.c_double),
+        ("outer", C.c_int),
+        ("cycle_tol", C.c_double),
     ]
 
 

@@ -43,6 +43,8 @@ def test_binding_structs_match_header(libpath):
     assert (p.n_inv, p.n_vec, tuple(p.block), p.coarse_tol, p.n_kv, p.tol, p.nu, p.mr_steps, p.coarse_restart) == (
         6, 20, (4, 4, 4, 4), 5e-2, 25, 1e-10, 2, 4, 30)
     assert ddamg.lib.ddamg_error_string(-4) == b"not converged"
+    # mixed-precision outer scheme (no counterpart in the paper)
+    assert (p.outer, p.cycle_tol) == (ddamg.OUTER_REFINE, 1e-5)
 
 
 def test_invalid_lattice_rejected_without_gpu_work(libpath):
@@ -56,3 +58,16 @@ def test_invalid_lattice_rejected_without_gpu_work(libpath):
     with pytest.raises(ddamg.DDAMGError) as e:
         ddamg.Solver((12, 12, 12, 12), U, 0.0, 1.0, p, setup=False)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("kw", [{"outer": 2}, {"cycle_tol": 0.0}, {"cycle_tol": 1.0}])
+def test_invalid_outer_scheme_rejected_without_gpu_work(libpath, kw):
+    import numpy as np
+
+    from paper_1303_1377_gb300 import ddamg
+
+    p = ddamg.default_params(block=(2, 2, 2, 2), **kw)
+    U = np.zeros((4 ** 4, 4, 3, 3), dtype=np.complex128)
+    with pytest.raises(ddamg.DDAMGError) as e:
+        ddamg.Solver((4, 4, 4, 4), U, 0.0, 1.0, p, setup=False)
+    assert e.value.status == -1 and "cycle_tol" in str(e.value)

@@ -49,8 +49,8 @@ class Case:
         self.v = synth.random_test_vectors(dims, N, seed=102)
         self.dd = dd
 
-    def solver(self, prec, vectors=None):
-        p = self.dd.default_params(n_vec=self.N, block=self.block, precision=prec, nu=2)
+    def solver(self, prec, vectors=None, **kw):
+        p = self.dd.default_params(n_vec=self.N, block=self.block, precision=prec, nu=2, **kw)
         s = self.dd.Solver(self.dims, self.U, self.m0, CSW, p, setup=False)
         s.setup_from_vectors(self.v if vectors is None else vectors)
         return s
@@ -91,6 +91,17 @@ def test_sap(name, nu, dd):
         assert relerr(s.apply_sap(b, nu), ref) < 1e-12
     with c.solver(dd.PREC_SINGLE) as s:
         assert relerr(s.apply_sap(b, nu), ref) < 2e-5  # FP32, iterated MR steps
+
+
+def test_sap_four_rhs_lanes_with_partial_group(dd):
+    """FP32 SAP with 5 right-hand sides on 4^4 blocks: one full group of four lanes and one
+    group with a single active lane, against the oracle right-hand side by right-hand side."""
+    c = case("8^4/4^4", dd)
+    sap = SAP(c.D, c.block, mr_steps=4)
+    b = synth.gaussian_spinors(c.dims, 5, seed=114)
+    ref = np.stack([sap.apply(b[r], 2) for r in range(5)])
+    with c.solver(dd.PREC_SINGLE) as s:
+        assert relerr(s.apply_sap(b, 2), ref) < 2e-5
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -157,14 +168,16 @@ def test_half_precision_operators(dd):
         assert relerr(s.coarse_solve(e, fixed_iters=6), np.stack([cs.solve(e[r], fixed_iters=6) for r in range(5)])) < 2e-2
 
 
-@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
-def test_solve_matches_oracle(prec, dd):
-    """Oracle setup (Algorithm 2) -> same vectors on the GPU -> FGMRES solves agree."""
+@pytest.mark.parametrize("prec,outer", [("DOUBLE", "DW"), ("SINGLE", "DW"), ("SINGLE", "REFINE"), ("HALF", "DW"),
+                                        ("HALF", "REFINE")])
+def test_solve_matches_oracle(prec, outer, dd):
+    """Oracle setup (Algorithm 2) -> same vectors on the GPU -> FGMRES solves agree
+    (both outer schemes of the mixed-precision modes)."""
     c = case("4^4/2^4", dd)
     mg = TwoLevel(c.D, OParams(N=c.N, agg_block=c.block, sap_block=c.block, n_inv=2, nu=2))
     vecs = mg.setup(c.v)
     b = synth.gaussian_spinors(c.dims, 2, seed=109)
-    with c.solver(getattr(dd, "PREC_" + prec), vectors=vecs) as s:
+    with c.solver(getattr(dd, "PREC_" + prec), vectors=vecs, outer=getattr(dd, "OUTER_" + outer)) as s:
         z, st, rc = s.solve(b)
     assert rc == 0
     for q in range(2):
@@ -190,6 +203,23 @@ def test_gpu_setup_solve_8x8x8x8(prec, dd):
     assert rc == 0
     res = np.linalg.norm(b[0] - D.apply(z[0])) / np.linalg.norm(b[0])
     assert res <= 1e-10, res
+
+
+@pytest.mark.parametrize("cycle_tol", [0.3, 1e-3])
+def test_refinement_cycles(cycle_tol, dd):
+    """FP32 cycles with FP64 residual correction: a loose per-cycle reduction forces several
+    restarts, each started from the FP64 true residual; the result still has an FP64 relative
+    residual <= 1e-10 and agrees with the oracle's solve."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 2, seed=113)
+    with c.solver(dd.PREC_SINGLE, outer=dd.OUTER_REFINE, cycle_tol=cycle_tol) as s:
+        z, st, rc = s.solve(b)
+    assert rc == 0
+    # one V-cycle step reduces this easy system's residual by about 1e-2, so a cycle ends after one
+    # step at cycle_tol 0.3 (>= 4 restarts to 1e-10) and after two or more at 1e-3 (>= 1 restart)
+    assert st[0]["restarts"] >= (4 if cycle_tol > 0.1 else 1)
+    for q in range(2):
+        assert np.linalg.norm(b[q] - c.D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
 
 
 def test_batch_equals_single_solves(dd):

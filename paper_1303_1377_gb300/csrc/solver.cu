@@ -915,6 +915,7 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     P.fixed = fixed_iters > 0;
     P.maxiter = fixed_iters > 0 ? fixed_iters : h->p.coarse_maxiter;
     P.reorth = false;
+    P.lean = std::is_same<T, float>::value;  // FP32 kernels with the norm fused into the update
     P.Vb = basis;
     P.Zb = nullptr;
     P.w = w;

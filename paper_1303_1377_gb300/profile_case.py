@@ -3,8 +3,9 @@
 usage: python -m paper_1303_1377_gb300.profile_case [--dims 24,24,24,24] [--precision half] [--nrhs 12]
 
 It builds D for a synthetic gauge field, an interpolation from seeded random test
-vectors, then applies one SAP iteration, three steps of the odd-even coarse GMRES
-and one double-word Dslash to nrhs right-hand sides resident on the GPU.
+vectors, then applies one SAP iteration, three steps of the odd-even coarse GMRES,
+one double-word Dslash, one FP32 Dslash, one restriction and one prolongation to
+nrhs right-hand sides resident on the GPU.
 """
 from __future__ import annotations
 
@@ -33,6 +34,8 @@ def main():
     s.coarse_solve(e, fixed_iters=3)
     if prec != ddamg.PREC_DOUBLE:
         s.apply_D_mixed(x.to(torch.complex64))
+        s.apply_D_f32(x.to(torch.complex64))
+    s.prolong(s.restrict(x))
     torch.cuda.synchronize()
     s.close()
     print("ok")

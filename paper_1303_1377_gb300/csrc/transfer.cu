@@ -70,6 +70,7 @@ __global__ void restrict_kernel(Geom g, const cplx<Tp>* __restrict__ P, int N, c
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int myq = bitrev_idx<K>(lane & (K - 1));
+#pragma unroll 2
     for (int j = 0; j < N; ++j) {
         T v[K];
 #pragma unroll
@@ -114,13 +115,13 @@ static int launch_restrict_r(const Geom& g, const cplx<Tp>* P, int N, const cplx
     return 0;
 }
 
-// FP32 (and half-P) restriction takes 4 right-hand sides per CTA, FP64 one (register budget)
+// FP32 (and half-P) restriction takes 2 right-hand sides per CTA, FP64 one (register budget)
 template <typename T, typename Tp>
 int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st) {
     int r0 = 0;
-    if constexpr (sizeof(T) == 4) if (nrhs >= 4) {
-        { int e_ = (launch_restrict_r<T, Tp, 4>(g, P, N, in, out, 0, nrhs / 4, st)); if (e_) return e_; }
-        r0 = nrhs / 4 * 4;
+    if constexpr (sizeof(T) == 4) if (nrhs >= 2) {
+        { int e_ = (launch_restrict_r<T, Tp, 2>(g, P, N, in, out, 0, nrhs / 2, st)); if (e_) return e_; }
+        r0 = nrhs / 2 * 2;
     }
     if (r0 < nrhs) { int e_ = (launch_restrict_r<T, Tp, 1>(g, P, N, in, out, r0, nrhs - r0, st)); if (e_) return e_; }
     return 0;

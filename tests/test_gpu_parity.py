@@ -68,15 +68,15 @@ def case(name, dd):
 @pytest.mark.parametrize("name", list(CASES))
 def test_dslash_fp64_fp32(name, dd):
     c = case(name, dd)
-    x = synth.gaussian_spinors(c.dims, 3, seed=103)
-    ref = np.stack([c.D.apply(x[r]) for r in range(3)])
+    x = synth.gaussian_spinors(c.dims, 6, seed=103)  # FP32: one group of four lanes and a partial one
+    ref = np.stack([c.D.apply(x[r]) for r in range(6)])
     with c.solver(dd.PREC_SINGLE) as s:
         assert relerr(s.apply_D(x), ref) < 1e-13
         y32 = s.apply_D_f32(x.astype(np.complex64))
         assert relerr(y32, ref) < 2e-6
         # double-word path: exact FP32 input, FP64-accurate output
         x32 = x.astype(np.complex64)
-        ref32 = np.stack([c.D.apply(x32[r].astype(np.complex128)) for r in range(3)])
+        ref32 = np.stack([c.D.apply(x32[r].astype(np.complex128)) for r in range(6)])
         assert relerr(s.apply_D_mixed(x32), ref32) < 1e-13
 
 

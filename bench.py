@@ -38,6 +38,7 @@ WORKLOADS = {
 }
 C_SW = 1.0
 WORKLOADS_JSON = os.path.join(ROOT, "paper_1303_1377_gb300", "workloads.json")
+TRAFFIC_JSON = os.path.join(ROOT, "paper_1303_1377_gb300", "ncu_traffic.json")
 
 
 def workload_m0(w):
@@ -298,7 +299,8 @@ def main():
     sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     fp32_peak_tf = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ridge = fp32_peak_tf * 1e12 / (peak * 1e9)
-    traffic = json.load(open(WORKLOADS_JSON)).get("ncu_traffic", {}).get(f"{args.workload}/{args.precision}/{dominant}")
+    tr = json.load(open(TRAFFIC_JSON)).get(f"{args.workload}/{args.precision}/{dominant}")
+    traffic = tr["bytes_per_launch"] if tr else None
     if flops_pl > 0 and flops_pl / bytes_pl > ridge:
         ach = flops_pl / sec / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": fp32_peak_tf,

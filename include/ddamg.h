@@ -62,14 +62,17 @@ typedef enum {
 
 /* Outer iteration of SINGLE and HALF mode (no counterpart in the paper, which
  * keeps the whole FGMRES in FP64; FP64 arithmetic runs at about 1/60 of FP32 on
- * this GPU).  Both certify the result with the FP64 residual b - D z. */
+ * this GPU).  Both certify the result with the true residual b - D z, accurate to
+ * about 2^-48 relative to |D| |z|. */
 typedef enum {
     DDAMG_OUTER_DW = 0,    /* one FGMRES(n_kv): double-word (~48-bit) Arnoldi basis and products D z,
                               FP64 iterate; true FP64 residual at every restart */
     DDAMG_OUTER_REFINE = 1 /* FGMRES cycles in FP32 (basis, D z, Gram-Schmidt), each ended once every
                               right-hand side has reduced its residual by cycle_tol (or after n_kv
-                              steps); between cycles the FP64 iterate is updated and the FP64 true
-                              residual b - D z starts the next cycle */
+                              steps); between cycles the FP64 iterate is updated and the true
+                              residual b - D z starts the next cycle.  Here D z is formed without
+                              FP64 arithmetic: z = z_h + z_l (an FP32 pair, ~2^-48 relative),
+                              D z_h in double-word arithmetic, D z_l in FP32, b - D z in FP64 */
 } ddamg_outer;
 
 typedef struct {

@@ -697,6 +697,42 @@ int scale_f32(cplx<float>* w, const cplx<double>* scale, size_t n, int nrhs, cud
     return 0;
 }
 
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi): the pair holds x to about 2^-48 relative
+__global__ void split_f64_kernel(const double2* __restrict__ x, float2* __restrict__ hi, float2* __restrict__ lo, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = x[q];
+        const float hr = (float)v.x, hm = (float)v.y;
+        hi[q] = make_float2(hr, hm);
+        lo[q] = make_float2((float)(v.x - (double)hr), (float)(v.y - (double)hm));
+    }
+}
+int split_f64(const cplx<double>* x, cplx<float>* hi, cplx<float>* lo, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    split_f64_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(hi),
+                                             reinterpret_cast<float2*>(lo), n);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// w += t (FP64 += FP32)
+__global__ void add_f32_kernel(double2* __restrict__ w, const float2* __restrict__ t, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        double2 a = w[q];
+        const float2 b = t[q];
+        a.x += (double)b.x;
+        a.y += (double)b.y;
+        w[q] = a;
+    }
+}
+int add_f32(cplx<double>* w, const cplx<float>* t, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    add_f32_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<double2*>(w), reinterpret_cast<const float2*>(t), n);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
 // Reorthogonalisation test of classical Gram-Schmidt (the DGKS criterion with
 // threshold eta): request a second pass when, for any active right-hand side,
 // ||w after||^2 < eta^2 ||w before||^2.

@@ -1150,7 +1150,21 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
             return dslash<double, TZ>(h, z, nullptr, reinterpret_cast<cplx<double>*>(w), nrhs);
         }
     };
-    P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int { return dslash<double, double>(h, z, nullptr, w, nrhs); };
+    P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int {
+        if constexpr (std::is_same<TV, float>::value) {
+            // D z for the FP64 iterate without FP64 arithmetic: z = z_h + z_l (FP32 pair, ~2^-48),
+            // D z_h in double-word arithmetic (exact products, FP64-accurate sums), D z_l in FP32
+            // (its rounding is ~2^-24 of a term already ~2^-24 smaller), summed in FP64
+            cplx<float>* zh = h->ws_outer[2].as<cplx<float>>();
+            cplx<float>* zl = h->ws_outer[3].as<cplx<float>>();
+            DD_TRY(split_f64(z, zh, zl, fld * nrhs, st));
+            DD_TRY(dslash_dw(h, zh, w, nrhs));
+            DD_TRY((dslash<float, float>(h, zl, nullptr, zh, nrhs)));
+            return add_f32(w, zh, fld * nrhs, st);
+        } else {
+            return dslash<double, double>(h, z, nullptr, w, nrhs);
+        }
+    };
     P.M = [&](const cplx<TV>* v, cplx<TZ>* z) -> int {
         const cplx<TZ>* r;
         if (std::is_same<TV, dwf>::value) {

@@ -539,8 +539,9 @@ __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4*
         for (int i = 0; i < KB; ++i) {
             if (i < k) {
                 const float4 a = Ar[i * istride4 + e];  // conj(a) w for both complex numbers
-                fr[i] = fmaf(a.x, wv.x, fmaf(a.y, wv.y, fmaf(a.z, wv.z, fmaf(a.w, wv.w, fr[i]))));
-                fi[i] = fmaf(a.x, wv.y, fmaf(-a.y, wv.x, fmaf(a.z, wv.w, fmaf(-a.w, wv.z, fi[i]))));
+                // two independent products per component keep the accumulator chain two FMAs deep
+                fr[i] += fmaf(a.x, wv.x, a.y * wv.y) + fmaf(a.z, wv.z, a.w * wv.w);
+                fi[i] += fmaf(a.x, wv.y, -a.y * wv.x) + fmaf(a.z, wv.w, -a.w * wv.z);
             }
         }
         if (++cnt == kFlush) {
@@ -594,8 +595,6 @@ int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, c
         const unsigned grid = ctas * nrhs;
         if (kk <= 1)
             multidot_f32_kernel<1><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
-        else if (kk <= 4)
-            multidot_f32_kernel<4><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
         else if (kk <= 8)
             multidot_f32_kernel<8><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
         else

@@ -75,6 +75,15 @@ typedef enum {
                               D z_h in double-word arithmetic, D z_l in FP32, b - D z in FP64 */
 } ddamg_outer;
 
+/* Test-vector update in the second phase of the adaptive setup (Sec. 5): after P and
+ * D_c are rebuilt from v_1..v_N, every v_j is updated and normalised. */
+typedef enum {
+    DDAMG_SETUP_DDALPHA = 0, /* Algorithm 2 (DD-alphaAMG setup): v_j <- v_j + C (v_j - D v_j), one V-cycle
+                                iteration on D v = v_j started from v_j */
+    DDAMG_SETUP_IDSETUP = 1  /* Algorithm 1 (inexact-deflation setup): v_j <- C v_j, the same iteration
+                                started from 0 */
+} ddamg_setup_update;
+
 typedef struct {
     int dims[4]; /* L0 (time), L1, L2, L3 */
 } ddamg_lattice;
@@ -98,6 +107,8 @@ typedef struct {
     double time_limit_s;  /* wall-clock limit per solve call, <= 0: none (0) */
     int outer;            /* ddamg_outer of SINGLE and HALF mode (DDAMG_OUTER_REFINE) */
     double cycle_tol;     /* residual reduction of one FP32 cycle of DDAMG_OUTER_REFINE, in (0, 1) (1e-5) */
+    int setup_update;     /* ddamg_setup_update: test-vector update of the setup's second phase
+                             (DDAMG_SETUP_DDALPHA) */
 } ddamg_params;
 
 /* Statistics of one solve (the quantities reported in Tables 3-9). */

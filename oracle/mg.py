@@ -6,12 +6,15 @@ V-cycle with no pre- and nu post-smoothing steps (Sec. 4.2, Eq. iterationmatrix)
 Evaluated as: e_c = D_c^{-1} P^H r (inexact, odd-even GMRES), x = P e_c,
 r' = r - D x, x += M_SAP^(nu) r'.
 
-Setup (Algorithm 1 with the update of Algorithm 2):
+Setup (the loop of Algorithm 1):
   v_1..v_N random;
   for eta = 1..3: for j: v_j <- M_SAP^(eta) v_j
-  for eta = 1..n_inv: (re)build P, D_c from v; for j: v_j <- v_j + C^(nu)(v_j - D v_j); v_j <- v_j/||v_j||
+  for eta = 1..n_inv: (re)build P, D_c from v; for j: v_j <- update(v_j); v_j <- v_j/||v_j||
   and, as the paper is silent on it, a final rebuild of P and D_c from the last vectors
-  (flag rebuild_after_last).
+  (flag rebuild_after_last).  The update is that of Algorithm 2 (the default,
+  setup_update = "ddalpha"): v_j + C^(nu)(v_j - D v_j), one V-cycle iteration on D v = v_j
+  started from v_j; or that of Algorithm 1 (setup_update = "idsetup", the inexact-deflation
+  setup): C^(nu) v_j, the same iteration started from 0.
 
 Solver: FGMRES(n_kv) right-preconditioned by one V-cycle (Sec. 5), tol 1e-10.
 Defaults are Table 1.
@@ -44,6 +47,7 @@ class Params:
     mr_steps: int = 4
     max_outer: int = 10000
     rebuild_after_last: bool = True
+    setup_update: str = "ddalpha"  # "ddalpha" (Algorithm 2) or "idsetup" (Algorithm 1)
     stats: dict = field(default_factory=dict)
 
 
@@ -71,8 +75,16 @@ class TwoLevel:
         r2 = r - self.D.apply(x)
         return x + self.sap.apply(r2, self.p.nu)
 
+    def setup_update(self, v: np.ndarray) -> np.ndarray:
+        """The test-vector update of the setup's second phase, before normalisation."""
+        if self.p.setup_update == "idsetup":
+            return self.vcycle(v)  # Algorithm 1: C^(nu) v
+        if self.p.setup_update != "ddalpha":
+            raise ValueError("setup_update must be 'ddalpha' or 'idsetup'")
+        return v + self.vcycle(v - self.D.apply(v))  # Algorithm 2: v + C^(nu) (v - D v)
+
     def setup(self, v0: np.ndarray):
-        """Algorithm 2 (Algorithm 1 with the modified update)."""
+        """Algorithm 2 (default) or Algorithm 1, per Params.setup_update."""
         v = np.array(v0, dtype=np.complex128, copy=True)
         for eta in (1, 2, 3):
             for j in range(v.shape[0]):
@@ -80,7 +92,7 @@ class TwoLevel:
         for _ in range(self.p.n_inv):
             self.build(v)
             for j in range(v.shape[0]):
-                v[j] = v[j] + self.vcycle(v[j] - self.D.apply(v[j]))
+                v[j] = self.setup_update(v[j])
                 v[j] = v[j] / np.sqrt(np.sum(np.abs(v[j]) ** 2))
         if self.p.rebuild_after_last or self.p.n_inv == 0:
             self.build(v)

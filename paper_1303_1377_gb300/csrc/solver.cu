@@ -1066,10 +1066,17 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
     for (int it = 0; it < h->p.n_inv; ++it) {
         DD_TRY(to64());
         DD_TRY(build_interpolation(h));
-        // v_j <- v_j + C (v_j - D v_j);  v_j <- v_j / ||v_j||
-        DD_TRY((dslash<T, T>(h, v, v, t1, N)));
-        DD_TRY(vcycle<T>(h, t1, t2, N, 0));
-        DD_TRY((lincomb<T, T>(v, fld, 1.0, t2, 0, fld, 1, kb.ones, N, fld, N, nullptr, st)));
+        if (h->p.setup_update == DDAMG_SETUP_IDSETUP) {
+            // Algorithm 1: v_j <- C v_j
+            DD_TRY(vcycle<T>(h, v, t2, N, 0));
+            DD_CUDA(cudaMemcpyAsync(v, t2, sizeof(cplx<T>) * fld * N, cudaMemcpyDeviceToDevice, st));
+        } else {
+            // Algorithm 2: v_j <- v_j + C (v_j - D v_j)
+            DD_TRY((dslash<T, T>(h, v, v, t1, N)));
+            DD_TRY(vcycle<T>(h, t1, t2, N, 0));
+            DD_TRY((lincomb<T, T>(v, fld, 1.0, t2, 0, fld, 1, kb.ones, N, fld, N, nullptr, st)));
+        }
+        // v_j <- v_j / ||v_j||
         DD_TRY((multidot<T, T>(v, 0, fld, 1, v, fld, fld, N, kb.nrm, 1, kb.dscr, st)));
         std::vector<cplx<double>> nn(N);
         DD_CUDA(cudaMemcpyAsync(nn.data(), kb.nrm, sizeof(cplx<double>) * N, cudaMemcpyDeviceToHost, st));
@@ -1230,9 +1237,10 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
     if (p.n_vec < 1 || p.n_vec > 32 || p.nu < 0 || p.mr_steps < 0 || p.n_kv < 1 || p.coarse_restart < 1 ||
         p.precision < DDAMG_PREC_DOUBLE || p.precision > DDAMG_PREC_HALF || p.n_inv < 0 ||
         (p.outer != DDAMG_OUTER_DW && p.outer != DDAMG_OUTER_REFINE) ||
-        (p.outer == DDAMG_OUTER_REFINE && !(p.cycle_tol > 0 && p.cycle_tol < 1))) {
+        (p.outer == DDAMG_OUTER_REFINE && !(p.cycle_tol > 0 && p.cycle_tol < 1)) ||
+        (p.setup_update != DDAMG_SETUP_DDALPHA && p.setup_update != DDAMG_SETUP_IDSETUP)) {
         set_error("parameter out of range (1 <= n_vec <= 32, n_kv >= 1, coarse_restart >= 1, nu, mr_steps, n_inv >= 0, "
-                  "outer in {0, 1}, 0 < cycle_tol < 1)");
+                  "outer in {0, 1}, 0 < cycle_tol < 1, setup_update in {0, 1})");
         return DDAMG_ERR_INVALID_ARG;
     }
     long long vb = (long long)p.block[0] * p.block[1] * p.block[2] * p.block[3];
@@ -1373,6 +1381,7 @@ void ddamg_default_params(ddamg_params* p) {
     p->time_limit_s = 0;
     p->outer = DDAMG_OUTER_REFINE;
     p->cycle_tol = 1e-5;
+    p->setup_update = DDAMG_SETUP_DDALPHA;
 }
 
 const char* ddamg_error_string(int s) {

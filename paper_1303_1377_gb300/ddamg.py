@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libddamg.so")
 
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OUTER_DW, OUTER_REFINE = 0, 1
+SETUP_DDALPHA, SETUP_IDSETUP = 0, 1
 
 STATUS = {
     0: "OK",
@@ -65,6 +66,7 @@ class Params(C.Structure):
         ("time_limit_s", C.c_double),
         ("outer", C.c_int),
         ("cycle_tol", C.c_double),
+        ("setup_update", C.c_int),
     ]
 
 

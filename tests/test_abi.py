@@ -45,6 +45,7 @@ def test_binding_structs_match_header(libpath):
     assert ddamg.lib.ddamg_error_string(-4) == b"not converged"
     # mixed-precision outer scheme (no counterpart in the paper)
     assert (p.outer, p.cycle_tol) == (ddamg.OUTER_REFINE, 1e-5)
+    assert p.setup_update == ddamg.SETUP_DDALPHA  # Algorithm 2
 
 
 def test_invalid_lattice_rejected_without_gpu_work(libpath):
@@ -60,7 +61,7 @@ def test_invalid_lattice_rejected_without_gpu_work(libpath):
     assert e.value.status == -1
 
 
-@pytest.mark.parametrize("kw", [{"outer": 2}, {"cycle_tol": 0.0}, {"cycle_tol": 1.0}])
+@pytest.mark.parametrize("kw", [{"outer": 2}, {"cycle_tol": 0.0}, {"cycle_tol": 1.0}, {"setup_update": 2}])
 def test_invalid_outer_scheme_rejected_without_gpu_work(libpath, kw):
     import numpy as np
 

@@ -188,6 +188,24 @@ def test_solve_matches_oracle(prec, outer, dd):
         assert st[q]["rel_residual"] <= 1e-10
 
 
+@pytest.mark.parametrize("prec,update,tol", [("DOUBLE", "ddalpha", 1e-8), ("DOUBLE", "idsetup", 1e-8),
+                                             ("SINGLE", "ddalpha", 1e-3)])
+def test_gpu_setup_matches_oracle(prec, update, tol, dd):
+    """The adaptive setup run on the GPU (phase 1: M_SAP^(eta) for eta = 1, 2, 3; then n_inv = 2
+    rebuild-and-update rounds with the update of Algorithm 2 or of Algorithm 1) from the oracle's
+    initial vectors gives the oracle's test vectors: to rounding in FP64, and within the FP32
+    V-cycle's reach in SINGLE mode."""
+    c = case("4^4/2^4", dd)
+    mg = TwoLevel(c.D, OParams(N=c.N, agg_block=c.block, sap_block=c.block, n_inv=2, nu=2, setup_update=update))
+    ref = mg.setup(c.v)
+    p = dd.default_params(n_vec=c.N, block=c.block, precision=getattr(dd, "PREC_" + prec), nu=2, n_inv=2,
+                          setup_update=dd.SETUP_DDALPHA if update == "ddalpha" else dd.SETUP_IDSETUP)
+    with dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False) as s:
+        s.run_setup(c.v)
+        got = s.vectors()
+    assert relerr(got, ref) < tol
+
+
 @pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
 def test_gpu_setup_solve_8x8x8x8(prec, dd):
     """The 8^4 workload (aggregates 4^4, N = 20, nu = 3): GPU adaptive setup + solve;

@@ -74,6 +74,28 @@ def test_vcycle_equals_dense_iteration_matrix(small):
     assert np.linalg.norm(upd.ravel() - (C @ v.ravel() + (np.eye(n) - C @ Dd) @ v.ravel())) < 1e-9 * np.linalg.norm(upd)
 
 
+def test_setup_updates_against_dense_iteration_matrix(small):
+    """The two setup updates against the dense C^(nu) (exact coarse and block solves):
+    Algorithm 1 (inexact deflation) v <- C v; Algorithm 2 v <- C v + (I - C D) v."""
+    D, mg, Dd = small
+    n = Dd.shape[0]
+    P, CGC, Msap = _dense_operators(mg, Dd)
+    C = Msap @ (np.eye(n) - Dd @ CGC) + CGC
+    v = synth.gaussian_spinors(D.lat.dims, 1, seed=45)[0]
+    Cv = C @ v.ravel()
+    try:
+        mg.p.setup_update = "idsetup"
+        u1 = mg.setup_update(v).ravel()
+        mg.p.setup_update = "ddalpha"
+        u2 = mg.setup_update(v).ravel()
+    finally:
+        mg.p.setup_update = "ddalpha"
+    assert np.linalg.norm(u1 - Cv) < 1e-9 * np.linalg.norm(Cv)
+    assert np.linalg.norm(u2 - (Cv + v.ravel() - C @ (Dd @ v.ravel()))) < 1e-9 * np.linalg.norm(u2)
+    # the two differ by the V-cycle error propagator applied to v, which is not zero here
+    assert np.linalg.norm(u2 - u1) > 1e-3 * np.linalg.norm(u2)
+
+
 def test_full_solve_2x2x2x2_dense_lu():
     """Whole method on a 2^4 lattice (SAP blocks and aggregates of one site): the FGMRES solution
     agrees with a dense LU and its true residual is below 1e-10."""

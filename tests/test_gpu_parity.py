@@ -319,6 +319,42 @@ def test_n_vec_24_coarse_blocks_48(dd):
             assert max(np.linalg.norm(b[r] - D.apply(z[r])) / np.linalg.norm(b[r]) for r in range(2)) <= 1e-10
 
 
+def test_degenerate_inputs(dd):
+    """Edge cases of the solve: an all-zero right-hand side alone and inside a batch (z = 0, no
+    iterations), a nonzero initial guess (the initial residual path), an empty batch (rejected),
+    and the free field U = 1 (the clover term reduces to (4 + m0) I)."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 3, seed=115)
+    b[1] = 0
+    with c.solver(dd.PREC_SINGLE) as s:
+        z, st, rc = s.solve(b)
+        assert rc == 0
+        assert np.all(z[1] == 0) and st[1]["iterations"] == 0 and st[1]["rel_residual"] == 0
+        for q in (0, 2):
+            assert np.linalg.norm(b[q] - c.D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
+        b2 = synth.gaussian_spinors(c.dims, 2, seed=118)
+        z2, _, rc = s.solve(b2)
+        assert rc == 0
+        zg, stg, rc = s.solve(b2, z=synth.gaussian_spinors(c.dims, 2, seed=116))
+        assert rc == 0
+        for q in range(2):
+            assert np.linalg.norm(b2[q] - c.D.apply(zg[q])) <= 1e-10 * np.linalg.norm(b2[q])
+            assert np.linalg.norm(zg[q] - z2[q]) <= 1e-8 * np.linalg.norm(z2[q])
+        with pytest.raises(dd.DDAMGError) as e:
+            s.solve(b[:0])
+        assert e.value.status == -1
+    dims = (8, 8, 8, 8)
+    U1 = synth.unit_gauge(dims)
+    D1 = DiracOperator(U1, dims, 0.05, CSW)
+    p = dd.default_params(n_vec=6, precision=dd.PREC_SINGLE)
+    bf = synth.gaussian_spinors(dims, 2, seed=117)
+    with dd.Solver(dims, U1, 0.05, CSW, p) as s:
+        z, st, rc = s.solve(bf)
+    assert rc == 0
+    for q in range(2):
+        assert np.linalg.norm(bf[q] - D1.apply(z[q])) <= 1e-10 * np.linalg.norm(bf[q])
+
+
 def test_error_statuses(dd):
     c = case("4^4/2^4", dd)
     p = dd.default_params(n_vec=c.N, block=c.block)

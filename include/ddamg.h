@@ -169,6 +169,28 @@ int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_s
 int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol,
                       ddamg_stats* st);
 
+/* Continuous batching (no counterpart in the paper).  A handle keeps up to n_slots
+ * right-hand sides in flight.  ddamg_slots_cycle runs one outer cycle (one FGMRES cycle
+ * of the handle's outer scheme, on all running slots in lock step); between calls the
+ * host admits right-hand sides into free slots and takes finished ones out, so a new
+ * request waits at most one cycle, not for a whole batch.  A slot is finished (DONE) when
+ * the true residual at the start of a cycle meets tol * ||b|| (params.tol); FAILED means a
+ * non-finite value or max_outer iterations.  Slot storage: 2 * n_slots FP64 fields on the
+ * device, owned by the handle (freed by ddamg_slots_close or ddamg_destroy).  All calls
+ * run on the handle's stream and return after it has synchronised; b and z may be host
+ * or device pointers in the layout of ddamg_solve. */
+typedef enum {
+    DDAMG_SLOT_FREE = 0,
+    DDAMG_SLOT_RUNNING = 1,
+    DDAMG_SLOT_DONE = 2,
+    DDAMG_SLOT_FAILED = 3
+} ddamg_slot_state;
+int ddamg_slots_open(ddamg_handle* h, int n_slots);            /* needs a setup; drops open slots */
+int ddamg_slot_put(ddamg_handle* h, int slot, const double* b);  /* slot must be FREE; z starts at 0 */
+int ddamg_slots_cycle(ddamg_handle* h, int* state, ddamg_stats* st); /* state[n_slots], st[n_slots] out, either may be NULL */
+int ddamg_slot_take(ddamg_handle* h, int slot, double* z);       /* slot DONE or FAILED -> FREE */
+int ddamg_slots_close(ddamg_handle* h);
+
 /* out = D in (Sec. 2.2, FP64) for n_rhs spinor fields. */
 int ddamg_apply_D(ddamg_handle* h, const double* in, double* out, int n_rhs);
 

@@ -217,7 +217,14 @@ struct ddamg_handle {
     int* d_flag = nullptr;
     // workspaces
     Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[5];
-    KrylovBufs kc, ko;  // coarse GMRES, outer FGMRES
+    KrylovBufs kc, ko;
+    // continuous batching: right-hand sides and iterates of the slots (internal order, FP64)
+    int n_slots = 0;
+    cplx<double>* slot_b = nullptr;
+    cplx<double>* slot_x = nullptr;
+    std::vector<int> slot_state;
+    std::vector<long long> slot_iters;
+    std::vector<double> slot_resid;  // coarse GMRES, outer FGMRES
     // stats of the current call
     long long coarse_iters = 0;
     int vcycles = 0;
@@ -591,6 +598,7 @@ struct KrylovProblem {
     bool reorth;           // classical Gram-Schmidt twice
     bool lean = false;     // FP32 basis: one Gram-Schmidt pass, a second one only on heavy cancellation
     double cycle_tol = 0;  // > 0: a cycle ends once every rhs has reduced its residual by this factor
+    int max_cycles = 0;    // > 0: return after this many cycles (x updated, no closing residual)
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
     cplx<TZ>* Zb;          // [m][nrhs][n] when M is set
     cplx<TV>* w;           // [nrhs][n]
@@ -602,6 +610,8 @@ struct KrylovResult {
     std::vector<long long> iters;
     std::vector<double> resid;  // last residual estimate relative to ||b||
     std::vector<double> bnorm;
+    std::vector<int> start_active;  // per rhs at the start of the first cycle (0: converged or not enabled)
+    std::vector<int> flags;         // per rhs: bit 1 = non-finite value met
     int restarts = 0;
     bool nonfinite = false;
     bool converged = true;
@@ -687,6 +697,9 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
     R.iters.assign(nr, 0);
     R.resid.assign(nr, 0.0);
     R.bnorm.assign(nr, 0.0);
+    R.flags.assign(nr, 0);
+    R.start_active.assign(nr, 0);
+    int ncycles = 0;
     // ||b||, targets, enabled
     DD_TRY((multidot<TB, TB>(P.b, 0, n, 1, P.b, n, n, nr, kb.nrm, 1, kb.dscr, st)));
     std::vector<cplx<double>> hb(nr);
@@ -744,12 +757,15 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
         }
         DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaMemcpyAsync(kb.h_resid, s.resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaMemcpyAsync(kb.h_flags, s.flags, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
         DD_CUDA(cudaStreamSynchronize(st));
         int nact = 0;
         for (int r = 0; r < nr; ++r) {
             nact += kb.h_active[r];
             if (en[r]) R.resid[r] = R.bnorm[r] > 0 ? kb.h_resid[r] / R.bnorm[r] : 0.0;
+            R.flags[r] |= kb.h_flags[r];
         }
+        if (ncycles == 0) R.start_active.assign(kb.h_active, kb.h_active + nr);
         if (nact == 0) break;
         if (total >= P.maxiter) {
             R.converged = false;
@@ -854,9 +870,12 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             R.iters[r] += kb.h_steps[r];
             if (kb.h_steps[r] > 0) R.resid[r] = R.bnorm[r] > 0 ? kb.h_resid[r] / R.bnorm[r] : 0.0;
             if (kb.h_flags[r] & 2) R.nonfinite = true;
+            R.flags[r] |= kb.h_flags[r];
         }
         if (P.fixed && total >= P.maxiter) break;
         if (R.nonfinite) break;
+        ++ncycles;
+        if (P.max_cycles > 0 && ncycles >= P.max_cycles) break;
         // restart: V0 = b - A x
         DD_TRY(residual_to_V0());
         ++R.restarts;
@@ -1132,7 +1151,8 @@ static int run_setup(ddamg_handle* h, const double* v0) {
 // TV = basis type: double-word FP32 pairs when the V-cycle is FP32 (GB300's FP64
 // rate is a small fraction of its FP32 rate), FP64 for the all-FP64 path.
 template <typename TZ, typename TV>
-static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R) {
+static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R,
+                   const int* enabled_host = nullptr, int max_cycles = 0) {
     cudaStream_t st = h->stream;
     const size_t fld = (size_t)12 * h->V;
     const int m = h->p.n_kv;
@@ -1196,7 +1216,8 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     P.Zb = h->ws_outer[1].as<cplx<TZ>>();
     P.w = h->ws_outer[2].as<cplx<TV>>();
     P.wB = sep ? h->ws_outer[4].as<cplx<double>>() : reinterpret_cast<cplx<double>*>(P.w);
-    P.enabled_host = nullptr;
+    P.enabled_host = enabled_host;
+    P.max_cycles = max_cycles;
     if (std::is_same<TV, float>::value) {
         // refinement: FP32 cycles, each ended at cycle_tol relative reduction (or n_kv steps),
         // with the FP64 iterate updated and the FP64 true residual formed between cycles
@@ -1508,6 +1529,133 @@ int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_s
 
 int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st) {
     return solve_common(h, b, z, n_rhs, tol, st);
+}
+
+// ---------------------------------------------------------------------------
+// continuous batching: right-hand sides enter and leave a fixed set of slots between
+// outer cycles; every cycle is one lock-step pass of the outer solver over the running slots
+// ---------------------------------------------------------------------------
+static int slot_check(ddamg_handle* h, int slot) {
+    if (!h || h->n_slots == 0) {
+        set_error("no slots: call ddamg_slots_open first");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    if (slot < 0 || slot >= h->n_slots) {
+        set_error("slot index out of range");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    return 0;
+}
+
+int ddamg_slots_close(ddamg_handle* h) {
+    if (!h) return DDAMG_ERR_INVALID_ARG;
+    dfree(h->slot_b);
+    dfree(h->slot_x);
+    h->n_slots = 0;
+    h->slot_state.clear();
+    h->slot_iters.clear();
+    h->slot_resid.clear();
+    return 0;
+}
+
+int ddamg_slots_open(ddamg_handle* h, int n_slots) {
+    DD_TRY(check_ready(h));
+    if (n_slots < 1) {
+        set_error("slots_open: n_slots < 1");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    DD_TRY(ddamg_slots_close(h));
+    const size_t n = (size_t)12 * h->V * n_slots;
+    DD_TRY(dalloc_n(&h->slot_b, n));
+    DD_TRY(dalloc_n(&h->slot_x, n));
+    DD_CUDA(cudaMemsetAsync(h->slot_b, 0, sizeof(cplx<double>) * n, h->stream));
+    DD_CUDA(cudaMemsetAsync(h->slot_x, 0, sizeof(cplx<double>) * n, h->stream));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    h->n_slots = n_slots;
+    h->slot_state.assign(n_slots, DDAMG_SLOT_FREE);
+    h->slot_iters.assign(n_slots, 0);
+    h->slot_resid.assign(n_slots, 0.0);
+    return 0;
+}
+
+int ddamg_slot_put(ddamg_handle* h, int slot, const double* b) {
+    DD_TRY(slot_check(h, slot));
+    if (!b) return DDAMG_ERR_INVALID_ARG;
+    if (h->slot_state[slot] != DDAMG_SLOT_FREE) {
+        set_error("slot_put: the slot is not free (take its result first)");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(fine_in<double>(h, b, 1, h->ws_io[0], h->slot_b + fld * slot));
+    DD_CUDA(cudaMemsetAsync(h->slot_x + fld * slot, 0, sizeof(cplx<double>) * fld, h->stream));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    h->slot_state[slot] = DDAMG_SLOT_RUNNING;
+    h->slot_iters[slot] = 0;
+    h->slot_resid[slot] = 1.0;
+    return 0;
+}
+
+int ddamg_slots_cycle(ddamg_handle* h, int* state, ddamg_stats* st) {
+    DD_TRY(check_ready(h));
+    if (h->n_slots == 0) return slot_check(h, 0);
+    const int S = h->n_slots;
+    std::vector<int> en(S);
+    int nrun = 0;
+    for (int r = 0; r < S; ++r) nrun += (en[r] = h->slot_state[r] == DDAMG_SLOT_RUNNING);
+    h->coarse_iters = 0;
+    h->vcycles = 0;
+    h->coarse_seconds = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    if (nrun > 0) {
+        KrylovResult R;
+        const double tol = h->p.tol;
+        int rc = !h->single() ? solve_T<double, double>(h, h->slot_b, h->slot_x, S, tol, false, R, en.data(), 1)
+                 : h->p.outer == DDAMG_OUTER_REFINE ? solve_T<float, float>(h, h->slot_b, h->slot_x, S, tol, false, R, en.data(), 1)
+                                                    : solve_T<float, dwf>(h, h->slot_b, h->slot_x, S, tol, false, R, en.data(), 1);
+        if (rc) return rc;
+        for (int r = 0; r < S; ++r) {
+            if (!en[r]) continue;
+            h->slot_resid[r] = R.resid[r];
+            if (R.flags[r] & 2) {
+                h->slot_state[r] = DDAMG_SLOT_FAILED;
+            } else if (!R.start_active[r]) {
+                h->slot_state[r] = DDAMG_SLOT_DONE;  // certified by the true residual at the start of this cycle
+            } else {
+                h->slot_iters[r] += R.iters[r];
+                if (h->slot_iters[r] >= h->p.max_outer) h->slot_state[r] = DDAMG_SLOT_FAILED;
+            }
+        }
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int r = 0; r < S; ++r) {
+        if (state) state[r] = h->slot_state[r];
+        if (st) {
+            st[r].iterations = (int)h->slot_iters[r];
+            st[r].restarts = 0;
+            st[r].coarse_iterations = h->coarse_iters;
+            st[r].vcycles = h->vcycles;
+            st[r].rel_residual = h->slot_resid[r];
+            st[r].solve_seconds = secs;
+            st[r].coarse_seconds = h->coarse_seconds;
+            st[r].status = h->slot_state[r] == DDAMG_SLOT_FAILED
+                               ? (h->slot_iters[r] >= h->p.max_outer ? DDAMG_ERR_NOT_CONVERGED : DDAMG_ERR_NONFINITE)
+                               : DDAMG_OK;
+        }
+    }
+    return 0;
+}
+
+int ddamg_slot_take(ddamg_handle* h, int slot, double* z) {
+    DD_TRY(slot_check(h, slot));
+    if (!z) return DDAMG_ERR_INVALID_ARG;
+    if (h->slot_state[slot] != DDAMG_SLOT_DONE && h->slot_state[slot] != DDAMG_SLOT_FAILED) {
+        set_error("slot_take: the slot has no finished result");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    const size_t fld = (size_t)12 * h->V;
+    DD_TRY(fine_out<double>(h, h->slot_x + fld * slot, z, 1));
+    h->slot_state[slot] = DDAMG_SLOT_FREE;
+    return 0;
 }
 
 int ddamg_apply_D(ddamg_handle* h, const double* in, double* out, int n_rhs) {
@@ -1881,6 +2029,8 @@ int ddamg_destroy(ddamg_handle* h) {
     for (auto& s : h->ws_coarse) s.release();
     for (auto& s : h->ws_io) s.release();
     for (auto& s : h->ws_outer) s.release();
+    dfree(h->slot_b);
+    dfree(h->slot_x);
     h->kc.release();
     h->ko.release();
     for (auto& r : h->prof) {

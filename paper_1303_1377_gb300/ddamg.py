@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libddamg.so")
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OUTER_DW, OUTER_REFINE = 0, 1
 SETUP_DDALPHA, SETUP_IDSETUP = 0, 1
+SLOT_FREE, SLOT_RUNNING, SLOT_DONE, SLOT_FAILED = 0, 1, 2, 3
 
 STATUS = {
     0: "OK",
@@ -127,6 +128,11 @@ def _load():
         "ddamg_profile_families": (I, [C.c_char_p, I]),
         "ddamg_launch_count": (LL, []),
         "ddamg_debug_fail_allocs": (None, [I]),
+        "ddamg_slots_open": (I, [P, I]),
+        "ddamg_slot_put": (I, [P, I, P]),
+        "ddamg_slots_cycle": (I, [P, C.POINTER(I), C.POINTER(Stats)]),
+        "ddamg_slot_take": (I, [P, I, P]),
+        "ddamg_slots_close": (I, [P]),
         "ddamg_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -254,6 +260,33 @@ class Solver:
         rc = lib.ddamg_solve_batch(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
         _check(rc, "ddamg_solve_batch", allow=(-4, -5) if allow_fail else ())
         return z, [s.as_dict() for s in st], rc
+
+    # -- continuous batching ------------------------------------------------------
+    def slots_open(self, n_slots: int):
+        _check(lib.ddamg_slots_open(self.h, int(n_slots)), "ddamg_slots_open")
+        self.n_slots = int(n_slots)
+
+    def slot_put(self, slot: int, b):
+        """Admit one right-hand side b[V, 4, 3] into a free slot (initial guess 0)."""
+        b = _host(b, np.complex128)
+        _check(lib.ddamg_slot_put(self.h, int(slot), _ptr(b)), "ddamg_slot_put")
+
+    def slots_cycle(self):
+        """One outer cycle over the running slots; returns (states[n_slots], stats)."""
+        states = (C.c_int * self.n_slots)()
+        st = (Stats * self.n_slots)()
+        _check(lib.ddamg_slots_cycle(self.h, states, st), "ddamg_slots_cycle")
+        return list(states), [x.as_dict() for x in st]
+
+    def slot_take(self, slot: int, out=None):
+        """The solution of a finished slot, which becomes free."""
+        z = out if out is not None else np.empty((self.V, 4, 3), dtype=np.complex128)
+        _check(lib.ddamg_slot_take(self.h, int(slot), _ptr(z)), "ddamg_slot_take")
+        return z
+
+    def slots_close(self):
+        _check(lib.ddamg_slots_close(self.h), "ddamg_slots_close")
+        self.n_slots = 0
 
     # -- operator pieces --------------------------------------------------------
     def _fine_op(self, fn, x, *extra, dtype=np.complex128):

@@ -143,7 +143,17 @@ def oracle_sample(w, m0, fgmres_iters_per_solve, seconds_budget=15.0):
     return 1.0 / per_solve, dict(sample=f"{iters} oracle FGMRES iterations (one point source) on the 8^4 version of the workload "
                                         f"(same eps, c_sw, m0, N_v={w['N']}, 4^4 blocks, nu={w['nu']}; P from seeded random vectors), "
                                         f"{dt:.2f} s/iteration x volume ratio {scale:.0f} x {fgmres_iters_per_solve} FGMRES iterations "
-                                        f"per solve", seconds=time.perf_counter() - t0)
+                                        f"per solve (the oracle's own count on the 8^4 counterpart with the adaptive setup)",
+                seconds=time.perf_counter() - t0)
+
+
+def oracle_iterations(workload):
+    """FGMRES iterations per solve of the oracle's full method (adaptive setup) on the workload's
+    8^4 counterpart, as recorded by oracle/count_iterations.py."""
+    rec = json.load(open(WORKLOADS_JSON)).get("fgmres_iterations_8x8x8x8", {}).get(workload)
+    if not rec:
+        return None, None
+    return int(rec["iterations"]), f"oracle, 8^4 counterpart with the adaptive setup: {rec['iterations']} iterations"
 
 
 def run_reference(args, w):
@@ -152,7 +162,11 @@ def run_reference(args, w):
         return 0
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     m0, _ = workload_m0(w)
-    iters_per_solve = json.load(open(WORKLOADS_JSON)).get("fgmres_iterations_per_solve", {}).get(args.workload, 30)
+    iters_per_solve, src = oracle_iterations(args.workload)
+    if iters_per_solve is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration count for {args.workload}: "
+                          f"run python -m oracle.count_iterations for it"}), flush=True)
+        return 0
     vals = []
     for k in range(args.warmup + args.steps):
         v, info = oracle_sample(w, m0, iters_per_solve, seconds_budget=8.0)
@@ -365,7 +379,8 @@ def main():
                                          "speedup_of_value": value / (1.0 / tp)}
         plain.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, info = oracle_sample(w, m0, max(iters), seconds_budget=15.0)
+        n_or, _ = oracle_iterations(args.workload)
+        v, info = oracle_sample(w, m0, n_or if n_or else max(iters), seconds_budget=15.0)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": info["sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

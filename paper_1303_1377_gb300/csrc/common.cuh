@@ -98,6 +98,16 @@ __host__ __device__ __forceinline__ double tiny_normal<double>() { return 2.2250
 //   group in lexicographic block order.  Inside a block: even sites first, then
 //   odd, each group lexicographic.  Directions d = 2 mu + (backward ? 1 : 0).
 // ---------------------------------------------------------------------------
+// Per-site (AoS) copies of the FP32 links and site terms for the SAP block solver: all
+// components of one site sit together, so each is a vector load at a fixed offset from the
+// site's base address (the [comp][V] layout needs a separate offset k V per component).
+struct LinksAoS {
+    const float4* p;  // [V][4][5]: U_mu(x) as 9 complex (18 floats) + 2 padding floats
+};
+struct CloverAoS {
+    const float4* p;  // [V][18]: the 72 packed reals of the site's two hermitian 6x6 blocks
+};
+
 struct Geom {
     int V;       // fine sites
     int Vb;      // sites per block

@@ -46,6 +46,12 @@ __device__ __forceinline__ void load_link(cplx<T> (&W)[9], const cplx<T>* __rest
     for (int q = 0; q < 9; ++q) W[q] = ldg_c(U + (size_t)(mu * 9 + q) * V + i);
 }
 
+__device__ __forceinline__ void load_link(cplx<float> (&W)[9], const LinksAoS& U, int /*V*/, int mu, int i) {
+    const float4* q = U.p + ((size_t)i * 4 + mu) * 5;
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3), e = __ldg(q + 4);
+    W[0] = mk(a.x, a.y), W[1] = mk(a.z, a.w), W[2] = mk(b.x, b.y), W[3] = mk(b.z, b.w), W[4] = mk(c.x, c.y);
+    W[5] = mk(c.z, c.w), W[6] = mk(d.x, d.y), W[7] = mk(d.z, d.w), W[8] = mk(e.x, e.y);
+}
 // acc += hop of psi_n (the neighbour spinor) through link W in direction MU,
 // FWD: (I - gamma_mu) (x) W with W = U_mu(x);  !FWD: (I + gamma_mu) (x) W^H with W = U_mu(x - mu).
 // acc collects  [g ; -s B^H g],  g = W h (or W^H h), s = +1 forward / -1 backward.
@@ -155,6 +161,33 @@ __device__ __forceinline__ void herm_apply(const T* __restrict__ cl, int V, int 
                 cmac(y.v[h * 6 + a], m, x.v[h * 6 + b]);
                 cmac_conj(y.v[h * 6 + b], m, x.v[h * 6 + a]);
                 ++q;
+            }
+        }
+    }
+}
+
+// the same product with the site term read from its per-site copy (9 float4 per block)
+__device__ __forceinline__ void herm_apply(const CloverAoS& cl, int /*V*/, int i, const Spinor<float>& x, Spinor<float>& y) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4* q = cl.p + (size_t)i * 18 + h * 9;
+        float c[36];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 v = __ldg(q + k);
+            c[4 * k] = v.x, c[4 * k + 1] = v.y, c[4 * k + 2] = v.z, c[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) y.v[h * 6 + a] = c[a] * x.v[h * 6 + a];
+        int m = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < 6; ++b) {
+                const cplx<float> e = mk(c[6 + 2 * m], c[7 + 2 * m]);
+                cmac(y.v[h * 6 + a], e, x.v[h * 6 + b]);
+                cmac_conj(y.v[h * 6 + b], e, x.v[h * 6 + a]);
+                ++m;
             }
         }
     }

@@ -17,9 +17,8 @@ namespace ddamg {
 // restricted to its two 2x2 chiral blocks: [plane][half][s][t] (re, im)
 __constant__ double c_gg[6][2][2][2][2];
 
-template <int MU, typename T, typename Ts>
-__device__ __forceinline__ void hop_pair(const Geom& g, const cplx<T>* __restrict__ U, const cplx<Ts>* __restrict__ in, int i,
-                                         Spinor<T>& acc) {
+template <int MU, typename T, typename Ts, typename UT>
+__device__ __forceinline__ void hop_pair(const Geom& g, const UT& U, const cplx<Ts>* __restrict__ in, int i, Spinor<T>& acc) {
     cplx<T> W[9];
     Spinor<T> pn;
     int f = fine_nbr(g, i, 2 * MU);
@@ -90,9 +89,9 @@ template int launch_dslash<float, float>(const Geom&, const FineOp<float>&, cons
 
 // sum over in-block neighbours of the hops of D applied to a block-local field
 // held in shared memory (sm[k * H + local index]), at local site l (global i).
-template <int MU, typename T>
-__device__ __forceinline__ void block_hop_pair(const Geom& g, const cplx<T>* __restrict__ U, const cplx<T>* sm, int H,
-                                               int base_local, int l, int i, int blk, Spinor<T>& acc) {
+template <int MU, typename T, typename UT>
+__device__ __forceinline__ void block_hop_pair(const Geom& g, const UT& U, const cplx<T>* sm, int H, int base_local, int l, int i,
+                                               int blk, Spinor<T>& acc) {
     cplx<T> W[9];
     Spinor<T> pn;
     int e = __ldg(g.lnbr + (2 * MU) * g.Vb + l);
@@ -114,9 +113,9 @@ __device__ __forceinline__ void block_hop_pair(const Geom& g, const cplx<T>* __r
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void block_hops(const Geom& g, const cplx<T>* __restrict__ U, const cplx<T>* sm, int H, int base_local,
-                                           int l, int i, int blk, Spinor<T>& acc) {
+template <typename T, typename UT>
+__device__ __forceinline__ void block_hops(const Geom& g, const UT& U, const cplx<T>* sm, int H, int base_local, int l, int i, int blk,
+                                           Spinor<T>& acc) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
     block_hop_pair<0>(g, U, sm, H, base_local, l, i, blk, acc);
@@ -126,8 +125,8 @@ __device__ __forceinline__ void block_hops(const Geom& g, const cplx<T>* __restr
 }
 
 // full D at one site with z read from global memory (residual)
-template <typename T>
-__device__ __forceinline__ void site_D(const Geom& g, const FineOp<T>& op, const cplx<T>* __restrict__ z, int i, Spinor<T>& out) {
+template <typename T, typename OpT>
+__device__ __forceinline__ void site_D(const Geom& g, const OpT& op, const cplx<T>* __restrict__ z, int i, Spinor<T>& out) {
     Spinor<T> acc;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
@@ -303,12 +302,14 @@ __global__ void __launch_bounds__(128 * R, 1) sap_colour_kernel(Geom g, FineOp<T
 // ---------------------------------------------------------------------------
 // R right-hand sides ride in adjacent lanes (lane = R * site-pair + slot), so the
 // link and site-term loads of the R lanes of one site are a single transaction.
-template <typename T, int R>
-__global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_kernel(Geom g, FineOp<T> op, const cplx<T>* __restrict__ bsrc,
+// HC: the half-block size as a compile-time constant (0: taken from g at run time), which turns
+// every shared-memory offset k * H into an immediate.
+template <typename T, int R, typename OpT, int HC = 0>
+__global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_kernel(Geom g, OpT op, const cplx<T>* __restrict__ bsrc,
                                                                                      cplx<T>* __restrict__ z, int colour, int nrhs,
                                                                                      int mr_steps) {
     extern __shared__ unsigned char smem_raw[];
-    const int H = g.Vb / 2;
+    const int H = HC ? HC : g.Vb / 2;
     const int slot = threadIdx.x % R;
     const int t = threadIdx.x / R;
     const int slot_stride = 48 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
@@ -447,18 +448,18 @@ static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cp
     return 0;
 }
 
-template <typename T, int R>
-static int launch_sap_lean(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
+template <typename T, int R, typename OpT, int HC = 0>
+static int launch_sap_lean(const Geom& g, const OpT& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                            cudaStream_t st) {
     const int H = g.Vb / 2;
     size_t smem = (size_t)R * (48 * H + 4) * sizeof(cplx<T>) + (size_t)(R * H / 32 + 1) * R * 3 * sizeof(T) + 64;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(sap_colour_lean_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(sap_colour_lean_kernel<T, R, OpT, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr = true;
     }
     long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
-    sap_colour_lean_kernel<T, R><<<(unsigned)nblk, R * H, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    sap_colour_lean_kernel<T, R, OpT, HC><<<(unsigned)nblk, R * H, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
     DD_CHECK_LAUNCH();
     return 0;
 }
@@ -475,6 +476,51 @@ int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx
     if (sizeof(T) == 4 && H <= 128 && nrhs >= 2) return launch_sap_r<T, 2>(g, op, b, z, colour, nrhs, mr_steps, st);
     return launch_sap_r<T, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
 }
+bool sap_aos_supported(const Geom& g, int nrhs) {
+    const int H = g.Vb / 2;
+    return (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) || H % 32 == 0;
+}
+int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
+                          cudaStream_t st) {
+    const int H = g.Vb / 2;
+    if (nrhs >= 4 && H == 128) return launch_sap_lean<float, 4, FineOpAoS, 128>(g, op, b, z, colour, nrhs, mr_steps, st);  // 4^4 blocks
+    if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<float, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
+    if (H % 32 == 0) return launch_sap_lean<float, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
+    return -1;
+}
+
+__global__ void links_to_aos_kernel(const cplx<float>* __restrict__ U, float4* __restrict__ out, int V) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;  // q = site * 4 + mu
+    if (q >= 4 * V) return;
+    const int i = q / 4, mu = q % 4;
+    float f[20];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const cplx<float> u = U[(size_t)(mu * 9 + c) * V + i];
+        f[2 * c] = u.re, f[2 * c + 1] = u.im;
+    }
+    f[18] = f[19] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[(size_t)q * 5 + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+int links_to_aos(const cplx<float>* U, float4* out, int V, cudaStream_t st) {
+    links_to_aos_kernel<<<ceil_div(4LL * V, 256), 256, 0, st>>>(U, out, V);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+__global__ void clover_to_aos_kernel(const float* __restrict__ cl, float4* __restrict__ out, int V) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // q = site * 18 + k
+    if (q >= (size_t)18 * V) return;
+    const int i = (int)(q / 18), k = (int)(q % 18);
+    out[q] = make_float4(cl[(size_t)(4 * k) * V + i], cl[(size_t)(4 * k + 1) * V + i], cl[(size_t)(4 * k + 2) * V + i],
+                         cl[(size_t)(4 * k + 3) * V + i]);
+}
+int clover_to_aos(const float* cl, float4* out, int V, cudaStream_t st) {
+    clover_to_aos_kernel<<<ceil_div(18LL * V, 256), 256, 0, st>>>(cl, out, V);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
 template int launch_sap_colour<double>(const Geom&, const FineOp<double>&, const cplx<double>*, cplx<double>*, int, int, int,
                                        cudaStream_t);
 template int launch_sap_colour<float>(const Geom&, const FineOp<float>&, const cplx<float>*, cplx<float>*, int, int, int,

@@ -14,6 +14,11 @@ struct FineOp {
     const T* clovinv;   // [72][V] A^{-1} (used on even sites)
 };
 
+struct FineOpAoS {  // LinksAoS, CloverAoS: common.cuh
+    LinksAoS U;
+    CloverAoS clov, clovinv;
+};
+
 // coarse stencil in storage type S (float, double or __half2 packed as cplx<half>)
 template <typename S>
 struct CoarseOp {
@@ -31,6 +36,13 @@ int launch_dslash(const Geom& g, const FineOp<T>& op, const cplx<Ts>* in, const 
 template <typename T>
 int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                       cudaStream_t st);
+// FP32 SAP sweep reading links and site terms from their per-site copies
+int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
+                          cudaStream_t st);
+bool sap_aos_supported(const Geom& g, int nrhs);
+// [comp][V] -> per-site copies (links: 4 x 9 complex -> [V][4][5] float4; site term: 72 -> [V][18] float4)
+int links_to_aos(const cplx<float>* U, float4* out, int V, cudaStream_t st);
+int clover_to_aos(const float* cl, float4* out, int V, cudaStream_t st);
 int upload_gamma_products(const double* gg);
 int launch_dslash_dw(const Geom& g, const float4* U, const float2* clov, const cplx<float>* in, void* out, bool out_dw, int nrhs,
                      cudaStream_t st);

@@ -202,6 +202,7 @@ struct ddamg_handle {
     double *clov64 = nullptr, *clovinv64 = nullptr;
     cplx<float>* U32 = nullptr;
     float *clov32 = nullptr, *clovinv32 = nullptr;
+    float4 *Uaos = nullptr, *clov_aos = nullptr, *clovinv_aos = nullptr;  // per-site FP32 copies for the SAP
     float4* Udw = nullptr;    // links as double-word FP32 pairs (FGMRES matvec on FP32 inputs)
     float2* clovdw = nullptr;  // site terms as double-word pairs
     // interpolation
@@ -525,6 +526,13 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
         for (int colour = 0; colour < 2; ++colour) {
             Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * sizeof(T) + 144.0 * sizeof(T) + nrhs * 36.0 * 2 * sizeof(T)),
                     (double)h->V / 4 * nrhs * sap_pair_flops(h));
+            if constexpr (std::is_same<T, float>::value) {
+                if (sap_aos_supported(h->g, nrhs)) {
+                    const FineOpAoS op{LinksAoS{h->Uaos}, CloverAoS{h->clov_aos}, CloverAoS{h->clovinv_aos}};
+                    DD_TRY(launch_sap_colour_aos(h->g, op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
+                    continue;
+                }
+            }
             DD_TRY(launch_sap_colour<T>(h->g, L.op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
         }
     return 0;
@@ -1301,7 +1309,8 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
         return fail(rc);
     if (h->single()) {
         if ((rc = dalloc_n(&h->U32, V * 36)) || (rc = dalloc_n(&h->clov32, V * 72)) || (rc = dalloc_n(&h->clovinv32, V * 72)) ||
-            (rc = dalloc_n(&h->Udw, V * 36)) || (rc = dalloc_n(&h->clovdw, V * 72)))
+            (rc = dalloc_n(&h->Udw, V * 36)) || (rc = dalloc_n(&h->clovdw, V * 72)) || (rc = dalloc_n(&h->Uaos, V * 20)) ||
+            (rc = dalloc_n(&h->clov_aos, V * 18)) || (rc = dalloc_n(&h->clovinv_aos, V * 18)))
             return fail(rc);
     }
     if (h->half()) {
@@ -1329,7 +1338,9 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             (rc = convert<float, double>(h->clov64, h->clov32, V * 72, h->stream)) ||
             (rc = convert<float, double>(h->clovinv64, h->clovinv32, V * 72, h->stream)) ||
             (rc = launch_to_dw(reinterpret_cast<const double*>(h->U64), reinterpret_cast<float2*>(h->Udw), V * 72, h->stream)) ||
-            (rc = launch_to_dw(h->clov64, h->clovdw, V * 72, h->stream)))
+            (rc = launch_to_dw(h->clov64, h->clovdw, V * 72, h->stream)) || (rc = links_to_aos(h->U32, h->Uaos, h->V, h->stream)) ||
+            (rc = clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream)) ||
+            (rc = clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream)))
             return fail(rc);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1910,6 +1921,8 @@ int ddamg_set_mass(ddamg_handle* h, double m0) {
         DD_TRY((convert<float, double>(h->clov64, h->clov32, (size_t)h->V * 72, h->stream)));
         DD_TRY((convert<float, double>(h->clovinv64, h->clovinv32, (size_t)h->V * 72, h->stream)));
         DD_TRY(launch_to_dw(h->clov64, h->clovdw, (size_t)h->V * 72, h->stream));
+        DD_TRY(clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream));
+        DD_TRY(clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream));
     }
     if (h->ready) {
         // mass re-use (Sec. 6.3): P is kept, D_c moves by (m0' - m0) I, only the inverses are redone
@@ -2010,6 +2023,9 @@ int ddamg_destroy(ddamg_handle* h) {
     dfree(h->clov64);
     dfree(h->clovinv64);
     dfree(h->U32);
+    dfree(h->Uaos);
+    dfree(h->clov_aos);
+    dfree(h->clovinv_aos);
     dfree(h->clov32);
     dfree(h->clovinv32);
     dfree(h->V64);

@@ -312,11 +312,10 @@ __global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_ker
     const int H = HC ? HC : g.Vb / 2;
     const int slot = threadIdx.x % R;
     const int t = threadIdx.x / R;
-    const int slot_stride = 48 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
+    const int slot_stride = 36 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
     cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)slot * slot_stride;  // [12][H] even work vector
     cplx<T>* SO = SE + 12 * H;                                                         // [12][H] rho
     cplx<T>* SX = SO + 12 * H;                                                         // [12][H] x_o (first: r_o)
-    cplx<T>* SR = SX + 12 * H;                                                         // [12][H] r_e
     T* red = reinterpret_cast<T*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)R * slot_stride);  // [nwarps][R][3]
     const int ngroups = (nrhs + R - 1) / R;
     const int r = (blockIdx.x % ngroups) * R + slot;
@@ -332,10 +331,7 @@ __global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_ker
         if (act) {
             site_D(g, op, zr, ie, tmp);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                tmp.v[k] = b[(size_t)k * g.V + ie] - tmp.v[k];
-                SR[k * H + t] = tmp.v[k];
-            }
+            for (int k = 0; k < 12; ++k) tmp.v[k] = b[(size_t)k * g.V + ie] - tmp.v[k];
             herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
 #pragma unroll
             for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
@@ -344,8 +340,11 @@ __global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_ker
             for (int k = 0; k < 12; ++k) SX[k * H + t] = b[(size_t)k * g.V + io] - tmp.v[k];
         }
     }
-    __syncthreads();
-    if (act) {  // rho = r_o - D_oe A_ee^{-1} r_e ; x_o = 0
+    __syncthreads();  // every read of z in this block is done: z may be updated from here on
+    if (act) {  // z_e += A_ee^{-1} r_e (the even part of the correction that does not depend on x_o);
+                // rho = r_o - D_oe A_ee^{-1} r_e ; x_o = 0
+#pragma unroll
+        for (int k = 0; k < 12; ++k) zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + SE[k * H + t];
         Spinor<T> hs;
         block_hops(g, op.U, SE, H, 0, lo, io, blk, hs);
 #pragma unroll
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_ker
         Spinor<T> hs, tmp2;
         block_hops(g, op.U, SX, H, H, le, ie, blk, hs);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) hs.v[k] = SR[k * H + t] + T(0.5) * hs.v[k];
+        for (int k = 0; k < 12; ++k) hs.v[k] = T(0.5) * hs.v[k];  // x_e = A_ee^{-1} r_e (added above) + A_ee^{-1} (1/2 hops x_o)
         herm_apply(op.clovinv, g.V, ie, hs, tmp2);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -452,7 +451,7 @@ template <typename T, int R, typename OpT, int HC = 0>
 static int launch_sap_lean(const Geom& g, const OpT& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                            cudaStream_t st) {
     const int H = g.Vb / 2;
-    size_t smem = (size_t)R * (48 * H + 4) * sizeof(cplx<T>) + (size_t)(R * H / 32 + 1) * R * 3 * sizeof(T) + 64;
+    size_t smem = (size_t)R * (36 * H + 4) * sizeof(cplx<T>) + (size_t)(R * H / 32 + 1) * R * 3 * sizeof(T) + 64;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(sap_colour_lean_kernel<T, R, OpT, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -515,7 +515,7 @@ int axpy_norm_dw(cplx<dwf>* w, const cplx<dwf>* A, size_t istride, size_t rstrid
 // arithmetic stays a small fraction of the work.  Requires even n and
 // 16-byte aligned vectors (every fine vector is 12 V complex numbers).
 // ---------------------------------------------------------------------------
-constexpr int kFlush = 8;
+constexpr int kFlush = 32;
 
 template <int KB>
 __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4* __restrict__ A, size_t istride4, size_t arstride4, int k,
@@ -714,24 +714,6 @@ int split_f64(const cplx<double>* x, cplx<float>* hi, cplx<float>* lo, size_t n,
     return 0;
 }
 
-// w += t (FP64 += FP32)
-__global__ void add_f32_kernel(double2* __restrict__ w, const float2* __restrict__ t, size_t n) {
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        double2 a = w[q];
-        const float2 b = t[q];
-        a.x += (double)b.x;
-        a.y += (double)b.y;
-        w[q] = a;
-    }
-}
-int add_f32(cplx<double>* w, const cplx<float>* t, size_t n, cudaStream_t st) {
-    int blocks = ceil_div((long long)n, 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    add_f32_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<double2*>(w), reinterpret_cast<const float2*>(t), n);
-    DD_CHECK_LAUNCH();
-    return 0;
-}
-
 // Reorthogonalisation test of classical Gram-Schmidt (the DGKS criterion with
 // threshold eta): request a second pass when, for any active right-hand side,
 // ||w after||^2 < eta^2 ||w before||^2.
@@ -761,35 +743,53 @@ int add_columns_flag(cplx<double>* a, const cplx<double>* b, int n, const int* f
 }
 
 // x[r] += sum_i y[i][r] Z_i[r] for an FP64 iterate and FP32 preconditioned vectors: the sum is
-// formed in double-word arithmetic (exact FP32 products, ~2^-48 accumulation) and added once in FP64
+// formed in double-word arithmetic (exact FP32 products, ~2^-48 accumulation) and added once in FP64.
+// Grid: blockIdx.y = right-hand side.
 __global__ void xupdate_kernel(cplx<double>* __restrict__ x, const cplx<float>* __restrict__ Z, size_t istride, size_t n, int k,
                                const float4* __restrict__ cdwv, int nrhs) {
-    const size_t tot = n * nrhs;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
-        int r = (int)(q / n);
-        size_t e = q % n;
+    const int r = blockIdx.y;
+    cplx<double>* xr = x + (size_t)r * n;
+    const cplx<float>* Zr = Z + (size_t)r * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         cdw acc = cdw_zero();
+#pragma unroll 4
         for (int i = 0; i < k; ++i) {
-            float4 c = __ldg(cdwv + (size_t)i * nrhs + r);
-            cplx<float> zv = Z[i * istride + (size_t)r * n + e];
-            dw cr = {c.x, c.y}, ci = {c.z, c.w};
+            const float4 c = __ldg(cdwv + (size_t)i * nrhs + r);
+            const cplx<float> zv = Zr[i * istride + e];
+            const dw cr = {c.x, c.y}, ci = {c.z, c.w};
             dw_macf(acc.re, cr, zv.re);
             dw_macf(acc.re, dw_neg(ci), zv.im);
             dw_macf(acc.im, cr, zv.im);
             dw_macf(acc.im, ci, zv.re);
         }
-        cplx<double>& xv = x[(size_t)r * n + e];
-        xv = mk(xv.re + dw_to_double(acc.re), xv.im + dw_to_double(acc.im));
+        const cplx<double> xv = xr[e];
+        xr[e] = mk(xv.re + dw_to_double(acc.re), xv.im + dw_to_double(acc.im));
     }
 }
 int xupdate_dw(cplx<double>* x, const cplx<float>* Z, size_t istride, size_t n, int k, const cplx<double>* coef, int nrhs,
                float4* coef_scratch, cudaStream_t st) {
     coef_to_dw_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, nrhs, k, nrhs, 1.0, coef_scratch, nullptr);
     DD_CHECK_LAUNCH();
-    long long tot = (long long)n * nrhs;
-    int blocks = ceil_div(tot, 256);
+    int bx = (int)std::min<size_t>((n + 255) / 256, (size_t)std::max(1, 152 * 16 / nrhs));
+    xupdate_kernel<<<dim3(bx, nrhs), 256, 0, st>>>(x, Z, istride, n, k, coef_scratch, nrhs);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
+// V0 = fl32(b - (w + t)) for an FP64 w and an FP32 t (the true residual of the refinement cycles)
+__global__ void residual_f32_kernel(const double2* __restrict__ b, const double2* __restrict__ w, const float2* __restrict__ t,
+                                    float2* __restrict__ out, size_t n) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const double2 bv = b[q], wv = w[q];
+        const float2 tv = t[q];
+        out[q] = make_float2((float)(bv.x - (wv.x + (double)tv.x)), (float)(bv.y - (wv.y + (double)tv.y)));
+    }
+}
+int residual_f32(const cplx<double>* b, const cplx<double>* w, const cplx<float>* t, cplx<float>* out, size_t n, cudaStream_t st) {
+    int blocks = ceil_div((long long)n, 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    xupdate_kernel<<<blocks, 256, 0, st>>>(x, Z, istride, n, k, coef_scratch, nrhs);
+    residual_f32_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(w),
+                                                reinterpret_cast<const float2*>(t), reinterpret_cast<float2*>(out), n);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -52,8 +52,8 @@ int axpy_norm_f32(cplx<float>* w, const cplx<float>* A, size_t istride, size_t r
                   size_t n, int nrhs, double alpha, float2* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
                   cudaStream_t st);
 int scale_f32(cplx<float>* w, const cplx<double>* scale, size_t n, int nrhs, cudaStream_t st);
+int residual_f32(const cplx<double>* b, const cplx<double>* w, const cplx<float>* t, cplx<float>* out, size_t n, cudaStream_t st);
 int split_f64(const cplx<double>* x, cplx<float>* hi, cplx<float>* lo, size_t n, cudaStream_t st);
-int add_f32(cplx<double>* w, const cplx<float>* t, size_t n, cudaStream_t st);
 int convert_d2dw(const double* in, cplx<dwf>* out, size_t nreal, cudaStream_t st);
 int convert_dw2f(const cplx<dwf>* in, float* out, size_t nreal, cudaStream_t st);
 template <typename To, typename Ti>

@@ -596,6 +596,7 @@ struct KrylovProblem {
     int m;
     std::function<int(const cplx<TZ>*, cplx<TV>*)> A;
     std::function<int(const cplx<TB>*, cplx<TB>*)> Ax;
+    std::function<int(const cplx<TB>*, cplx<TV>*)> residual;  // optional: V0 = b - A x straight into the basis type
     std::function<int(const cplx<TV>*, cplx<TZ>*)> M;
     const cplx<TB>* b;
     cplx<TB>* x;
@@ -728,6 +729,7 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
     cplx<TV>* V0 = P.Vb;
     // V0 = b - A x (in the iterate's precision), or b for a zero guess
     auto residual_to_V0 = [&]() -> int {
+        if (P.residual) return P.residual(P.x, V0);
         DD_TRY(P.Ax(P.x, P.wB));
         DD_TRY((lincomb<TB, TB>(P.wB, n, -1.0, P.b, 0, n, 1, kb.ones, nr, n, nr, nullptr, st)));
         return bfrom<TV, TB>(V0, P.wB, n * nr, st);
@@ -1185,21 +1187,22 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
             return dslash<double, TZ>(h, z, nullptr, reinterpret_cast<cplx<double>*>(w), nrhs);
         }
     };
-    P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int {
-        if constexpr (std::is_same<TV, float>::value) {
-            // D z for the FP64 iterate without FP64 arithmetic: z = z_h + z_l (FP32 pair, ~2^-48),
-            // D z_h in double-word arithmetic (exact products, FP64-accurate sums), D z_l in FP32
-            // (its rounding is ~2^-24 of a term already ~2^-24 smaller), summed in FP64
-            cplx<float>* zh = h->ws_outer[2].as<cplx<float>>();
-            cplx<float>* zl = h->ws_outer[3].as<cplx<float>>();
-            DD_TRY(split_f64(z, zh, zl, fld * nrhs, st));
-            DD_TRY(dslash_dw(h, zh, w, nrhs));
-            DD_TRY((dslash<float, float>(h, zl, nullptr, zh, nrhs)));
-            return add_f32(w, zh, fld * nrhs, st);
-        } else {
-            return dslash<double, double>(h, z, nullptr, w, nrhs);
-        }
-    };
+    P.Ax = [&](const cplx<double>* z, cplx<double>* w) -> int { return dslash<double, double>(h, z, nullptr, w, nrhs); };
+    if constexpr (std::is_same<TV, float>::value) {
+        // The true residual b - D x of the refinement cycles without FP64 arithmetic in D:
+        // x = x_h + x_l (FP32 pair, ~2^-48), D x_h in double-word arithmetic (exact products,
+        // FP64-accurate sums), D x_l in FP32 (its rounding is ~2^-24 of a term already ~2^-24
+        // smaller); b - (D x_h + D x_l) is formed in FP64 and rounded once into the FP32 basis.
+        P.residual = [&](const cplx<double>* xx, cplx<TV>* v0) -> int {
+            cplx<float>* xh = h->ws_outer[2].as<cplx<float>>();
+            cplx<float>* xl = h->ws_outer[3].as<cplx<float>>();
+            cplx<double>* w = h->ws_outer[4].as<cplx<double>>();
+            DD_TRY(split_f64(xx, xh, xl, fld * nrhs, st));
+            DD_TRY(dslash_dw(h, xh, w, nrhs));
+            DD_TRY((dslash<float, float>(h, xl, nullptr, xh, nrhs)));
+            return residual_f32(b, w, xh, reinterpret_cast<cplx<float>*>(v0), fld * nrhs, st);
+        };
+    }
     P.M = [&](const cplx<TV>* v, cplx<TZ>* z) -> int {
         const cplx<TZ>* r;
         if (std::is_same<TV, dwf>::value) {

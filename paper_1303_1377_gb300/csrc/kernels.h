@@ -2,6 +2,8 @@
 // negative ddamg_status).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "../../include/ddamg.h"
 
@@ -54,6 +56,9 @@ template <typename T, typename Tp>
 int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
 template <typename T, typename Tp>
 int launch_prolong(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
+// half-precision V-cycle: prolongation as FP16 tensor-core products (needs Vb % 16 == 0, N <= 32)
+bool prolong_tc_supported(const Geom& g, int N);
+int launch_prolong_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, cudaStream_t st);
 int launch_gram_schmidt(const Geom& g, cplx<double>* P, int N, int* rank_fail, cudaStream_t st);
 int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, cplx<double>* T,
                       cudaStream_t st);

@@ -553,9 +553,13 @@ static int prolong_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs) 
     Level<T> L = level<T>(h);
     const double pb = h->half() ? 2.0 : sizeof(T);
     Prof pr(h, PF_PROLONG, (double)h->V * (12.0 * h->N * 2 * pb + 12.0 * nrhs * 2 * sizeof(T)));
-    if (std::is_same<T, float>::value && h->half())
+    if (std::is_same<T, float>::value && h->half()) {
+        if (prolong_tc_supported(h->g, h->N))
+            return launch_prolong_tc(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in), reinterpret_cast<cplx<float>*>(out),
+                                     nrhs, h->stream);
         return launch_prolong<float, __half>(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in),
                                              reinterpret_cast<cplx<float>*>(out), nrhs, h->stream);
+    }
     return launch_prolong<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
 }
 

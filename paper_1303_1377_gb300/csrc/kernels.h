@@ -56,6 +56,11 @@ template <typename T, typename Tp>
 int launch_restrict(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
 template <typename T, typename Tp>
 int launch_prolong(const Geom& g, const cplx<Tp>* P, int N, const cplx<T>* in, cplx<T>* out, int nrhs, cudaStream_t st);
+// half-precision V-cycle: restriction as FP16 tensor-core products (needs Vb % 16 == 0, N % 4 == 0, N <= 32)
+bool restrict_tc_supported(const Geom& g, int N);
+// rmax: nrhs ints of device scratch (the field maxima)
+int launch_restrict_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, int* rmax,
+                       cudaStream_t st);
 // half-precision V-cycle: prolongation as FP16 tensor-core products (needs Vb % 16 == 0, N <= 32)
 bool prolong_tc_supported(const Geom& g, int N);
 int launch_prolong_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, cudaStream_t st);

@@ -218,6 +218,7 @@ struct ddamg_handle {
     int* d_flag = nullptr;
     // workspaces
     Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[5];
+    Scratch ws_rmax;  // per right-hand-side field maxima of the tensor-core restriction
     KrylovBufs kc, ko;
     // continuous batching: right-hand sides and iterates of the slots (internal order, FP64)
     int n_slots = 0;
@@ -543,9 +544,15 @@ static int restrict_(ddamg_handle* h, const cplx<T>* in, cplx<T>* out, int nrhs)
     Level<T> L = level<T>(h);
     const double pb = h->half() ? 2.0 : sizeof(T);
     Prof pr(h, PF_RESTRICT, (double)h->V * (12.0 * h->N * 2 * pb + 12.0 * nrhs * 2 * sizeof(T)));
-    if (std::is_same<T, float>::value && h->half())
+    if (std::is_same<T, float>::value && h->half()) {
+        if (restrict_tc_supported(h->g, h->N)) {
+            DD_TRY(h->ws_rmax.ensure(sizeof(int) * nrhs));
+            return launch_restrict_tc(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in), reinterpret_cast<cplx<float>*>(out),
+                                      nrhs, h->ws_rmax.as<int>(), h->stream);
+        }
         return launch_restrict<float, __half>(h->g, h->P16, h->N, reinterpret_cast<const cplx<float>*>(in),
                                               reinterpret_cast<cplx<float>*>(out), nrhs, h->stream);
+    }
     return launch_restrict<T, T>(h->g, L.P, h->N, in, out, nrhs, h->stream);
 }
 template <typename T>
@@ -2052,6 +2059,7 @@ int ddamg_destroy(ddamg_handle* h) {
     for (auto& s : h->ws_coarse) s.release();
     for (auto& s : h->ws_io) s.release();
     for (auto& s : h->ws_outer) s.release();
+    h->ws_rmax.release();
     dfree(h->slot_b);
     dfree(h->slot_x);
     h->kc.release();

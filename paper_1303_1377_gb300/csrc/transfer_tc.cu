@@ -122,6 +122,168 @@ __global__ void __launch_bounds__(kProTCWarps * 32) prolong_tc_kernel(Geom g, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Restriction e[r][c][h N + j] = sum_{x in c, k in half h} conj(P_j[k][x]) in[r][k][x]
+// as FP16 tensor-core products with FP32 accumulation: per aggregate half,
+//   C = A B,  A rows (r, re/im): row g = Re x_r, row g + 8 = Im x_r (8 right-hand
+//   sides per m-tile), K = (component, site) in steps of 16 sites of one component,
+//   B columns (j, re/im) of P.  A lane then holds, for one (r, j),
+//     c0 = ReX.ReP, c1 = ReX.ImP, c2 = ImX.ReP, c3 = ImX.ImP  and
+//     e = (c0 + c3) + i (c2 - c1).
+// The warps of a CTA split the K range; their partial sums meet in shared memory.
+// Each right-hand side is scaled by a power of two that maps its largest entry on
+// the whole field below 2^14 before it is rounded to FP16: an FP16 normal number
+// keeps 11 significant bits over 29 binades, so only entries 2^28 below that
+// maximum lose precision (a separate pass finds the maxima).
+// ---------------------------------------------------------------------------
+constexpr int kResTCWarps = 8;
+
+template <int NTN>  // n-tiles over (j, re/im): N = 4 NTN test vectors
+__global__ void __launch_bounds__(kResTCWarps * 32) restrict_tc_kernel(Geom g, const __half2* __restrict__ P, int N,
+                                                                        const cplx<float>* __restrict__ in, cplx<float>* __restrict__ out,
+                                                                        int nrhs, int r0, const int* __restrict__ rmax) {
+    constexpr int MT = 2;  // 16 right-hand sides per launch group
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* red = reinterpret_cast<float*>(smem_raw);  // [warps][32 lanes][MT * NTN * 4]
+    __shared__ float scale[8 * MT], inv_scale[8 * MT];
+    const int c = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
+    const size_t blk0 = (size_t)c * g.Vb;
+    // 1. per right-hand side: power-of-two scale of its largest entry on the whole field
+    if (threadIdx.x < 8 * MT) {
+        const int r = r0 + threadIdx.x;
+        int ex = 0;
+        const float mm = r < nrhs ? __int_as_float(rmax[r]) : 0.f;
+        if (mm > 0.f) frexpf(mm, &ex);
+        scale[threadIdx.x] = ldexpf(1.f, 14 - ex);  // largest entry maps below 2^14
+        inv_scale[threadIdx.x] = ldexpf(1.f, ex - 14);
+    }
+    __syncthreads();
+    const int sg = g.Vb / 16;
+    for (int h = 0; h < 2; ++h) {
+        float acc[MT][NTN][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int n = 0; n < NTN; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[mt][n][q] = 0.f;
+        float sc[MT];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) sc[mt] = scale[8 * mt + gq];
+        // 2. this warp's share of the k-tiles (component kc, 16 sites from s0)
+#pragma unroll 2
+        for (int kt = w; kt < 6 * sg; kt += kResTCWarps) {
+            const int k = 6 * h + kt / sg, s0 = (kt % sg) * 16;
+            const size_t site = blk0 + s0 + 2 * t;
+            unsigned a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int r = r0 + 8 * mt + gq;
+                float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+                if (r < nrhs) {
+                    const float4* xr = reinterpret_cast<const float4*>(in + ((size_t)r * 12 + k) * g.V + site);
+                    lo = __ldg(xr);      // sites 2t, 2t+1
+                    hi = __ldg(xr + 4);  // sites 2t+8, 2t+9
+                }
+                const float f = sc[mt];
+                a[mt][0] = as_u32(__floats2half2_rn(lo.x * f, lo.z * f));  // row g (Re), K 2t, 2t+1
+                a[mt][1] = as_u32(__floats2half2_rn(lo.y * f, lo.w * f));  // row g+8 (Im)
+                a[mt][2] = as_u32(__floats2half2_rn(hi.x * f, hi.z * f));  // row g, K 2t+8, 2t+9
+                a[mt][3] = as_u32(__floats2half2_rn(hi.y * f, hi.w * f));
+            }
+            const int plane = gq & 1;
+#pragma unroll
+            for (int n = 0; n < NTN; ++n) {
+                const int j = 4 * n + (gq >> 1);
+                const uint2* pj = reinterpret_cast<const uint2*>(P + ((size_t)j * 12 + k) * g.V + site);
+                const uint2 v0 = __ldg(pj), v1 = __ldg(pj + 4);  // sites 2t, 2t+1 and 2t+8, 2t+9
+                const __half2 p00 = *reinterpret_cast<const __half2*>(&v0.x), p01 = *reinterpret_cast<const __half2*>(&v0.y);
+                const __half2 p10 = *reinterpret_cast<const __half2*>(&v1.x), p11 = *reinterpret_cast<const __half2*>(&v1.y);
+                const unsigned b0 = as_u32(plane ? __highs2half2(p00, p01) : __lows2half2(p00, p01));
+                const unsigned b1 = as_u32(plane ? __highs2half2(p10, p11) : __lows2half2(p10, p11));
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) mma16816_tr(acc[mt][n], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+            }
+        }
+        // 3. sum the warps' partial tiles and form e
+        float* my = red + ((size_t)w * 32 + lane) * (MT * NTN * 4);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int n = 0; n < NTN; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) my[(mt * NTN + n) * 4 + q] = acc[mt][n][q];
+        __syncthreads();
+        for (int q = threadIdx.x; q < 32 * MT * NTN; q += blockDim.x) {
+            const int ln = q % 32, tile = q / 32;  // tile = mt * NTN + n
+            float cc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int ww = 0; ww < kResTCWarps; ++ww) {
+                const float* src = red + ((size_t)ww * 32 + ln) * (MT * NTN * 4) + tile * 4;
+                cc[0] += src[0], cc[1] += src[1], cc[2] += src[2], cc[3] += src[3];
+            }
+            const int mt = tile / NTN, n = tile % NTN, rr = 8 * mt + (ln >> 2), j = 4 * n + (ln & 3), r = r0 + rr;
+            if (r < nrhs && j < N) {
+                const float is = inv_scale[rr];
+                out[((size_t)r * g.NB + c) * (2 * N) + h * N + j] = mk((cc[0] + cc[3]) * is, (cc[2] - cc[1]) * is);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// rmax[r] = bits of max |Re|, |Im| over the field of right-hand side r (non-negative floats
+// order like their bit patterns, so an integer atomicMax finds the largest)
+__global__ void field_absmax_kernel(const float4* __restrict__ in, size_t n4, int* __restrict__ rmax) {
+    const int r = blockIdx.y;
+    const float4* x = in + (size_t)r * n4;
+    float m = 0.f;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(x + q);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rmax + r, __float_as_int(m));
+}
+
+bool restrict_tc_supported(const Geom& g, int N) { return g.Vb % 16 == 0 && N % 4 == 0 && N <= 32; }
+
+int launch_restrict_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, int* rmax,
+                       cudaStream_t st) {
+    const __half2* P2 = reinterpret_cast<const __half2*>(P);
+    const int NTN = N / 4;
+    const size_t sm = (size_t)kResTCWarps * 32 * 2 * NTN * 4 * sizeof(float);
+    const size_t n4 = (size_t)12 * g.V / 2;  // float4 = two complex numbers; 12 V is even
+    DD_CUDA(cudaMemsetAsync(rmax, 0, sizeof(int) * nrhs, st));
+    const int bx = (int)std::min<size_t>((n4 + 255) / 256, (size_t)std::max(1, 152 * 8 / nrhs));
+    field_absmax_kernel<<<dim3(bx, nrhs), 256, 0, st>>>(reinterpret_cast<const float4*>(in), n4, rmax);
+    DD_CHECK_LAUNCH();
+    for (int r0 = 0; r0 < nrhs; r0 += 16) {
+        switch (NTN) {
+#define DD_RES_TC(n)                                                                                                   \
+    case n:                                                                                                            \
+        if (sm + 1024 > 48 * 1024) /* dynamic + static beyond the default 48 KB needs the opt-in */                           \
+            cudaFuncSetAttribute(restrict_tc_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);               \
+        restrict_tc_kernel<n><<<g.NB, kResTCWarps * 32, sm, st>>>(g, P2, N, in, out, nrhs, r0, rmax);                \
+        break;
+            DD_RES_TC(1)
+            DD_RES_TC(2)
+            DD_RES_TC(3)
+            DD_RES_TC(4)
+            DD_RES_TC(5)
+            DD_RES_TC(6)
+            DD_RES_TC(7)
+            DD_RES_TC(8)
+#undef DD_RES_TC
+            default:
+                return DDAMG_ERR_INVALID_ARG;
+        }
+        DD_CHECK_LAUNCH();
+    }
+    return 0;
+}
+
 bool prolong_tc_supported(const Geom& g, int N) { return g.Vb % 16 == 0 && N <= kProKPad; }
 
 int launch_prolong_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, cudaStream_t st) {

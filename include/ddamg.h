@@ -156,9 +156,12 @@ int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N);
 int ddamg_get_vectors(const ddamg_handle* h, double* V);
 
 /* Solve D z = b to ||b - D z|| <= tol ||b|| by FGMRES(n_kv) right-preconditioned
- * with one V-cycle (Sec. 5).  b, z: one spinor field each; z is the initial
- * guess on entry (pass zeros for the paper's zero guess) and the solution on
- * exit.  tol <= 0 uses params->tol.  st may be NULL.
+ * with one V-cycle (Sec. 5); in SINGLE and HALF mode the FGMRES runs as the
+ * params->outer scheme (ddamg_outer).  b, z: one spinor field each; z is the
+ * initial guess on entry (pass zeros for the paper's zero guess; an all-zero z
+ * skips the initial residual product) and the solution on exit.  The
+ * convergence test is always on the true residual.  tol <= 0 uses params->tol.
+ * st may be NULL.
  * Errors: INVALID_ARG, NOT_READY, OOM, CUDA, NOT_CONVERGED (z = last iterate),
  * NONFINITE, TIMEOUT. */
 int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_stats* st);
@@ -207,11 +210,17 @@ int ddamg_apply_D_mixed(ddamg_handle* h, const float* in, double* out, int n_rhs
 int ddamg_apply_sap(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);
 
 /* Coarse restriction out = P^H in (fine -> coarse) and prolongation out = P in
- * (coarse -> fine), Sec. 3.1; FP64 fields, V-cycle precision arithmetic. */
+ * (coarse -> fine), Sec. 3.1; FP64 fields, V-cycle precision arithmetic.  In
+ * DDAMG_PREC_HALF both are FP16 tensor-core products with FP32 accumulation: P is
+ * stored in FP16, and the FP32 operand is rounded to FP16 after a power-of-two
+ * scaling (per aggregate for the coarse input of the prolongation; by the field
+ * maximum of each right-hand side for the restriction), about 2^-12 relative
+ * error per entry.  n_rhs < 1 or a null pointer: DDAMG_ERR_INVALID_ARG. */
 int ddamg_restrict(ddamg_handle* h, const double* fine_in, double* coarse_out, int n_rhs);
 int ddamg_prolong(ddamg_handle* h, const double* coarse_in, double* fine_out, int n_rhs);
 
-/* out = D_c in for coarse vectors (Sec. 3.2), V-cycle precision arithmetic. */
+/* out = D_c in for coarse vectors (Sec. 3.2), V-cycle precision arithmetic (in
+ * DDAMG_PREC_HALF: D_c stored in FP16, FP16 tensor-core products, FP32 accumulation). */
 int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs);
 
 /* out = D_c in, like ddamg_apply_Dc, for callers that must not have this library

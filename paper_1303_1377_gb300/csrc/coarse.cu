@@ -151,11 +151,12 @@ static int launch_stencil_nrp(const CoarseOp<S>& op, int site_begin, int nsites,
     size_t stage = (size_t)9 * op.nc * NRP * sizeof(cplx<T>);
     size_t reduce = (size_t)(KG + 1) * op.nc * NRP * sizeof(cplx<T>);
     size_t smem = stage > reduce ? stage : reduce;
-    static bool attr = false;
-    if (!attr) {
+    // set once per kernel instance (a function-local static initialiser is thread safe)
+    static const bool attr = [] {
         cudaFuncSetAttribute(coarse_stencil_kernel<T, S, NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     coarse_stencil_kernel<T, S, NRP><<<nsites, nt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;

@@ -247,11 +247,12 @@ static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<f
     const int Kp = op.Kt_all * 16;
     size_t smem = (size_t)2 * NRP * (Kp + 8) * sizeof(__half) + (size_t)2 * op.nc * 2 * NRP * sizeof(float) +
                   (size_t)op.nc * NRP * sizeof(cplx<float>);
-    static bool attr = false;
-    if (!attr) {
+    // set once per kernel instance (a function-local static initialiser is thread safe)
+    static const bool attr = [] {
         cudaFuncSetAttribute(coarse_tc_kernel<NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     coarse_tc_kernel<NRP><<<nsites, 32 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -132,7 +134,7 @@ __device__ __forceinline__ int fine_nbr(const Geom& g, int i, int d) {
 // ---------------------------------------------------------------------------
 // launch bookkeeping
 // ---------------------------------------------------------------------------
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;  // several host threads may drive handles at once
 void set_error(const std::string& msg);
 
 #define DD_LAUNCHED() (::ddamg::g_launches++)

@@ -436,11 +436,12 @@ static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cp
     const int H = g.Vb / 2;
     const int nt = ((H + 31) / 32) * 32;
     size_t smem = (size_t)R * 36 * H * sizeof(cplx<T>) + (size_t)R * 3 * 32 * sizeof(T);
-    static bool attr_set = false;
-    if (!attr_set) {
+    // set once per kernel instance (a function-local static initialiser is thread safe)
+    static const bool attr_set = [] {
         cudaFuncSetAttribute(sap_colour_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
     sap_colour_kernel<T, R><<<(unsigned)nblk, R * nt, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
     DD_CHECK_LAUNCH();
@@ -452,11 +453,12 @@ static int launch_sap_lean(const Geom& g, const OpT& op, const cplx<T>* b, cplx<
                            cudaStream_t st) {
     const int H = g.Vb / 2;
     size_t smem = (size_t)R * (36 * H + 4) * sizeof(cplx<T>) + (size_t)(R * H / 32 + 1) * R * 3 * sizeof(T) + 64;
-    static bool attr = false;
-    if (!attr) {
+    // set once per kernel instance (a function-local static initialiser is thread safe)
+    static const bool attr = [] {
         cudaFuncSetAttribute(sap_colour_lean_kernel<T, R, OpT, HC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
     sap_colour_lean_kernel<T, R, OpT, HC><<<(unsigned)nblk, R * H, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
     DD_CHECK_LAUNCH();

@@ -19,7 +19,7 @@
 
 namespace ddamg {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 static int g_fail_allocs = 0;
@@ -615,7 +615,7 @@ struct KrylovProblem {
     double tol;            // relative to ||b_r||
     long long maxiter;     // Arnoldi steps per rhs
     bool fixed;            // run exactly maxiter steps (no tolerance)
-    bool reorth;           // classical Gram-Schmidt twice
+    bool reorth;           // second Gram-Schmidt pass: always (generic path), on the DGKS test (lean path)
     bool lean = false;     // FP32 basis: one Gram-Schmidt pass, a second one only on heavy cancellation
     double cycle_tol = 0;  // > 0: a cycle ends once every rhs has reduced its residual by this factor
     int max_cycles = 0;    // > 0: return after this many cycles (x updated, no closing residual)
@@ -1447,7 +1447,7 @@ const char* ddamg_error_string(int s) {
 
 const char* ddamg_last_error(void) { return g_err.c_str(); }
 
-long long ddamg_launch_count(void) { return (long long)g_launches; }
+long long ddamg_launch_count(void) { return (long long)g_launches.load(); }
 
 void ddamg_debug_fail_allocs(int n) { g_fail_allocs = n; }
 

@@ -32,12 +32,15 @@ __device__ __forceinline__ void hop_pair(const Geom& g, const UT& U, const cplx<
 }
 
 // out = D in  (RESID: out = b - D in).  in may be of a different precision Ts.
+// Thread (x, y) of a CTA: site tile * 32 + x, right-hand side blockIdx.y * blockDim.y + y, so the
+// warps of one CTA cover the same 32 sites for several right-hand sides and share the links and
+// site terms through L1; each warp's spinor loads stay 32 consecutive sites of one field.
 template <typename T, typename Ts, bool RESID>
-__global__ void __launch_bounds__(128) dslash_kernel(Geom g, FineOp<T> op, const cplx<Ts>* __restrict__ in,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 384 : 128, sizeof(T) == 4 ? 2 : 1) dslash_kernel(Geom g, FineOp<T> op, const cplx<Ts>* __restrict__ in,
                                                      const cplx<T>* __restrict__ b, cplx<T>* __restrict__ out, int nrhs) {
-    int r = blockIdx.x % nrhs;
-    int i = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-    if (i >= g.V) return;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    if (i >= g.V || r >= nrhs) return;
     const size_t off = (size_t)r * 12 * g.V;
     const cplx<Ts>* inr = in + off;
     Spinor<T> acc;
@@ -62,12 +65,12 @@ __global__ void __launch_bounds__(128) dslash_kernel(Geom g, FineOp<T> op, const
 template <typename T, typename Ts>
 int launch_dslash(const Geom& g, const FineOp<T>& op, const cplx<Ts>* in, const cplx<T>* b, cplx<T>* out, int nrhs,
                   cudaStream_t st) {
-    const int nt = 128;
-    long long nblk = (long long)ceil_div(g.V, nt) * nrhs;
+    const int ry = std::min(nrhs, sizeof(T) == 4 ? 12 : 4);  // right-hand sides per CTA
+    const dim3 grid((unsigned)ceil_div(g.V, 32), (unsigned)ceil_div(nrhs, ry)), block(32, ry);
     if (b)
-        dslash_kernel<T, Ts, true><<<(unsigned)nblk, nt, 0, st>>>(g, op, in, b, out, nrhs);
+        dslash_kernel<T, Ts, true><<<grid, block, 0, st>>>(g, op, in, b, out, nrhs);
     else
-        dslash_kernel<T, Ts, false><<<(unsigned)nblk, nt, 0, st>>>(g, op, in, b, out, nrhs);
+        dslash_kernel<T, Ts, false><<<grid, block, 0, st>>>(g, op, in, b, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -746,12 +746,14 @@ __device__ __noinline__ void dw_hop_rt(cdw (&acc)[12], const cplx<float>* __rest
 
 }  // namespace
 
+// thread (x, y): site blockIdx.x * 32 + x, right-hand side blockIdx.y * blockDim.y + y (the warps of
+// a CTA share the double-word links and site terms of 32 sites through L1)
 template <bool OUT_DW>
 __global__ void __launch_bounds__(128) dslash_dw_kernel(Geom g, const float4* __restrict__ U, const float2* __restrict__ clov,
                                                         const cplx<float>* __restrict__ in, void* __restrict__ outp, int nrhs) {
-    int r = blockIdx.x % nrhs;
-    int i = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-    if (i >= g.V) return;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    if (i >= g.V || r >= nrhs) return;
     const size_t off = (size_t)r * 12 * g.V;
     const cplx<float>* inr = in + off;
     cdw acc[12];
@@ -825,10 +827,10 @@ __global__ void __launch_bounds__(128) dslash_dw_kernel(Geom g, const float4* __
 
 int launch_dslash_dw(const Geom& g, const float4* U, const float2* clov, const cplx<float>* in, void* out, bool out_dw, int nrhs,
                      cudaStream_t st) {
-    const int nt = 128;
-    long long nblk = (long long)ceil_div(g.V, nt) * nrhs;
-    if (out_dw) dslash_dw_kernel<true><<<(unsigned)nblk, nt, 0, st>>>(g, U, clov, in, out, nrhs);
-    else dslash_dw_kernel<false><<<(unsigned)nblk, nt, 0, st>>>(g, U, clov, in, out, nrhs);
+    const int ry = std::min(nrhs, 4);
+    const dim3 grid((unsigned)ceil_div(g.V, 32), (unsigned)ceil_div(nrhs, ry)), block(32, ry);
+    if (out_dw) dslash_dw_kernel<true><<<grid, block, 0, st>>>(g, U, clov, in, out, nrhs);
+    else dslash_dw_kernel<false><<<grid, block, 0, st>>>(g, U, clov, in, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -314,7 +314,7 @@ def main():
     fp32_peak_tf = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ridge = fp32_peak_tf * 1e12 / (peak * 1e9)
     tr = json.load(open(TRAFFIC_JSON)).get(f"{args.workload}/{args.precision}/{dominant}")
-    traffic = tr["bytes_per_launch"] if tr else None
+    traffic = tr["bytes_per_launch"] if tr else None  # null: no DRAM capture of this kernel version
     if flops_pl > 0 and flops_pl / bytes_pl > ridge:
         ach = flops_pl / sec / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": fp32_peak_tf,
@@ -325,6 +325,8 @@ def main():
         ach = bytes_pl / sec / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": ach / peak, "traffic": traffic}
+    if traffic is None:
+        roof["traffic_note"] = "no ncu DRAM capture of the current version of this kernel"
     roof.update({"launches": d["launches"], "avg_launch_us": 1e6 * sec, "algorithmic_bytes_per_launch": bytes_pl,
                  "algorithmic_flops_per_launch": flops_pl, "time_share_of_step": d["total_ms"] / ms if ms else None})
     iters = [s["iterations"] for s in stats[-1]]

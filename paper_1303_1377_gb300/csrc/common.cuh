@@ -109,6 +109,13 @@ struct LinksAoS {
 struct CloverAoS {
     const float4* p;  // [V][18]: the 72 packed reals of the site's two hermitian 6x6 blocks
 };
+// the same per-site copies in FP16 (half-precision V-cycle): FP32 arithmetic on load
+struct LinksAoS16 {
+    const uint4* p;  // [V][4][3]: U_mu(x) as 9 complex halves (36 bytes) + 12 padding bytes
+};
+struct CloverAoS16 {
+    const uint4* p;  // [V][9]: the 72 packed reals as halves
+};
 
 struct Geom {
     int V;       // fine sites

@@ -1,6 +1,8 @@
 // Device helpers of the Wilson-clover operator (Sec. 2.2) shared by the fine
 // kernels and the coarse-stencil assembly.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace ddamg {
@@ -51,6 +53,17 @@ __device__ __forceinline__ void load_link(cplx<float> (&W)[9], const LinksAoS& U
     const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3), e = __ldg(q + 4);
     W[0] = mk(a.x, a.y), W[1] = mk(a.z, a.w), W[2] = mk(b.x, b.y), W[3] = mk(b.z, b.w), W[4] = mk(c.x, c.y);
     W[5] = mk(c.z, c.w), W[6] = mk(d.x, d.y), W[7] = mk(d.z, d.w), W[8] = mk(e.x, e.y);
+}
+__device__ __forceinline__ float2 h2f(unsigned u) { return __half22float2(*reinterpret_cast<const __half2*>(&u)); }
+__device__ __forceinline__ void load_link(cplx<float> (&W)[9], const LinksAoS16& U, int /*V*/, int mu, int i) {
+    const uint4* q = U.p + ((size_t)i * 4 + mu) * 3;
+    const uint4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    const unsigned w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 f = h2f(w[k]);
+        W[k] = mk(f.x, f.y);
+    }
 }
 // acc += hop of psi_n (the neighbour spinor) through link W in direction MU,
 // FWD: (I - gamma_mu) (x) W with W = U_mu(x);  !FWD: (I + gamma_mu) (x) W^H with W = U_mu(x - mu).
@@ -166,6 +179,38 @@ __device__ __forceinline__ void herm_apply(const T* __restrict__ cl, int V, int 
     }
 }
 
+// the same product with the site term read from its FP16 per-site copy (9 x 16 bytes per site):
+// block h's 36 halves start at half 36 h, inside the aligned 16-byte words 4h .. 4h + 4
+__device__ __forceinline__ void herm_apply(const CloverAoS16& cl, int /*V*/, int i, const Spinor<float>& x, Spinor<float>& y) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint4* q = cl.p + (size_t)i * 9 + 4 * h;
+        unsigned w[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const uint4 v = __ldg(q + k);
+            w[4 * k] = v.x, w[4 * k + 1] = v.y, w[4 * k + 2] = v.z, w[4 * k + 3] = v.w;
+        }
+        const int o = 2 * h;  // block h's first half is word o (each word holds two halves)
+        auto cf = [&](int j) -> float {
+            const float2 f = h2f(w[o + j / 2]);
+            return (j & 1) ? f.y : f.x;
+        };
+#pragma unroll
+        for (int a2 = 0; a2 < 6; ++a2) y.v[h * 6 + a2] = cf(a2) * x.v[h * 6 + a2];
+        int m = 0;
+#pragma unroll
+        for (int a2 = 0; a2 < 6; ++a2) {
+#pragma unroll
+            for (int b2 = a2 + 1; b2 < 6; ++b2) {
+                const cplx<float> e = mk(cf(6 + 2 * m), cf(7 + 2 * m));
+                cmac(y.v[h * 6 + a2], e, x.v[h * 6 + b2]);
+                cmac_conj(y.v[h * 6 + b2], e, x.v[h * 6 + a2]);
+                ++m;
+            }
+        }
+    }
+}
 // the same product with the site term read from its per-site copy (9 float4 per block)
 __device__ __forceinline__ void herm_apply(const CloverAoS& cl, int /*V*/, int i, const Spinor<float>& x, Spinor<float>& y) {
 #pragma unroll

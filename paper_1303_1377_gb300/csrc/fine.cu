@@ -7,6 +7,8 @@
 //   links   cplx<T>[4][9][V]      U_mu(x)[a][b] at ((mu*9 + a*3 + b) * V + x)
 //   clover  T[72][V]              two hermitian 6x6 chiral blocks (spins {0,1}, {2,3}),
 //                                 each 6 real diagonal entries + 15 complex upper entries
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "dirac.cuh"
 #include "dw.cuh"
@@ -491,6 +493,53 @@ int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>*
     if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<float, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
     if (H % 32 == 0) return launch_sap_lean<float, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
     return -1;
+}
+
+int launch_sap_colour_aos16(const Geom& g, const FineOpAoS16& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs,
+                            int mr_steps, cudaStream_t st) {
+    const int H = g.Vb / 2;
+    if (nrhs >= 4 && H == 128) return launch_sap_lean<float, 4, FineOpAoS16, 128>(g, op, b, z, colour, nrhs, mr_steps, st);
+    if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<float, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
+    if (H % 32 == 0) return launch_sap_lean<float, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
+    return -1;
+}
+
+__device__ __forceinline__ unsigned pack_h2(float a, float b) {
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned*>(&v);
+}
+__global__ void links_to_aos16_kernel(const cplx<float>* __restrict__ U, uint4* __restrict__ out, int V) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;  // q = site * 4 + mu
+    if (q >= 4 * V) return;
+    const int i = q / 4, mu = q % 4;
+    unsigned w[12];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const cplx<float> u = U[(size_t)(mu * 9 + c) * V + i];
+        w[c] = pack_h2(u.re, u.im);
+    }
+    w[9] = w[10] = w[11] = 0u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[(size_t)q * 3 + k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+int links_to_aos16(const cplx<float>* U, uint4* out, int V, cudaStream_t st) {
+    links_to_aos16_kernel<<<ceil_div(4LL * V, 256), 256, 0, st>>>(U, out, V);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+__global__ void clover_to_aos16_kernel(const float* __restrict__ cl, uint4* __restrict__ out, int V) {
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // q = site * 9 + k
+    if (q >= (size_t)9 * V) return;
+    const int i = (int)(q / 9), k = (int)(q % 9);
+    unsigned w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w[e] = pack_h2(cl[(size_t)(8 * k + 2 * e) * V + i], cl[(size_t)(8 * k + 2 * e + 1) * V + i]);
+    out[q] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+int clover_to_aos16(const float* cl, uint4* out, int V, cudaStream_t st) {
+    clover_to_aos16_kernel<<<ceil_div(9LL * V, 256), 256, 0, st>>>(cl, out, V);
+    DD_CHECK_LAUNCH();
+    return 0;
 }
 
 __global__ void links_to_aos_kernel(const cplx<float>* __restrict__ U, float4* __restrict__ out, int V) {

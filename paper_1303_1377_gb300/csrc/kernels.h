@@ -20,6 +20,10 @@ struct FineOpAoS {  // LinksAoS, CloverAoS: common.cuh
     LinksAoS U;
     CloverAoS clov, clovinv;
 };
+struct FineOpAoS16 {
+    LinksAoS16 U;
+    CloverAoS16 clov, clovinv;
+};
 
 // coarse stencil in storage type S (float, double or __half2 packed as cplx<half>)
 template <typename S>
@@ -42,6 +46,11 @@ int launch_sap_colour(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx
 int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
                           cudaStream_t st);
 bool sap_aos_supported(const Geom& g, int nrhs);
+int launch_sap_colour_aos16(const Geom& g, const FineOpAoS16& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs,
+                            int mr_steps, cudaStream_t st);
+// FP32 [comp][V] -> FP16 per-site copies (links [V][4][3] uint4, site term [V][9] uint4)
+int links_to_aos16(const cplx<float>* U, uint4* out, int V, cudaStream_t st);
+int clover_to_aos16(const float* cl, uint4* out, int V, cudaStream_t st);
 // [comp][V] -> per-site copies (links: 4 x 9 complex -> [V][4][5] float4; site term: 72 -> [V][18] float4)
 int links_to_aos(const cplx<float>* U, float4* out, int V, cudaStream_t st);
 int clover_to_aos(const float* cl, float4* out, int V, cudaStream_t st);

@@ -203,6 +203,7 @@ struct ddamg_handle {
     cplx<float>* U32 = nullptr;
     float *clov32 = nullptr, *clovinv32 = nullptr;
     float4 *Uaos = nullptr, *clov_aos = nullptr, *clovinv_aos = nullptr;  // per-site FP32 copies for the SAP
+    uint4 *Uaos16 = nullptr, *clov_aos16 = nullptr, *clovinv_aos16 = nullptr;  // half mode: FP16 per-site copies
     float4* Udw = nullptr;    // links as double-word FP32 pairs (FGMRES matvec on FP32 inputs)
     float2* clovdw = nullptr;  // site terms as double-word pairs
     // interpolation
@@ -525,9 +526,18 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
     Level<T> L = level<T>(h);
     for (int it = 0; it < nu; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * sizeof(T) + 144.0 * sizeof(T) + nrhs * 36.0 * 2 * sizeof(T)),
+            // operator bytes at their stored size: FP16 links and site terms on the half-mode path
+            const bool f16 = std::is_same<T, float>::value && h->half() && sap_aos_supported(h->g, nrhs);
+            const double opb = f16 ? 2.0 : (double)sizeof(T);
+            Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * opb + 144.0 * opb + nrhs * 36.0 * 2 * sizeof(T)),
                     (double)h->V / 4 * nrhs * sap_pair_flops(h));
             if constexpr (std::is_same<T, float>::value) {
+                if (f16) {
+                    // half-precision V-cycle: links and site terms of the smoother stored in FP16
+                    const FineOpAoS16 op{LinksAoS16{h->Uaos16}, CloverAoS16{h->clov_aos16}, CloverAoS16{h->clovinv_aos16}};
+                    DD_TRY(launch_sap_colour_aos16(h->g, op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
+                    continue;
+                }
                 if (sap_aos_supported(h->g, nrhs)) {
                     const FineOpAoS op{LinksAoS{h->Uaos}, CloverAoS{h->clov_aos}, CloverAoS{h->clovinv_aos}};
                     DD_TRY(launch_sap_colour_aos(h->g, op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
@@ -1337,6 +1347,8 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             (rc = dalloc_n(&h->P16, V * 12 * N)))
             return fail(rc);
         h->tc = CoarseTC{h->Bh, h->Dh, h->d_bnbr, h->NB, (int)nc, Mt, Kta, Kth, Ktd};
+        if ((rc = dalloc_n(&h->Uaos16, V * 12)) || (rc = dalloc_n(&h->clov_aos16, V * 9)) || (rc = dalloc_n(&h->clovinv_aos16, V * 9)))
+            return fail(rc);
     } else if (h->single()) {
         if ((rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
             (rc = dalloc_n(&h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2)))
@@ -1355,6 +1367,10 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             (rc = launch_to_dw(h->clov64, h->clovdw, V * 72, h->stream)) || (rc = links_to_aos(h->U32, h->Uaos, h->V, h->stream)) ||
             (rc = clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream)) ||
             (rc = clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream)))
+            return fail(rc);
+        if (h->half() && ((rc = links_to_aos16(h->U32, h->Uaos16, h->V, h->stream)) ||
+                          (rc = clover_to_aos16(h->clov32, h->clov_aos16, h->V, h->stream)) ||
+                          (rc = clover_to_aos16(h->clovinv32, h->clovinv_aos16, h->V, h->stream))))
             return fail(rc);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1937,6 +1953,10 @@ int ddamg_set_mass(ddamg_handle* h, double m0) {
         DD_TRY(launch_to_dw(h->clov64, h->clovdw, (size_t)h->V * 72, h->stream));
         DD_TRY(clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream));
         DD_TRY(clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream));
+        if (h->half()) {
+            DD_TRY(clover_to_aos16(h->clov32, h->clov_aos16, h->V, h->stream));
+            DD_TRY(clover_to_aos16(h->clovinv32, h->clovinv_aos16, h->V, h->stream));
+        }
     }
     if (h->ready) {
         // mass re-use (Sec. 6.3): P is kept, D_c moves by (m0' - m0) I, only the inverses are redone
@@ -2038,6 +2058,9 @@ int ddamg_destroy(ddamg_handle* h) {
     dfree(h->clovinv64);
     dfree(h->U32);
     dfree(h->Uaos);
+    dfree(h->Uaos16);
+    dfree(h->clov_aos16);
+    dfree(h->clovinv_aos16);
     dfree(h->clov_aos);
     dfree(h->clovinv_aos);
     dfree(h->clov32);

@@ -104,6 +104,22 @@ def test_sap_four_rhs_lanes_with_partial_group(dd):
         assert relerr(s.apply_sap(b, 2), ref) < 2e-5
 
 
+def test_sap_half_mode_fp16_operator(dd):
+    """Half mode on 4^4 blocks: the smoother reads FP16 copies of the links and site terms and
+    computes in FP32. Against the FP64 oracle it stays at the FP16 storage level (stated tolerance
+    2e-3 relative to the field maximum after nu = 2 sweeps of four MR steps), for a full group of
+    four right-hand sides and for a partial one."""
+    c = case("8^4/4^4", dd)
+    sap = SAP(c.D, c.block, mr_steps=4)
+    b = synth.gaussian_spinors(c.dims, 5, seed=115)
+    ref = np.stack([sap.apply(b[r], 2) for r in range(5)])
+    p = dd.default_params(n_vec=8, block=c.block, precision=dd.PREC_HALF, nu=2)  # half mode wants N % 4 == 0
+    with dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False) as s:
+        s.setup_from_vectors(synth.random_test_vectors(c.dims, 8, seed=116))
+        assert relerr(s.apply_sap(b, 2), ref) < 2e-3
+        assert relerr(s.apply_sap(b[:4], 2), ref[:4]) < 2e-3
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_transfer_and_coarse_stencil(name, dd):
     c = case(name, dd)

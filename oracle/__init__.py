@@ -15,6 +15,8 @@ reordering beyond what the paper states.  Section references are to the paper:
   Sec. 4.3  Algorithm 1 (inexact deflation setup)
   Sec. 5    Algorithm 2 (DD-alpha-AMG setup), FGMRES with one V-cycle
   Sec. 6    odd-even preconditioning, Table 1 default parameters
+  Sec. 3, 7 the recursion to more than two levels (multilevel.py, with the readings
+            the paper leaves open stated in its docstring)
 
 Pin status of each function is listed in the module docstrings; the pins
 themselves live in tests/test_oracle_*.py.  Parity unpinned: iteration counts

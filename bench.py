@@ -19,6 +19,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # the oracle baseline runs on one core
@@ -60,32 +61,33 @@ class ClockSampler:
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path=None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = path
+        self.tmp = False
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.tmp = self.path is None
+            if self.tmp:
+                fd, self.path = tempfile.mkstemp(prefix=f"clocks_gpu{self.gpu}_", suffix=".csv")
+                os.close(fd)
+            else:
+                os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
+    @staticmethod
+    def parse(lines):
+        """Median SM clock, the maximum clock and every throttle reason seen Active, from the
+        query lines (index, sm, max sm, power, active mask, then the four reasons)."""
         sm, smax, reasons = [], None, set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -94,10 +96,40 @@ class ClockSampler:
                 smax = float(parts[2])
             except ValueError:
                 continue
-            for n, v in zip(names[1:], parts[5:9]):
+            for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+    def stop(self):
+        if not self.proc:
+            if self.tmp and self.path and os.path.exists(self.path):
+                os.remove(self.path)
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        with open(self.path) as f:
+            out = self.parse(f)
+        if self.tmp:
+            os.remove(self.path)
+        return out
+
+
+def metric_name(workload):
+    if workload == "32x32x32x64":
+        return "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)"
+    return f"solves/s to rel. residual 1e-10 ({workload})"
+
+
+def workload_description(workload, w, m0):
+    """The workload as both arms state it in config.workload."""
+    return (f"{workload} lattice (L0={w['dims'][0]}), SU(3) links exp(i eps H) eps={w['eps']} seed={w['seed']}, c_sw={C_SW}, "
+            f"m0={m0:.6f}, {w['nrhs']} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
+            f"MR(4), FGMRES(25) tol 1e-10, coarse GMRES(30) tol 5e-2")
 
 
 def make_rhs(w, V):
@@ -174,11 +206,11 @@ def run_reference(args, w):
             vals.append(v)
     value = float(np.mean(vals))
     line = {
-        "impl": "reference", "metric": "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)", "value": value,
+        "impl": "reference", "metric": metric_name(args.workload), "value": value,
         "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w["nrhs"] / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} lattice, eps={w['eps']}, c_sw={C_SW}, m0={m0:.6f}, {w['nrhs']} {w['rhs']} sources, "
-                               f"N_v={w['N']}, 4^4 blocks, nu={w['nu']}", "l2": "oracle on host cores"},
+        "config": {"workload": workload_description(args.workload, w, m0), "precision": "FP64 throughout (the oracle)",
+                   "l2": "oracle on host cores"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -201,6 +233,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain single-RHS FP64 comparison solve")
+    ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -260,7 +293,7 @@ def main():
     solver.profile([dominant])
     solver.profile_reset()
     # timed region
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv)
     clocks.start()
     n_launch0 = ddamg.launch_count()
     launches_before_timed = n_launch0
@@ -331,13 +364,11 @@ def main():
                  "algorithmic_flops_per_launch": flops_pl, "time_share_of_step": d["total_ms"] / ms if ms else None})
     iters = [s["iterations"] for s in stats[-1]]
     line = {
-        "metric": "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)" if args.workload == "32x32x32x64" else f"solves/s to rel. residual 1e-10 ({args.workload})",
+        "metric": metric_name(args.workload),
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.precision], "data": "synthetic",
-        "config": {"workload": f"{args.workload} lattice (L0={dims[0]}), SU(3) links exp(i eps H) eps={w['eps']} seed={w['seed']}, c_sw={C_SW}, "
-                               f"m0={m0:.6f}, {nr} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
-                               f"MR(4), FGMRES(25) tol 1e-10, coarse GMRES(30) tol 5e-2, V-cycle {args.precision}",
+        "config": {"workload": workload_description(args.workload, w, m0),
                    "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision,
                    "outer": (f"FP32 FGMRES cycles to {args.cycle_tol:g} + FP64 residual correction" if args.outer == "refine"
                              and args.precision != "double" else "double-word FGMRES" if args.precision != "double" else "FP64 FGMRES")},

@@ -18,5 +18,10 @@ def test_reference_arm_prints_the_contract_line():
               "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "solves/s"
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert line["metric"] == bench.metric_name("8x8x8x8")  # the same metric and workload text as the GPU arm
+    assert line["config"]["workload"].startswith("8x8x8x8 lattice (L0=8)")
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0

@@ -72,3 +72,34 @@ def test_invalid_outer_scheme_rejected_without_gpu_work(libpath, kw):
     with pytest.raises(ddamg.DDAMGError) as e:
         ddamg.Solver((4, 4, 4, 4), U, 0.0, 1.0, p, setup=False)
     assert e.value.status == -1 and "cycle_tol" in str(e.value)
+
+
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    """Size and every field offset of the ABI structs, as a C compiler lays them out from
+    include/ddamg.h, equal those of the ctypes binding."""
+    import shutil
+    import subprocess
+
+    from paper_1303_1377_gb300 import ddamg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ddamg_lattice": ddamg.Lattice, "ddamg_params": ddamg.Params, "ddamg_stats": ddamg.Stats,
+               "ddamg_kernel_profile": ddamg.KernelProfile}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ddamg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
     DDAMG_PREC_DOUBLE = 0, /* V-cycle in FP64 */
     DDAMG_PREC_SINGLE = 1, /* V-cycle in FP32 (the paper's mixed precision, Sec. 6) */
-    DDAMG_PREC_HALF = 2    /* V-cycle in FP32 with D_c and P stored in FP16 (FP32 accumulation) */
+    DDAMG_PREC_HALF = 2    /* V-cycle in FP32 with D_c and P stored in FP16 (FP32 accumulation); on
+                              4^4 blocks the smoother also reads FP16 copies of the links and site terms */
 } ddamg_precision;
 
 /* Outer iteration of SINGLE and HALF mode (no counterpart in the paper, which
@@ -206,7 +207,10 @@ int ddamg_apply_D_f32(ddamg_handle* h, const float* in, float* out, int n_rhs);
  * output).  Needs a single- or half-precision handle. */
 int ddamg_apply_D_mixed(ddamg_handle* h, const float* in, double* out, int n_rhs);
 
-/* out = M_SAP^(nu) in (Sec. 2.3) in the V-cycle precision; FP64 fields in/out. */
+/* out = M_SAP^(nu) in (Sec. 2.3) in the V-cycle precision; FP64 fields in/out.  In
+ * DDAMG_PREC_HALF on 4^4 blocks the links and site terms are read from FP16 copies (FP32
+ * arithmetic): the result then differs from the FP64 operator's by the FP16 storage error,
+ * a few 1e-4 relative to the field's maximum. */
 int ddamg_apply_sap(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);
 
 /* Coarse restriction out = P^H in (fine -> coarse) and prolongation out = P in

@@ -26,11 +26,13 @@ from . import ddamg
 
 
 def estimate_bytes(V: int, n_vec: int, n_slots: int, n_kv: int) -> int:
-    """Device memory of one operator: FP64/FP32/double-word links and site terms, the test
+    """Device memory of one operator: FP64/FP32/double-word links and site terms, the smoother's
+    per-site copies of them (FP32: 5 + 2 x 18 float4; FP16 in half mode: 12 + 2 x 9 uint4), the test
     vectors and interpolation (FP64, FP32, FP16), the setup's work fields (N FP32 fields,
     three of them), and per slot the FP32 bases (n_kv + 1 + n_kv fields) plus the FP64 slot
     right-hand side, iterate and residual work fields."""
     per_site = 4 * 9 * (16 + 8 + 16) + 2 * 72 * (8 + 4 + 8)
+    per_site += (4 * 5 + 2 * 18) * 16 + (4 * 3 + 2 * 9) * 16
     per_site += n_vec * 12 * (16 + 16 + 8 + 4)
     per_site += 3 * n_vec * 12 * 8
     per_slot = (2 * n_kv + 1) * 12 * 8 + 6 * 12 * 16

@@ -384,6 +384,9 @@ def main():
         "coarse_iterations_per_solve": stats[-1][0]["coarse_iterations"],
         "max_rel_residual": rel,
         "setup_seconds": t_setup,
+        # one setup serving one batch: the batch's solves over setup + one step's time
+        "amortised_incl_setup": {"value": nr / (t_setup + ms / args.steps / 1e3), "unit": "solves/s",
+                                 "per": f"one setup and one batch of {nr} right-hand sides"},
         "gauge_generation_seconds": t_gauge,
         "kernel_profile_first_step": prof_all,
     }

@@ -22,8 +22,9 @@ import sys
 import tempfile
 import time
 
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # the oracle baseline runs on one core
-os.environ.setdefault("OMP_NUM_THREADS", "1")
+if __name__ == "__main__":  # the oracle baseline runs on one core (set before numpy loads its BLAS)
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
 
 import numpy as np
 

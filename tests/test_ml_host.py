@@ -1,0 +1,199 @@
+"""The CUDA library's level-1 operations for the recursion to a third level (ml_geom.h, ml_ops.cuh),
+run on the host through their loop executor, against the oracle's multilevel classes.
+
+The same functors and orchestration run on the GPU through a grid-stride kernel; this checks their
+index arithmetic and algebra without a GPU.  The harness is built with nvcc as host code."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle.aggregation import Aggregation
+from oracle.coarse import CoarseOperator
+from oracle.dirac import DiracOperator
+from oracle.lattice import Blocking, Lattice
+from oracle.multilevel import StencilAggregation, StencilCoarse, StencilOperator, StencilSAP
+from paper_1303_1377_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1303_1377_gb300", "csrc")
+
+# (fine dims, level-0 aggregate, N0, level-1 block, N1)
+CASES = {
+    "8^4 -> 4^4 (2^4 blocks)": ((8, 8, 8, 8), (2, 2, 2, 2), 3, (2, 2, 2, 2), 3),
+    "4^4 -> 2x2x2x4 (1x1x1x2 blocks)": ((4, 4, 4, 4), (2, 2, 2, 1), 2, (1, 1, 1, 2), 2),
+}
+
+P_D = ctypes.POINTER(ctypes.c_double)
+P_I = ctypes.POINTER(ctypes.c_int)
+
+
+def dp(a):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(P_D)
+
+
+def ip(a):
+    return np.ascontiguousarray(a, dtype=np.int32).ctypes.data_as(P_I)
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = tmp_path_factory.mktemp("mlh") / "libmlh.so"
+    subprocess.run([nvcc, "-x", "cu", "-shared", "-Xcompiler", "-fPIC", "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-I", CSRC,
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "ml_host", "ml_harness.cu"), "-o", str(out)],
+                   check=True)
+    return ctypes.CDLL(str(out))
+
+
+class Level1:
+    """Level 1 of the oracle (D_1 = P_0^H D P_0) and the harness's internal orders."""
+
+    def __init__(self, lib, name):
+        dims, agg0, N0, b1, N1 = CASES[name]
+        D = DiracOperator(synth.gauge_field(dims, 0.4, seed=91), dims, 0.1, 1.0)
+        Dc = CoarseOperator(D, Aggregation(D.lat, agg0, synth.random_test_vectors(dims, N0, seed=92)))
+        self.A = StencilOperator(Dc.clat, Dc.B)
+        self.L1 = np.array(Dc.clat.dims, dtype=np.int32)
+        self.b1 = np.array(b1, dtype=np.int32)
+        self.nc, self.N1, self.lib = self.A.n, N1, lib
+        sz = np.zeros(4, dtype=np.int32)
+        assert lib.mlh_geom_sizes(ip(self.L1), ip(self.b1), ip(sz)) == 0
+        self.NB, self.NB2, self.Vb1, self.Vb1e = (int(s) for s in sz)
+        g = {k: np.zeros(n, dtype=np.int32) for k, n in (("lex1", self.NB), ("nbr1", 8 * self.NB), ("sites", self.NB2 * self.Vb1),
+                                                         ("blk_of", self.NB), ("loc_of", self.NB), ("nbr2", 8 * self.NB2),
+                                                         ("lex2", self.NB2))}
+        same = np.zeros(8 * self.NB, dtype=np.uint8)
+        assert lib.mlh_geom_fill(ip(self.L1), ip(self.b1), *(g[k].ctypes.data_as(P_I) for k in ("lex1", "nbr1", "sites", "blk_of", "loc_of")),
+                                 same.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), g["nbr2"].ctypes.data_as(P_I),
+                                 g["lex2"].ctypes.data_as(P_I)) == 0
+        self.g, self.same = g, same.reshape(8, self.NB)
+        lex1 = g["lex1"]
+        # column-major blocks in internal order; inverses of the even self blocks
+        self.B1 = np.ascontiguousarray(self.A.B[lex1].transpose(0, 1, 3, 2))
+        self.Dinv1 = np.ascontiguousarray(np.linalg.inv(self.A.B[lex1[: self.NB // 2], 0]).transpose(0, 2, 1))
+
+    def to_int(self, x):  # [nrhs, NB, nc] lexicographic -> internal
+        return np.ascontiguousarray(x[:, self.g["lex1"]])
+
+    def to_lex(self, x):
+        out = np.empty_like(x)
+        out[:, self.g["lex1"]] = x
+        return out
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def lv(request, lib):
+    return Level1(lib, request.param)
+
+
+def test_blocking_matches_the_oracle(lv):
+    """Internal order (even sites first), neighbours, blocks, in-block flags and the level-2 lattice
+    agree with the oracle's lattice and blocking."""
+    lat = Lattice(tuple(lv.L1))
+    lex1, lex2 = lv.g["lex1"], lv.g["lex2"]
+    assert sorted(lex1) == list(range(lv.NB))
+    assert np.all(lat.parity[lex1[: lv.NB // 2]] == 0) and np.all(lat.parity[lex1[lv.NB // 2:]] == 1)
+    int1 = np.empty(lv.NB, dtype=np.int64)
+    int1[lex1] = np.arange(lv.NB)
+    blk = Blocking(lat, tuple(lv.b1))
+    nbr1 = lv.g["nbr1"].reshape(8, lv.NB)
+    for d in range(8):
+        mu, s = d >> 1, (-1 if d & 1 else 1)
+        assert np.array_equal(nbr1[d], int1[lat.neighbour(mu, s)[lex1]])
+        assert np.array_equal(lv.same[d].astype(bool), blk.same_block(mu, s)[lex1])
+    sites = lv.g["sites"].reshape(lv.NB2, lv.Vb1)
+    assert lv.Vb1e == lv.Vb1 // 2
+    for c2 in range(lv.NB2):
+        assert set(lex1[sites[c2]]) == set(blk.sites[lex2[c2]])
+        assert np.all(sites[c2, : lv.Vb1e] < lv.NB // 2) and np.all(sites[c2, lv.Vb1e:] >= lv.NB // 2)
+        assert np.all(lv.g["blk_of"][sites[c2]] == c2) and np.array_equal(lv.g["loc_of"][sites[c2]], np.arange(lv.Vb1))
+    lat2 = Lattice(blk.nb_dims)
+    assert np.all(lat2.parity[lex2[: lv.NB2 // 2]] == 0) and np.all(lat2.parity[lex2[lv.NB2 // 2:]] == 1)
+    int2 = np.empty(lv.NB2, dtype=np.int64)
+    int2[lex2] = np.arange(lv.NB2)
+    nbr2 = lv.g["nbr2"].reshape(8, lv.NB2)
+    for d in range(8):
+        assert np.array_equal(nbr2[d], int2[lat2.neighbour(d >> 1, -1 if d & 1 else 1)[lex2]])
+
+
+def test_operator_apply(lv):
+    x = synth.gaussian_coarse(lv.NB, lv.nc, 2, seed=93)
+    y = np.zeros_like(x)
+    assert lv.lib.mlh_apply(ip(lv.L1), ip(lv.b1), lv.nc, dp(lv.B1), dp(lv.to_int(x)), dp(y), 2) == 0
+    ref = np.stack([lv.A.apply(x[r]) for r in range(2)])
+    assert np.max(np.abs(lv.to_lex(y) - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+def test_sap_matches_the_oracle(lv, nu):
+    """nu red-black SAP iterations with MR(4) block solves, from zero and from a nonzero start."""
+    b = synth.gaussian_coarse(lv.NB, lv.nc, 3, seed=94)
+    sap = StencilSAP(lv.A, tuple(lv.b1), mr_steps=4)
+    for z0 in (np.zeros_like(b), synth.gaussian_coarse(lv.NB, lv.nc, 3, seed=95)):
+        ref = []
+        for r in range(3):
+            z = z0[r].copy()
+            for _ in range(nu):
+                z = sap.iterate(z, b[r])
+            ref.append(z)
+        ref = np.stack(ref)
+        z = lv.to_int(z0)
+        assert lv.lib.mlh_sap(ip(lv.L1), ip(lv.b1), lv.nc, dp(lv.B1), dp(lv.Dinv1), dp(lv.to_int(b)), dp(z), 3, nu, 4) == 0
+        assert np.max(np.abs(lv.to_lex(z) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_gram_schmidt_and_transfers_match_the_oracle(lv):
+    """P_1 from the harness's ordered Gram-Schmidt restricts and prolongs like the oracle's
+    aggregation of the same level-1 test vectors."""
+    vec = synth.gaussian_coarse(lv.NB, lv.nc, lv.N1, seed=96)  # [N1, NB, nc]
+    P = np.zeros((lv.NB2, 2, lv.Vb1 * lv.nc // 2, lv.N1), dtype=np.complex128)
+    assert lv.lib.mlh_gram_schmidt(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.to_int(vec)), dp(P)) == 0
+    agg = StencilAggregation(Lattice(tuple(lv.L1)), tuple(lv.b1), vec)
+    x = synth.gaussian_coarse(lv.NB, lv.nc, 2, seed=97)
+    e = np.zeros((2, lv.NB2, 2 * lv.N1), dtype=np.complex128)
+    assert lv.lib.mlh_restrict(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(P), dp(lv.to_int(x)), dp(e), 2) == 0
+    lex2 = lv.g["lex2"]
+    ref = np.stack([agg.restrict(x[r]) for r in range(2)])[:, lex2]
+    assert np.max(np.abs(e - ref)) < 1e-12 * np.max(np.abs(ref))
+    ec = synth.gaussian_coarse(lv.NB2, 2 * lv.N1, 2, seed=98)  # internal level-2 order
+    y = np.zeros((2, lv.NB, lv.nc), dtype=np.complex128)
+    assert lv.lib.mlh_prolong(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(P), dp(ec), dp(y), 2) == 0
+    ec_lex = np.empty_like(ec)
+    ec_lex[:, lex2] = ec
+    ref = np.stack([agg.prolong(ec_lex[r]) for r in range(2)])
+    assert np.max(np.abs(lv.to_lex(y) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_galerkin_stencil_matches_the_oracle(lv):
+    """D_2 = P_1^H D_1 P_1 assembled by the harness equals the oracle's stencil, block by block."""
+    vec = synth.gaussian_coarse(lv.NB, lv.nc, lv.N1, seed=99)
+    P = np.zeros((lv.NB2, 2, lv.Vb1 * lv.nc // 2, lv.N1), dtype=np.complex128)
+    assert lv.lib.mlh_gram_schmidt(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.to_int(vec)), dp(P)) == 0
+    nc2 = 2 * lv.N1
+    B2 = np.zeros((lv.NB2, 9, nc2, nc2), dtype=np.complex128)
+    assert lv.lib.mlh_galerkin(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.B1), dp(P), dp(B2)) == 0
+    ref = StencilCoarse(lv.A, StencilAggregation(Lattice(tuple(lv.L1)), tuple(lv.b1), vec)).B
+    ref_int = ref[lv.g["lex2"]].transpose(0, 1, 3, 2)
+    assert np.max(np.abs(B2 - ref_int)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_rank_deficient_level1_vectors_are_reported(lv):
+    vec = synth.gaussian_coarse(lv.NB, lv.nc, lv.N1, seed=100)
+    vec[-1] = vec[0]
+    P = np.zeros((lv.NB2, 2, lv.Vb1 * lv.nc // 2, lv.N1), dtype=np.complex128)
+    assert lv.lib.mlh_gram_schmidt(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.to_int(vec)), dp(P)) == -8
+
+
+def test_invalid_level1_blockings_are_refused(lib):
+    sz = np.zeros(4, dtype=np.int32)
+    for L1, b1 in (((4, 4, 4, 4), (4, 2, 2, 2)),   # one block in a direction (odd count)
+                   ((4, 4, 4, 4), (3, 2, 2, 2)),   # does not divide
+                   ((2, 2, 2, 2), (1, 1, 1, 1))):  # every block extent odd
+        assert lib.mlh_geom_sizes(ip(np.array(L1)), ip(np.array(b1)), ip(sz)) == -1

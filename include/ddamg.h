@@ -297,6 +297,65 @@ long long ddamg_launch_count(void);
 /* Test hook: make the next n device allocations of the library fail (OOM). */
 void ddamg_debug_fail_allocs(int n);
 
+/* ---- Recursion to a third level (Sec. 3: the two-level algorithm formulated again for the coarse
+ * system, whose solve then needs only low accuracy; Sec. 7: 3 and 4 levels).  The paper prints no
+ * algorithm for it; this one is:
+ *   level 1 = the handle's coarse lattice and D_1 = D_c; its lattice blocks (block1) are the
+ *   level-1 SAP domains and aggregates; P_1 is the ordered orthonormal basis of the level-1 test
+ *   vectors on each (block, Gamma5^c half); D_2 = P_1^H D_1 P_1, solved by odd-even GMRES (Sec. 6);
+ *   the level-1 V-cycle is x = P_1 D_2^{-1} P_1^H r followed by nu1 SAP iterations on D_1 x = r;
+ *   the fine V-cycle's coarse solve becomes FGMRES(inner_kv) on D_1 to inner_tol preconditioned by
+ *   the level-1 V-cycle (inner = 0), or one level-1 V-cycle (inner = 1).
+ * DOUBLE-precision handles only.  The third level is tied to the coarse operator it was built
+ * from: after ddamg_run_setup, ddamg_setup_from_vectors or ddamg_set_mass the calls below return
+ * DDAMG_ERR_NOT_READY until ddamg_ml_build runs again.
+ * Level-1 vectors use the coarse layout of ddamg_restrict ([n_rhs][coarse sites lex][2N]);
+ * level-2 vectors are [n_rhs][level-2 sites lex][2 n_vec1], the level-2 sites being the level-1
+ * blocks numbered lexicographically by block coordinates, component h * n_vec1 + j for the j-th
+ * vector on the Gamma5^c half h.  Pointers may be host or device memory (as elsewhere). */
+typedef struct {
+    int block1[4];      /* level-1 block in coarse sites: SAP domain and aggregate (2,2,2,2) */
+    int n_vec1;         /* level-1 test vectors N_1 per aggregate half (20) */
+    int nu1;            /* SAP iterations of the level-1 V-cycle (2) */
+    int mr_steps1;      /* MR steps of its block solver (4) */
+    int inner;          /* 0: FGMRES on D_1 with the level-1 V-cycle; 1: one level-1 V-cycle (0) */
+    int inner_kv;       /* restart length of that FGMRES (10) */
+    double inner_tol;   /* its relative residual target (5e-2) */
+    int inner_maxiter;  /* cap on its iterations per solve (1000) */
+    double coarse_tol;  /* relative residual target of the odd-even GMRES on D_2 (5e-2) */
+    int coarse_restart; /* its restart length (30) */
+    int coarse_maxiter; /* cap on its iterations per solve (1000) */
+} ddamg_ml_params;
+void ddamg_ml_default_params(ddamg_ml_params* p);
+
+/* Build level 2 from the level-1 test vectors v1 ([n_vec1][coarse sites lex][2N]): P_1, D_2 and the
+ * inverses of D_2's even diagonal blocks.  INVALID_ARG: not DOUBLE precision, block1 not dividing
+ * the coarse lattice into an even number of blocks per direction (with one even extent), or a
+ * parameter out of range; RANK: v1 linearly dependent on an aggregate or a singular diagonal block
+ * of D_2 (the previous third level is then released). */
+int ddamg_ml_build(ddamg_handle* h, const ddamg_ml_params* p, const double* v1);
+/* Release the third level (ddamg_destroy does it too). */
+int ddamg_ml_release(ddamg_handle* h);
+/* out = M_SAP^(nu) in on level 1 (red-black SAP of D_1 over the level-1 blocks, MR block solves). */
+int ddamg_ml_apply_sap1(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);
+/* Level-1 restriction out = P_1^H in (level 1 -> level 2) and prolongation out = P_1 in. */
+int ddamg_ml_restrict1(ddamg_handle* h, const double* in, double* out, int n_rhs);
+int ddamg_ml_prolong1(ddamg_handle* h, const double* in, double* out, int n_rhs);
+/* out = D_2 in on level-2 vectors. */
+int ddamg_ml_apply_D2(ddamg_handle* h, const double* in, double* out, int n_rhs);
+/* out = the level-1 V-cycle applied to in (level-1 vectors). */
+int ddamg_ml_vcycle1(ddamg_handle* h, const double* in, double* out, int n_rhs);
+/* out = the fine V-cycle with the recursive coarse solve applied to in (fine spinors);
+ * inner_fixed_iters > 0 runs exactly that many FGMRES steps on D_1 instead of stopping at inner_tol. */
+int ddamg_ml_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, int inner_fixed_iters);
+/* Three-level solve: FGMRES(n_kv) on D preconditioned by ddamg_ml_vcycle, from z = 0, to the
+ * relative residual tol; status and stats as ddamg_solve_batch (coarse_iterations = FGMRES steps
+ * on D_1). */
+int ddamg_ml_solve(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st);
+/* Counters of the last ddamg_ml_solve: out[0] FGMRES steps on D_1, out[1] GMRES steps on D_2,
+ * out[2] level-1 V-cycles (per right-hand side). */
+int ddamg_ml_counts(const ddamg_handle* h, long long* out);
+
 /* Release every resource of the handle. */
 int ddamg_destroy(ddamg_handle* h);
 

@@ -186,6 +186,10 @@ struct KrylovBufs {
 
 using namespace ddamg;
 
+namespace ddamg {
+struct MLState;  // third level of the recursion (multilevel.inc)
+}
+
 struct ddamg_handle {
     // geometry
     int L[4], b[4], nbk[4];
@@ -236,6 +240,9 @@ struct ddamg_handle {
     int prof_mask = 0;  // bit f: record kernel family f
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
+    // recursion to a third level (ddamg_ml_build); coarse_gen counts rebuilds and shifts of D_c
+    ddamg::MLState* ml = nullptr;
+    unsigned long long coarse_gen = 0;
 
     bool single() const { return p.precision != DDAMG_PREC_DOUBLE; }
     bool half() const { return p.precision == DDAMG_PREC_HALF; }
@@ -1061,6 +1068,7 @@ static int finish_coarse(ddamg_handle* h) {
         DD_TRY((convert<float, double>(h->Dinv64, h->Dinv32, (size_t)(h->NB / 2) * nc * nc * 2, st)));
     }
     DD_CUDA(cudaStreamSynchronize(st));
+    ++h->coarse_gen;
     h->ready = true;
     return 0;
 }
@@ -1415,6 +1423,8 @@ static int coarse_out(ddamg_handle* h, const cplx<T>* src, double* out, int nrhs
     DD_TRY((coarse_perm<double, T>(src, reinterpret_cast<cplx<double>*>(dv), h->d_clex_of, h->NB, h->nc, nrhs, 0, h->stream)));
     return finish_out(h, out, dv, sizeof(cplx<double>) * n * nrhs, host);
 }
+
+static void ml_release(ddamg_handle* h);  // multilevel.inc
 
 }  // namespace ddamg
 
@@ -2048,6 +2058,7 @@ int ddamg_profile_read(ddamg_handle* h, ddamg_kernel_profile* out, int max) {
 int ddamg_destroy(ddamg_handle* h) {
     if (!h) return 0;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    ml_release(h);
     dfree(h->d_lnbr);
     dfree(h->d_bnbr);
     dfree(h->d_lex_of);
@@ -2098,3 +2109,5 @@ int ddamg_destroy(ddamg_handle* h) {
 }
 
 }  // extern "C"
+
+#include "multilevel.inc"

@@ -87,6 +87,24 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MLParams(C.Structure):
+    """ddamg_ml_params: the third level of the recursion (level-1 blocks, N_1, inner solves)."""
+
+    _fields_ = [
+        ("block1", C.c_int * 4),
+        ("n_vec1", C.c_int),
+        ("nu1", C.c_int),
+        ("mr_steps1", C.c_int),
+        ("inner", C.c_int),
+        ("inner_kv", C.c_int),
+        ("inner_tol", C.c_double),
+        ("inner_maxiter", C.c_int),
+        ("coarse_tol", C.c_double),
+        ("coarse_restart", C.c_int),
+        ("coarse_maxiter", C.c_int),
+    ]
+
+
 class KernelProfile(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_longlong), ("total_ms", C.c_double), ("bytes", C.c_double),
                 ("flops", C.c_double)]
@@ -133,6 +151,17 @@ def _load():
         "ddamg_slots_cycle": (I, [P, C.POINTER(I), C.POINTER(Stats)]),
         "ddamg_slot_take": (I, [P, I, P]),
         "ddamg_slots_close": (I, [P]),
+        "ddamg_ml_default_params": (None, [C.POINTER(MLParams)]),
+        "ddamg_ml_build": (I, [P, C.POINTER(MLParams), P]),
+        "ddamg_ml_release": (I, [P]),
+        "ddamg_ml_apply_sap1": (I, [P, P, P, I, I]),
+        "ddamg_ml_restrict1": (I, [P, P, P, I]),
+        "ddamg_ml_prolong1": (I, [P, P, P, I]),
+        "ddamg_ml_apply_D2": (I, [P, P, P, I]),
+        "ddamg_ml_vcycle1": (I, [P, P, P, I]),
+        "ddamg_ml_vcycle": (I, [P, P, P, I, I]),
+        "ddamg_ml_solve": (I, [P, P, P, I, D, C.POINTER(Stats)]),
+        "ddamg_ml_counts": (I, [P, C.POINTER(LL)]),
         "ddamg_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -152,6 +181,18 @@ def default_params(**kw) -> Params:
         if k == "block":
             for m in range(4):
                 p.block[m] = int(v[m])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def ml_default_params(**kw) -> MLParams:
+    p = MLParams()
+    lib.ddamg_ml_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "block1":
+            for m in range(4):
+                p.block1[m] = int(v[m])
         else:
             setattr(p, k, v)
     return p
@@ -260,6 +301,59 @@ class Solver:
         rc = lib.ddamg_solve_batch(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
         _check(rc, "ddamg_solve_batch", allow=(-4, -5) if allow_fail else ())
         return z, [s.as_dict() for s in st], rc
+
+    # -- recursion to a third level ------------------------------------------------
+    def ml_build(self, v1, params: MLParams | None = None):
+        """Level 2 from the level-1 test vectors v1[N1, coarse sites, 2N] (coarse layout)."""
+        self.ml_params = params if params is not None else ml_default_params()
+        v1 = _host(v1, np.complex128)
+        _check(lib.ddamg_ml_build(self.h, C.byref(self.ml_params), _ptr(v1)), "ddamg_ml_build")
+        nb1 = [self.coarse_dims()[m] // self.ml_params.block1[m] for m in range(4)]
+        self.n_level2 = int(np.prod(nb1))
+        self.level2_dof = 2 * self.ml_params.n_vec1
+
+    def coarse_dims(self):
+        return tuple(self.dims[m] // self.params.block[m] for m in range(4))
+
+    def ml_release(self):
+        _check(lib.ddamg_ml_release(self.h), "ddamg_ml_release")
+
+    def _ml_op(self, fn, x, out_shape, *extra):
+        x = _host(x, np.complex128)
+        nr = int(x.shape[0])
+        out = _empty_like(x, (nr,) + tuple(out_shape), np.complex128)
+        _check(fn(self.h, _ptr(x), _ptr(out), nr, *extra), fn.__name__)
+        return out
+
+    def ml_apply_sap1(self, x, nu: int):
+        return self._ml_op(lib.ddamg_ml_apply_sap1, x, (self.n_coarse, self.coarse_dof), int(nu))
+
+    def ml_restrict1(self, x):
+        return self._ml_op(lib.ddamg_ml_restrict1, x, (self.n_level2, self.level2_dof))
+
+    def ml_prolong1(self, e):
+        return self._ml_op(lib.ddamg_ml_prolong1, e, (self.n_coarse, self.coarse_dof))
+
+    def ml_apply_D2(self, e):
+        return self._ml_op(lib.ddamg_ml_apply_D2, e, (self.n_level2, self.level2_dof))
+
+    def ml_vcycle1(self, x):
+        return self._ml_op(lib.ddamg_ml_vcycle1, x, (self.n_coarse, self.coarse_dof))
+
+    def ml_vcycle(self, r, inner_fixed_iters: int = 0):
+        return self._ml_op(lib.ddamg_ml_vcycle, r, (self.V, 4, 3), int(inner_fixed_iters))
+
+    def ml_solve(self, b, tol: float = 1e-10, allow_fail: bool = False):
+        """Three-level solve of D z = b for b[n_rhs, V, 4, 3] from z = 0."""
+        b = _host(b, np.complex128)
+        nr = int(b.shape[0])
+        z = _empty_like(b, b.shape, np.complex128)
+        st = (Stats * nr)()
+        rc = lib.ddamg_ml_solve(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
+        _check(rc, "ddamg_ml_solve", allow=(-4, -5) if allow_fail else ())
+        cnt = (C.c_longlong * 3)()
+        lib.ddamg_ml_counts(self.h, cnt)
+        return z, [s.as_dict() for s in st], {"fgmres_steps_D1": cnt[0], "gmres_steps_D2": cnt[1], "vcycles1": cnt[2]}
 
     # -- continuous batching ------------------------------------------------------
     def slots_open(self, n_slots: int):

@@ -86,7 +86,7 @@ def test_struct_layouts_match_the_compiled_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"ddamg_lattice": ddamg.Lattice, "ddamg_params": ddamg.Params, "ddamg_stats": ddamg.Stats,
-               "ddamg_kernel_profile": ddamg.KernelProfile}
+               "ddamg_kernel_profile": ddamg.KernelProfile, "ddamg_ml_params": ddamg.MLParams}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ddamg.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -103,3 +103,15 @@ def test_struct_layouts_match_the_compiled_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_third_level_defaults_and_argument_checks(libpath):
+    """ddamg_ml_default_params, and the third-level calls refuse a null handle before any CUDA work."""
+    from paper_1303_1377_gb300 import ddamg
+
+    p = ddamg.ml_default_params()
+    assert (tuple(p.block1), p.n_vec1, p.nu1, p.mr_steps1, p.inner, p.inner_kv, p.inner_tol, p.coarse_tol, p.coarse_restart) == (
+        (2, 2, 2, 2), 20, 2, 4, 0, 10, 5e-2, 5e-2, 30)
+    assert ddamg.lib.ddamg_ml_build(None, ctypes.byref(p), None) == -1
+    assert ddamg.lib.ddamg_ml_solve(None, None, None, 1, 1e-10, None) == -1
+    assert ddamg.lib.ddamg_ml_release(None) == -1

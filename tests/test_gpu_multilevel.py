@@ -1,0 +1,118 @@
+"""The three-level path of the CUDA library (ddamg_ml_*) against the oracle's multilevel recursion.
+
+Not yet run on a GPU: the module runs only with DDAMG_ML_GPU=1, so its first GPU run is a
+deliberate single call rather than part of an unattended suite.  The level-1 functors it drives are
+checked on the host in tests/test_ml_host.py.
+
+Case: 8^4 fine lattice, 2^4 blocks, N = 4 -> level 1 = 4^4 coarse sites of 8 components; level-1
+blocks 2^4, N_1 = 3 -> level 2 = 2^4 sites of 6 components.  DOUBLE precision throughout, so the
+stated tolerances are rounding-level (1e-12 for single applications, 1e-9 where a Krylov solve to
+1e-14 or a fixed number of FGMRES steps sits inside)."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("DDAMG_ML_GPU") != "1", reason="three-level GPU path: first run pending")]
+
+from oracle.dirac import DiracOperator  # noqa: E402
+from oracle.mg import Params as OParams  # noqa: E402
+from oracle.multilevel import MultiLevel  # noqa: E402
+from paper_1303_1377_gb300 import synth  # noqa: E402
+
+DIMS, BLK, N0, BLK1, N1 = (8, 8, 8, 8), (2, 2, 2, 2), 4, (2, 2, 2, 2), 3
+M0, CSW = 0.05, 1.0
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_1303_1377_gb300 import ddamg
+
+    U = synth.gauge_field(DIMS, 0.5, seed=111)
+    D = DiracOperator(U, DIMS, M0, CSW)
+    v0 = synth.random_test_vectors(DIMS, N0, seed=112)
+    v1 = synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113)  # level-1 vectors, lexicographic coarse sites
+
+    def oracle(inner="fgmres", coarse_tol=1e-14, inner_tol=5e-2):
+        ml = MultiLevel(D, [OParams(N=N0, agg_block=BLK, sap_block=BLK, nu=2, coarse_tol=coarse_tol, coarse_maxiter=5000),
+                            OParams(N=N1, agg_block=BLK1, sap_block=BLK1, nu=2, coarse_tol=coarse_tol, coarse_maxiter=5000)],
+                        inner=inner, inner_tol=inner_tol)
+        ml.build([v0, v1])
+        return ml
+
+    def gpu(inner=0, coarse_tol=1e-14, inner_tol=5e-2):
+        p = ddamg.default_params(n_vec=N0, block=BLK, precision=ddamg.PREC_DOUBLE, nu=2, coarse_tol=coarse_tol)
+        s = ddamg.Solver(DIMS, U, M0, CSW, p, setup=False)
+        s.setup_from_vectors(v0)
+        s.ml_build(v1, ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2, inner=inner, coarse_tol=coarse_tol, inner_tol=inner_tol,
+                                               coarse_maxiter=5000))
+        return s
+
+    return dict(D=D, oracle=oracle, gpu=gpu, ddamg=ddamg)
+
+
+def test_level1_pieces(case):
+    """Level-1 restriction and prolongation, D_2, and level-1 SAP (nu = 2, MR(4))."""
+    ml = case["oracle"]()
+    l1 = ml.levels[1]
+    with case["gpu"]() as s:
+        x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=114)
+        assert rel(s.ml_restrict1(x), np.stack([l1.agg.restrict(x[r]) for r in range(2)])) < 1e-12
+        e = synth.gaussian_coarse(2 ** 4, 2 * N1, 2, seed=115)
+        assert rel(s.ml_prolong1(e), np.stack([l1.agg.prolong(e[r]) for r in range(2)])) < 1e-12
+        assert rel(s.ml_apply_D2(e), np.stack([l1.Dc.apply(e[r]) for r in range(2)])) < 1e-12
+        assert rel(s.ml_apply_sap1(x, 2), np.stack([l1.sap.apply(x[r], 2) for r in range(2)])) < 1e-12
+
+
+def test_level1_vcycle(case):
+    ml = case["oracle"]()
+    x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=116)
+    with case["gpu"]() as s:
+        assert rel(s.ml_vcycle1(x), np.stack([ml.levels[1].vcycle(x[r]) for r in range(2)])) < 1e-9
+
+
+@pytest.mark.parametrize("inner", ["fgmres", "vcycle"])
+def test_fine_vcycle_with_recursive_coarse_solve(case, inner):
+    """The fine V-cycle whose coarse solve is 3 FGMRES steps on D_1 with the level-1 V-cycle (or one
+    level-1 V-cycle)."""
+    ml = case["oracle"](inner=inner)
+    r = synth.gaussian_spinors(DIMS, 2, seed=117)
+    ref = np.stack([ml.levels[0].vcycle(r[q], coarse_fixed_iters=3) for q in range(2)])
+    with case["gpu"](inner=0 if inner == "fgmres" else 1) as s:
+        assert rel(s.ml_vcycle(r, 3), ref) < 1e-9
+
+
+def test_three_level_solve(case):
+    """Default inner solves (5e-2): true residual <= 1e-10 under the oracle's D, the oracle's solution
+    to 1e-8, and the counters show the recursion ran."""
+    D = case["D"]
+    b = synth.gaussian_spinors(DIMS, 2, seed=118)
+    ml = case["oracle"](coarse_tol=5e-2)
+    with case["gpu"](coarse_tol=5e-2) as s:
+        z, st, counts = s.ml_solve(b)
+    for q in range(2):
+        assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
+        zo, _ = ml.solve(b[q])
+        assert np.linalg.norm(z[q] - zo) <= 1e-8 * np.linalg.norm(zo)
+    assert counts["fgmres_steps_D1"] > 0 and counts["gmres_steps_D2"] > 0 and counts["vcycles1"] > 0
+
+
+def test_stale_third_level_and_precision_checks(case):
+    ddamg = case["ddamg"]
+    with case["gpu"]() as s:
+        s.set_mass(M0 + 0.01)
+        with pytest.raises(ddamg.DDAMGError) as e:
+            s.ml_vcycle1(synth.gaussian_coarse(4 ** 4, 2 * N0, 1, seed=119))
+        assert e.value.status == -7
+    p = ddamg.default_params(n_vec=N0, block=BLK, precision=ddamg.PREC_SINGLE, nu=2)
+    with ddamg.Solver(DIMS, synth.gauge_field(DIMS, 0.5, seed=111), M0, CSW, p, setup=False) as s:
+        s.setup_from_vectors(synth.random_test_vectors(DIMS, N0, seed=112))
+        with pytest.raises(ddamg.DDAMGError) as e:
+            s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1))
+        assert e.value.status == -1

@@ -325,6 +325,8 @@ typedef struct {
     double coarse_tol;  /* relative residual target of the odd-even GMRES on D_2 (5e-2) */
     int coarse_restart; /* its restart length (30) */
     int coarse_maxiter; /* cap on its iterations per solve (1000) */
+    int n_inv1;         /* rounds of the level-1 setup of ddamg_ml_setup (6) */
+    int setup_update1;  /* ddamg_setup_update of those rounds (DDAMG_SETUP_DDALPHA) */
 } ddamg_ml_params;
 void ddamg_ml_default_params(ddamg_ml_params* p);
 
@@ -334,6 +336,13 @@ void ddamg_ml_default_params(ddamg_ml_params* p);
  * parameter out of range; RANK: v1 linearly dependent on an aggregate or a singular diagonal block
  * of D_2 (the previous third level is then released). */
 int ddamg_ml_build(ddamg_handle* h, const ddamg_ml_params* p, const double* v1);
+/* Build level 2 by the adaptive setup on level 1 instead: Algorithm 1's first phase
+ * (v_j <- M_SAP^(eta) v_j, eta = 1, 2, 3, with the level-1 SAP) and n_inv1 rounds of Algorithm 2
+ * (or of Algorithm 1's update) with the level-1 V-cycle, all n_vec1 vectors as one batch, from the
+ * initial vectors v0 ([n_vec1][coarse sites lex][2N], e.g. random); P_1 and D_2 are rebuilt at the
+ * start of every round and after the last.  v_out (may be null) receives the final vectors.
+ * Errors as ddamg_ml_build. */
+int ddamg_ml_setup(ddamg_handle* h, const ddamg_ml_params* p, const double* v0, double* v_out);
 /* Release the third level (ddamg_destroy does it too). */
 int ddamg_ml_release(ddamg_handle* h);
 /* out = M_SAP^(nu) in on level 1 (red-black SAP of D_1 over the level-1 blocks, MR block solves). */

@@ -328,6 +328,47 @@ struct MLScatterB2 {
     }
 };
 
+// squared norm of each of the fields x[i] of length fs (one index per field)
+template <typename T>
+struct MLNorm2 {
+    const cplx<T>* x;
+    size_t fs;
+    T* out;
+    __host__ __device__ void operator()(long long i) const {
+        T acc = T(0);
+        for (size_t k = 0; k < fs; ++k) acc += norm2(x[(size_t)i * fs + k]);
+        out[i] = acc;
+    }
+};
+
+// x[r] /= sqrt(n2[r]) for every field r of length fs
+template <typename T>
+struct MLNormalize {
+    cplx<T>* x;
+    size_t fs;
+    const T* n2;
+    __host__ __device__ void operator()(long long i) const {
+        const T s = T(1) / sqrt(n2[(size_t)i / fs]);
+        x[i] = s * x[i];
+    }
+};
+
+// y = a + b (b may alias y)
+template <typename T>
+struct MLAdd {
+    const cplx<T>* a;
+    const cplx<T>* b;
+    cplx<T>* y;
+    __host__ __device__ void operator()(long long i) const { y[i] = a[i] + b[i]; }
+};
+
+template <typename T>
+struct MLCopy {
+    const cplx<T>* a;
+    cplx<T>* y;
+    __host__ __device__ void operator()(long long i) const { y[i] = a[i]; }
+};
+
 // ---------------------------------------------------------------------------
 // executors
 // ---------------------------------------------------------------------------
@@ -377,6 +418,54 @@ int ml_sap(const X& ex, const MLView<T>& v, const cplx<T>* b, cplx<T>* z, int nr
             if ((rc = ex.run(nf, MLAddColour<T>{v, w.x, z, col}))) return rc;
         }
     return 0;
+}
+
+// level-1 V-cycle (Sec. 4.2 on D_1): x = P_1 D_2^{-1} P_1^H r with the level-2 solve supplied by
+// coarse(eb, ex, nrhs), then nu SAP iterations on D_1 x = r from that x (which adds
+// M_SAP^(nu) (r - D_1 x), the SAP iteration being affine).  eb, ex: level-2 work vectors.
+template <class X, typename T, class Coarse>
+int ml_vcycle1_t(const X& ex, const MLView<T>& v, const cplx<T>* r, cplx<T>* x, int nrhs, int nu, int mr_steps, const MLSapWork<T>& w,
+                 cplx<T>* eb, cplx<T>* exx, Coarse&& coarse) {
+    int rc;
+    if ((rc = ex.run((long long)nrhs * v.NB2 * 2 * v.N1, MLRestrict<T>{v, r, eb}))) return rc;
+    if ((rc = coarse(eb, exx, nrhs))) return rc;
+    if ((rc = ex.run((long long)nrhs * v.NB * v.nc, MLProlong<T>{v, exx, x}))) return rc;
+    return ml_sap(ex, v, r, x, nrhs, nu, mr_steps, w);
+}
+
+// The setup of level 1 (Algorithm 1 phase 1, then n_inv rounds of Algorithm 2 -- or Algorithm 1's
+// update when idsetup -- on D_1), all N_1 vectors as one batch: P_1 and D_2 are frozen within a
+// round, so the updates are independent.  vec[N1][NB][nc] holds the initial vectors and returns
+// the final ones; rebuild(vec) forms P_1, D_2 and its inverses from vec (it is called at the start
+// of every round and once after the last); vcycle(r, x, nrhs) is the level-1 V-cycle; t, u are work
+// fields of N1 level-1 vectors, n2 a work array of N1 reals.
+template <class X, typename T, class Rebuild, class VCycle>
+int ml_setup1_t(const X& ex, const MLView<T>& v, cplx<T>* vec, int n_inv, bool idsetup, int mr_steps, const MLSapWork<T>& w, cplx<T>* t,
+                cplx<T>* u, T* n2, Rebuild&& rebuild, VCycle&& vcycle) {
+    const int N1 = v.N1;
+    const size_t fs = (size_t)v.NB * v.nc;
+    const long long nf = (long long)N1 * fs;
+    int rc;
+    // phase 1: v_j <- M_SAP^(eta) v_j for eta = 1, 2, 3 (SAP from zero, v_j the right-hand side)
+    for (int eta = 1; eta <= 3; ++eta) {
+        if ((rc = ex.run(nf, MLZero<T>{t}))) return rc;
+        if ((rc = ml_sap(ex, v, vec, t, N1, eta, mr_steps, w))) return rc;
+        if ((rc = ex.run(nf, MLCopy<T>{t, vec}))) return rc;
+    }
+    for (int it = 0; it < n_inv; ++it) {
+        if ((rc = rebuild(vec))) return rc;
+        if (idsetup) {
+            if ((rc = vcycle(vec, u, N1))) return rc;  // v <- C v
+            if ((rc = ex.run(nf, MLCopy<T>{u, vec}))) return rc;
+        } else {
+            if ((rc = ex.run(nf, MLFullApply<T>{v, vec, vec, t}))) return rc;  // t = v - D_1 v
+            if ((rc = vcycle(t, u, N1))) return rc;                             // u = C t
+            if ((rc = ex.run(nf, MLAdd<T>{vec, u, vec}))) return rc;           // v <- v + C (v - D_1 v)
+        }
+        if ((rc = ex.run(N1, MLNorm2<T>{vec, fs, n2}))) return rc;
+        if ((rc = ex.run(nf, MLNormalize<T>{vec, fs, n2}))) return rc;
+    }
+    return rebuild(vec);
 }
 
 // D_2 = P_1^H D_1 P_1 (Sec. 3.2): the block of direction 0 collects the self blocks and the

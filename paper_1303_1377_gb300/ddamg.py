@@ -102,6 +102,8 @@ class MLParams(C.Structure):
         ("coarse_tol", C.c_double),
         ("coarse_restart", C.c_int),
         ("coarse_maxiter", C.c_int),
+        ("n_inv1", C.c_int),
+        ("setup_update1", C.c_int),
     ]
 
 
@@ -153,6 +155,7 @@ def _load():
         "ddamg_slots_close": (I, [P]),
         "ddamg_ml_default_params": (None, [C.POINTER(MLParams)]),
         "ddamg_ml_build": (I, [P, C.POINTER(MLParams), P]),
+        "ddamg_ml_setup": (I, [P, C.POINTER(MLParams), P, P]),
         "ddamg_ml_release": (I, [P]),
         "ddamg_ml_apply_sap1": (I, [P, P, P, I, I]),
         "ddamg_ml_restrict1": (I, [P, P, P, I]),
@@ -311,6 +314,18 @@ class Solver:
         nb1 = [self.coarse_dims()[m] // self.ml_params.block1[m] for m in range(4)]
         self.n_level2 = int(np.prod(nb1))
         self.level2_dof = 2 * self.ml_params.n_vec1
+
+    def ml_setup(self, v0, params: MLParams | None = None):
+        """Level 2 by the adaptive setup on level 1 from the initial vectors v0[N1, coarse sites, 2N];
+        returns the final level-1 test vectors."""
+        self.ml_params = params if params is not None else ml_default_params()
+        v0 = _host(v0, np.complex128)
+        out = np.empty_like(v0) if not _is_torch(v0) else _empty_like(v0, tuple(v0.shape), np.complex128)
+        _check(lib.ddamg_ml_setup(self.h, C.byref(self.ml_params), _ptr(v0), _ptr(out)), "ddamg_ml_setup")
+        nb1 = [self.coarse_dims()[m] // self.ml_params.block1[m] for m in range(4)]
+        self.n_level2 = int(np.prod(nb1))
+        self.level2_dof = 2 * self.ml_params.n_vec1
+        return out
 
     def coarse_dims(self):
         return tuple(self.dims[m] // self.params.block[m] for m in range(4))

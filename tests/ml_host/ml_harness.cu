@@ -4,6 +4,7 @@
 // host-only shared library; the product never loads it.  Arrays are complex128 as (re, im) pairs in
 // the internal orders described in ml_ops.cuh; B1/Dinv1/B2 column-major.
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "ml_geom.h"
@@ -110,6 +111,124 @@ int mlh_galerkin(const int* L1, const int* b1, int nc, int N1, const double* B1,
     const int nc2 = 2 * N1;
     std::vector<C> E((size_t)nc2 * L.g.NB2 * nc2), e(E.size()), W((size_t)nc2 * L.g.NB * nc), Y(W.size());
     return ml_galerkin(MLHostExec{}, L.v, reinterpret_cast<C*>(B2), E.data(), W.data(), Y.data(), e.data());
+}
+
+// ---- the level-1 V-cycle and setup with an exact level-2 solve (dense inverse of D_2) ----
+
+namespace {
+// inverse of a dense n x n complex matrix (row-major) by Gauss-Jordan with partial pivoting
+bool dense_inverse(std::vector<C>& A, int n) {
+    std::vector<C> I((size_t)n * n, czero<double>());
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = mk(1.0, 0.0);
+    for (int p = 0; p < n; ++p) {
+        int piv = p;
+        for (int i = p + 1; i < n; ++i)
+            if (norm2(A[(size_t)i * n + p]) > norm2(A[(size_t)piv * n + p])) piv = i;
+        if (norm2(A[(size_t)piv * n + p]) == 0.0) return false;
+        for (int j = 0; j < n; ++j) {
+            std::swap(A[(size_t)p * n + j], A[(size_t)piv * n + j]);
+            std::swap(I[(size_t)p * n + j], I[(size_t)piv * n + j]);
+        }
+        const C d = A[(size_t)p * n + p];
+        const double dn = norm2(d);
+        const C dinv = mk(d.re / dn, -d.im / dn);
+        for (int j = 0; j < n; ++j) {
+            A[(size_t)p * n + j] = dinv * A[(size_t)p * n + j];
+            I[(size_t)p * n + j] = dinv * I[(size_t)p * n + j];
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i == p) continue;
+            const C f = A[(size_t)i * n + p];
+            for (int j = 0; j < n; ++j) {
+                A[(size_t)i * n + j] = A[(size_t)i * n + j] - f * A[(size_t)p * n + j];
+                I[(size_t)i * n + j] = I[(size_t)i * n + j] - f * I[(size_t)p * n + j];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+// the dense matrix of D_2 (internal level-2 order, row-major) from its nine-block stencil
+std::vector<C> dense_D2(const MLHostGeom& g, const C* B2, int nc2) {
+    const int n = g.NB2 * nc2;
+    std::vector<C> M((size_t)n * n, czero<double>());
+    for (int c2 = 0; c2 < g.NB2; ++c2)
+        for (int d = 0; d < 9; ++d) {
+            const int nb = d == 0 ? c2 : g.nbr2[(size_t)(d - 1) * g.NB2 + c2];
+            for (int col = 0; col < nc2; ++col)
+                for (int row = 0; row < nc2; ++row) {
+                    C& m = M[(size_t)(c2 * nc2 + row) * n + nb * nc2 + col];
+                    m = m + B2[(((size_t)c2 * 9 + d) * nc2 + col) * nc2 + row];
+                }
+        }
+    return M;
+}
+
+struct DenseCoarse {
+    const std::vector<C>* inv;
+    int n;
+    int operator()(const C* eb, C* ex, int nrhs) const {
+        for (int r = 0; r < nrhs; ++r)
+            for (int i = 0; i < n; ++i) {
+                C acc = czero<double>();
+                for (int j = 0; j < n; ++j) cmac(acc, (*inv)[(size_t)i * n + j], eb[(size_t)r * n + j]);
+                ex[(size_t)r * n + i] = acc;
+            }
+        return 0;
+    }
+};
+
+struct SapBufs {
+    std::vector<C> r, te, rho, u, w, s, x, alpha;
+    SapBufs(size_t nf, size_t na) : r(nf), te(nf), rho(nf), u(nf), w(nf), s(nf), x(nf), alpha(na) {}
+    MLSapWork<double> work() { return {r.data(), te.data(), rho.data(), u.data(), w.data(), s.data(), x.data(), alpha.data()}; }
+};
+}  // namespace
+
+// x = the level-1 V-cycle of r with D_2 solved exactly (D2inv: dense inverse, internal order)
+int mlh_vcycle1(const int* L1, const int* b1, int nc, int N1, const double* B1, const double* Dinv1, const double* P1, const double* D2inv,
+                const double* r, double* x, int nrhs, int nu, int mr_steps) {
+    HostLevel L(L1, b1, nc, N1, B1, Dinv1, P1);
+    if (L.ok) return -1;
+    const int n2 = L.g.NB2 * 2 * N1;
+    std::vector<C> inv(reinterpret_cast<const C*>(D2inv), reinterpret_cast<const C*>(D2inv) + (size_t)n2 * n2);
+    SapBufs sb((size_t)nrhs * L.g.NB * nc, (size_t)nrhs * L.g.NB2);
+    std::vector<C> eb((size_t)nrhs * n2), ex((size_t)nrhs * n2);
+    return ml_vcycle1_t(MLHostExec{}, L.v, reinterpret_cast<const C*>(r), reinterpret_cast<C*>(x), nrhs, nu, mr_steps, sb.work(), eb.data(),
+                        ex.data(), DenseCoarse{&inv, n2});
+}
+
+// the level-1 setup from the initial vectors vec (returned updated), with exact level-2 solves;
+// P1 and B2 receive the final interpolation and D_2
+int mlh_setup1(const int* L1, const int* b1, int nc, int N1, const double* B1, const double* Dinv1, double* vec, int n_inv, int idsetup,
+               int nu, int mr_steps, double* P1, double* B2) {
+    HostLevel L(L1, b1, nc, N1, B1, Dinv1, P1);
+    if (L.ok) return -1;
+    const int nc2 = 2 * N1, n2 = L.g.NB2 * nc2;
+    const size_t fs = (size_t)L.g.NB * nc;
+    SapBufs sb((size_t)N1 * fs, (size_t)N1 * L.g.NB2);
+    std::vector<C> t((size_t)N1 * fs), u((size_t)N1 * fs), E((size_t)nc2 * L.g.NB2 * nc2), e(E.size()), W((size_t)nc2 * fs), Y(W.size());
+    std::vector<C> inv;
+    std::vector<double> nrm(N1);
+    C* Pm = reinterpret_cast<C*>(P1);
+    C* Bm = reinterpret_cast<C*>(B2);
+    const MLView<double> v = L.v;
+    auto rebuild = [&](const C* vv) -> int {
+        int fail = 0;
+        MLHostExec{}.run((long long)L.g.NB2 * 2, MLGramSchmidt<double>{v, vv, Pm, &fail});
+        if (fail) return -8;
+        if (ml_galerkin(MLHostExec{}, v, Bm, E.data(), W.data(), Y.data(), e.data())) return -1;
+        inv = dense_D2(L.g, Bm, nc2);
+        return dense_inverse(inv, n2) ? 0 : -8;
+    };
+    std::vector<C> eb((size_t)N1 * n2), ex((size_t)N1 * n2);
+    SapBufs sv((size_t)N1 * fs, (size_t)N1 * L.g.NB2);
+    auto vcycle = [&](const C* r, C* x, int nr) -> int {
+        return ml_vcycle1_t(MLHostExec{}, v, r, x, nr, nu, mr_steps, sv.work(), eb.data(), ex.data(), DenseCoarse{&inv, n2});
+    };
+    return ml_setup1_t(MLHostExec{}, v, reinterpret_cast<C*>(vec), n_inv, idsetup != 0, mr_steps, sb.work(), t.data(), u.data(), nrm.data(),
+                       rebuild, vcycle);
 }
 
 }  // extern "C"

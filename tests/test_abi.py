@@ -112,6 +112,8 @@ def test_third_level_defaults_and_argument_checks(libpath):
     p = ddamg.ml_default_params()
     assert (tuple(p.block1), p.n_vec1, p.nu1, p.mr_steps1, p.inner, p.inner_kv, p.inner_tol, p.coarse_tol, p.coarse_restart) == (
         (2, 2, 2, 2), 20, 2, 4, 0, 10, 5e-2, 5e-2, 30)
+    assert (p.n_inv1, p.setup_update1) == (6, ddamg.SETUP_DDALPHA)
     assert ddamg.lib.ddamg_ml_build(None, ctypes.byref(p), None) == -1
     assert ddamg.lib.ddamg_ml_solve(None, None, None, 1, 1e-10, None) == -1
     assert ddamg.lib.ddamg_ml_release(None) == -1
+    assert ddamg.lib.ddamg_ml_setup(None, ctypes.byref(p), None, None) == -1

@@ -46,15 +46,19 @@ def case():
         ml.build([v0, v1])
         return ml
 
-    def gpu(inner=0, coarse_tol=1e-14, inner_tol=5e-2):
+    def handle(coarse_tol=1e-14):
         p = ddamg.default_params(n_vec=N0, block=BLK, precision=ddamg.PREC_DOUBLE, nu=2, coarse_tol=coarse_tol)
         s = ddamg.Solver(DIMS, U, M0, CSW, p, setup=False)
         s.setup_from_vectors(v0)
+        return s
+
+    def gpu(inner=0, coarse_tol=1e-14, inner_tol=5e-2):
+        s = handle(coarse_tol)
         s.ml_build(v1, ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2, inner=inner, coarse_tol=coarse_tol, inner_tol=inner_tol,
                                                coarse_maxiter=5000))
         return s
 
-    return dict(D=D, oracle=oracle, gpu=gpu, ddamg=ddamg)
+    return dict(D=D, oracle=oracle, gpu=gpu, handle=handle, ddamg=ddamg)
 
 
 def test_level1_pieces(case):
@@ -116,3 +120,23 @@ def test_stale_third_level_and_precision_checks(case):
         with pytest.raises(ddamg.DDAMGError) as e:
             s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1))
         assert e.value.status == -1
+
+
+@pytest.mark.parametrize("update", ["ddalpha", "idsetup"])
+def test_level1_setup(case, update):
+    """ddamg_ml_setup: Algorithm 1 phase 1 and one round of Algorithm 2 (or Algorithm 1's update) on D_1
+    with exact level-2 solves on both sides: the final level-1 vectors and D_2 equal the oracle's."""
+    from oracle.multilevel import StencilTwoLevel
+
+    ddamg = case["ddamg"]
+    A1 = case["oracle"]().levels[1].D
+    v10 = synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=120)
+    tl = StencilTwoLevel(A1, OParams(N=N1, agg_block=BLK1, sap_block=BLK1, nu=2, n_inv=1, coarse_tol=1e-14, coarse_maxiter=5000,
+                                     setup_update=update))
+    ref = tl.setup(v10)
+    with case["handle"]() as s:
+        out = s.ml_setup(v10, ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2, coarse_tol=1e-14, coarse_maxiter=5000, n_inv1=1,
+                                                      setup_update1=ddamg.SETUP_IDSETUP if update == "idsetup" else ddamg.SETUP_DDALPHA))
+        assert rel(out, ref) < 1e-9
+        e = synth.gaussian_coarse(2 ** 4, 2 * N1, 2, seed=121)
+        assert rel(s.ml_apply_D2(e), np.stack([tl.Dc.apply(e[r]) for r in range(2)])) < 1e-9

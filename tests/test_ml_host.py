@@ -197,3 +197,51 @@ def test_invalid_level1_blockings_are_refused(lib):
                    ((4, 4, 4, 4), (3, 2, 2, 2)),   # does not divide
                    ((2, 2, 2, 2), (1, 1, 1, 1))):  # every block extent odd
         assert lib.mlh_geom_sizes(ip(np.array(L1)), ip(np.array(b1)), ip(sz)) == -1
+
+
+def _level1_oracle(lv, vec=None, **kw):
+    from oracle.mg import Params
+    from oracle.multilevel import StencilTwoLevel
+
+    p = Params(N=lv.N1, agg_block=tuple(lv.b1), sap_block=tuple(lv.b1), nu=2, coarse_tol=1e-14, coarse_maxiter=5000, **kw)
+    return StencilTwoLevel(lv.A, p, vectors=vec)
+
+
+def _dense_inverse_internal(lv, Dc):
+    """Inverse of the oracle's D_2 as a dense matrix in the harness's internal level-2 order."""
+    nc2 = 2 * lv.N1
+    perm = (lv.g["lex2"][:, None] * nc2 + np.arange(nc2)[None, :]).ravel()
+    return np.ascontiguousarray(np.linalg.inv(Dc.dense())[np.ix_(perm, perm)])
+
+
+def test_level1_vcycle_matches_the_oracle(lv):
+    """x = P_1 D_2^{-1} P_1^H r, then two SAP iterations on D_1 x = r (exact level-2 solve on both sides)."""
+    vec = synth.gaussian_coarse(lv.NB, lv.nc, lv.N1, seed=101)
+    P = np.zeros((lv.NB2, 2, lv.Vb1 * lv.nc // 2, lv.N1), dtype=np.complex128)
+    assert lv.lib.mlh_gram_schmidt(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.to_int(vec)), dp(P)) == 0
+    tl = _level1_oracle(lv, vec)
+    inv = _dense_inverse_internal(lv, tl.Dc)
+    r = synth.gaussian_coarse(lv.NB, lv.nc, 2, seed=102)
+    x = np.zeros_like(r)
+    assert lv.lib.mlh_vcycle1(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.B1), dp(lv.Dinv1), dp(P), dp(inv), dp(lv.to_int(r)), dp(x), 2, 2,
+                              4) == 0
+    ref = np.stack([tl.vcycle(r[q]) for q in range(2)])
+    assert np.max(np.abs(lv.to_lex(x) - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("update", ["ddalpha", "idsetup"])
+def test_level1_setup_matches_the_oracle(lv, update):
+    """Algorithm 1 phase 1 and one round of Algorithm 2 (or of Algorithm 1's update) on D_1, all level-1
+    vectors as one batch, then the final rebuild: the vectors and D_2 equal the oracle's."""
+    vec0 = synth.gaussian_coarse(lv.NB, lv.nc, lv.N1, seed=103)
+    tl = _level1_oracle(lv, n_inv=1, setup_update=update)
+    ref = tl.setup(vec0)
+    vec = lv.to_int(vec0)
+    nc2 = 2 * lv.N1
+    P = np.zeros((lv.NB2, 2, lv.Vb1 * lv.nc // 2, lv.N1), dtype=np.complex128)
+    B2 = np.zeros((lv.NB2, 9, nc2, nc2), dtype=np.complex128)
+    assert lv.lib.mlh_setup1(ip(lv.L1), ip(lv.b1), lv.nc, lv.N1, dp(lv.B1), dp(lv.Dinv1), dp(vec), 1, int(update == "idsetup"), 2, 4, dp(P),
+                             dp(B2)) == 0
+    assert np.max(np.abs(lv.to_lex(vec) - ref)) < 1e-9 * np.max(np.abs(ref))
+    Bref = tl.Dc.B[lv.g["lex2"]].transpose(0, 1, 3, 2)
+    assert np.max(np.abs(B2 - Bref)) < 1e-9 * np.max(np.abs(Bref))

@@ -306,7 +306,9 @@ void ddamg_debug_fail_allocs(int n);
  *   the level-1 V-cycle is x = P_1 D_2^{-1} P_1^H r followed by nu1 SAP iterations on D_1 x = r;
  *   the fine V-cycle's coarse solve becomes FGMRES(inner_kv) on D_1 to inner_tol preconditioned by
  *   the level-1 V-cycle (inner = 0), or one level-1 V-cycle (inner = 1).
- * DOUBLE-precision handles only.  The third level is tied to the coarse operator it was built
+ * P_1, D_2 and its inverses are built in FP64; the level-1 and level-2 solves run in the handle's
+ * V-cycle precision (FP64 on DOUBLE handles, FP32 on SINGLE and HALF handles, with FP32 copies of
+ * D_1, P_1, D_2 and the inverses).  The third level is tied to the coarse operator it was built
  * from: after ddamg_run_setup, ddamg_setup_from_vectors or ddamg_set_mass the calls below return
  * DDAMG_ERR_NOT_READY until ddamg_ml_build runs again.
  * Level-1 vectors use the coarse layout of ddamg_restrict ([n_rhs][coarse sites lex][2N]);
@@ -331,7 +333,7 @@ typedef struct {
 void ddamg_ml_default_params(ddamg_ml_params* p);
 
 /* Build level 2 from the level-1 test vectors v1 ([n_vec1][coarse sites lex][2N]): P_1, D_2 and the
- * inverses of D_2's even diagonal blocks.  INVALID_ARG: not DOUBLE precision, block1 not dividing
+ * inverses of D_2's even diagonal blocks.  INVALID_ARG: block1 not dividing
  * the coarse lattice into an even number of blocks per direction (with one even extent), or a
  * parameter out of range; RANK: v1 linearly dependent on an aggregate or a singular diagonal block
  * of D_2 (the previous third level is then released). */
@@ -357,9 +359,9 @@ int ddamg_ml_vcycle1(ddamg_handle* h, const double* in, double* out, int n_rhs);
 /* out = the fine V-cycle with the recursive coarse solve applied to in (fine spinors);
  * inner_fixed_iters > 0 runs exactly that many FGMRES steps on D_1 instead of stopping at inner_tol. */
 int ddamg_ml_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, int inner_fixed_iters);
-/* Three-level solve: FGMRES(n_kv) on D preconditioned by ddamg_ml_vcycle, from z = 0, to the
- * relative residual tol; status and stats as ddamg_solve_batch (coarse_iterations = FGMRES steps
- * on D_1). */
+/* Three-level solve: ddamg_solve_batch (same outer scheme, initial guess z, tol, status and
+ * stats) with the fine V-cycle's coarse solve replaced by the recursion (coarse_iterations =
+ * FGMRES steps on D_1). */
 int ddamg_ml_solve(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st);
 /* Counters of the last ddamg_ml_solve: out[0] FGMRES steps on D_1, out[1] GMRES steps on D_2,
  * out[2] level-1 V-cycles (per right-hand side). */

@@ -243,6 +243,7 @@ struct ddamg_handle {
     // recursion to a third level (ddamg_ml_build); coarse_gen counts rebuilds and shifts of D_c
     ddamg::MLState* ml = nullptr;
     unsigned long long coarse_gen = 0;
+    bool ml_route = false;  // set by ddamg_ml_solve: the fine V-cycle takes the recursive coarse solve
 
     bool single() const { return p.precision != DDAMG_PREC_DOUBLE; }
     bool half() const { return p.precision == DDAMG_PREC_HALF; }
@@ -1189,6 +1190,9 @@ static int run_setup(ddamg_handle* h, const double* v0) {
 // ---------------------------------------------------------------------------
 // TV = basis type: double-word FP32 pairs when the V-cycle is FP32 (GB300's FP64
 // rate is a small fraction of its FP32 rate), FP64 for the all-FP64 path.
+template <typename T>
+static int ml_vcycle0(ddamg_handle* h, const cplx<T>* r, cplx<T>* x, int nrhs, int inner_fixed);  // multilevel.inc
+
 template <typename TZ, typename TV>
 static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R,
                    const int* enabled_host = nullptr, int max_cycles = 0) {
@@ -1243,7 +1247,7 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
             DD_TRY((convert<TZ, double>(reinterpret_cast<const double*>(v), reinterpret_cast<TZ*>(rT), 2 * fld * nrhs, st)));
             r = rT;
         }
-        return vcycle<TZ>(h, r, z, nrhs, 0);
+        return h->ml_route ? ml_vcycle0<TZ>(h, r, z, nrhs, 0) : vcycle<TZ>(h, r, z, nrhs, 0);
     };
     P.b = b;
     P.x = x;

@@ -359,10 +359,12 @@ class Solver:
         return self._ml_op(lib.ddamg_ml_vcycle, r, (self.V, 4, 3), int(inner_fixed_iters))
 
     def ml_solve(self, b, tol: float = 1e-10, allow_fail: bool = False):
-        """Three-level solve of D z = b for b[n_rhs, V, 4, 3] from z = 0."""
+        """Three-level solve of D z = b for b[n_rhs, V, 4, 3] from z = 0 (the outer scheme of the
+        handle's precision, as solve)."""
         b = _host(b, np.complex128)
         nr = int(b.shape[0])
         z = _empty_like(b, b.shape, np.complex128)
+        z[...] = 0
         st = (Stats * nr)()
         rc = lib.ddamg_ml_solve(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
         _check(rc, "ddamg_ml_solve", allow=(-4, -5) if allow_fail else ())

@@ -78,6 +78,45 @@ int mlh_sap(const int* L1, const int* b1, int nc, const double* B1, const double
     return ml_sap(MLHostExec{}, L.v, reinterpret_cast<const C*>(b), reinterpret_cast<C*>(z), nrhs, nu, mr_steps, wk);
 }
 
+// the same SAP in FP32 (the precision of the solves on SINGLE and HALF handles): inputs and the
+// result are complex128, rounded to complex64 on entry
+int mlh_sap_f32(const int* L1, const int* b1, int nc, const double* B1, const double* Dinv1, const double* b, double* z, int nrhs,
+                int nu, int mr_steps) {
+    MLHostGeom g;
+    if (ml_build_geom(L1, b1, g)) return -1;
+    auto to_f = [](const double* p, size_t n) {
+        std::vector<cplx<float>> out(n);
+        for (size_t i = 0; i < n; ++i) out[i] = mk((float)p[2 * i], (float)p[2 * i + 1]);
+        return out;
+    };
+    const size_t nf = (size_t)nrhs * g.NB * nc;
+    std::vector<cplx<float>> Bf = to_f(B1, (size_t)g.NB * 9 * nc * nc), Df = to_f(Dinv1, (size_t)(g.NB / 2) * nc * nc), bf = to_f(b, nf),
+                             zf = to_f(z, nf);
+    MLView<float> v{};
+    v.NB = g.NB;
+    v.nc = nc;
+    v.half = nc / 2;
+    v.NB2 = g.NB2;
+    v.Vb1 = g.Vb1;
+    v.Vb1e = g.Vb1e;
+    v.N1 = 1;
+    v.nbr1 = g.nbr1.data();
+    v.sites = g.sites.data();
+    v.blk_of = g.blk_of.data();
+    v.loc_of = g.loc_of.data();
+    v.same = g.same.data();
+    v.B1 = Bf.data();
+    v.Dinv1 = Df.data();
+    std::vector<cplx<float>> r(nf), te(nf), rho(nf), u(nf), w(nf), s(nf), x(nf), alpha((size_t)nrhs * g.NB2);
+    MLSapWork<float> wk{r.data(), te.data(), rho.data(), u.data(), w.data(), s.data(), x.data(), alpha.data()};
+    const int rc = ml_sap(MLHostExec{}, v, bf.data(), zf.data(), nrhs, nu, mr_steps, wk);
+    for (size_t i = 0; i < nf; ++i) {
+        z[2 * i] = zf[i].re;
+        z[2 * i + 1] = zf[i].im;
+    }
+    return rc;
+}
+
 int mlh_gram_schmidt(const int* L1, const int* b1, int nc, int N1, const double* vec, double* P1) {
     HostLevel L(L1, b1, nc, N1, nullptr, nullptr, nullptr);
     if (L.ok) return -1;

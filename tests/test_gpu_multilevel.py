@@ -140,3 +140,23 @@ def test_level1_setup(case, update):
         assert rel(out, ref) < 1e-9
         e = synth.gaussian_coarse(2 ** 4, 2 * N1, 2, seed=121)
         assert rel(s.ml_apply_D2(e), np.stack([tl.Dc.apply(e[r]) for r in range(2)])) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["SINGLE", "HALF"])
+def test_three_level_solve_mixed_precision(case, prec):
+    """SINGLE and HALF handles: level-1 and level-2 solves in FP32 inside the handle's outer scheme;
+    the true FP64 residual still reaches 1e-10 and the recursion runs."""
+    ddamg, D = case["ddamg"], case["D"]
+    U = synth.gauge_field(DIMS, 0.5, seed=111)
+    p = ddamg.default_params(n_vec=N0, block=BLK, precision=getattr(ddamg, "PREC_" + prec), nu=2)
+    b = synth.gaussian_spinors(DIMS, 2, seed=122)
+    with ddamg.Solver(DIMS, U, M0, CSW, p, setup=False) as s:
+        s.setup_from_vectors(synth.random_test_vectors(DIMS, N0, seed=112))
+        s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2))
+        x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=123)
+        ref = case["oracle"]().levels[1].sap
+        assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < 2e-5
+        z, st, counts = s.ml_solve(b)
+    for q in range(2):
+        assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
+    assert counts["fgmres_steps_D1"] > 0 and counts["gmres_steps_D2"] > 0

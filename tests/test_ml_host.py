@@ -245,3 +245,15 @@ def test_level1_setup_matches_the_oracle(lv, update):
     assert np.max(np.abs(lv.to_lex(vec) - ref)) < 1e-9 * np.max(np.abs(ref))
     Bref = tl.Dc.B[lv.g["lex2"]].transpose(0, 1, 3, 2)
     assert np.max(np.abs(B2 - Bref)) < 1e-9 * np.max(np.abs(Bref))
+
+
+def test_sap_in_fp32_stays_at_single_precision(lv):
+    """The FP32 instantiation (SINGLE and HALF handles): two SAP iterations agree with the FP64
+    oracle to the FP32 level of iterated MR steps (2e-5 relative to the field maximum)."""
+    b = synth.gaussian_coarse(lv.NB, lv.nc, 2, seed=104)
+    sap = StencilSAP(lv.A, tuple(lv.b1), mr_steps=4)
+    ref = np.stack([sap.apply(b[r], 2) for r in range(2)])
+    z = np.zeros((2, lv.NB, lv.nc), dtype=np.complex128)
+    assert lv.lib.mlh_sap_f32(ip(lv.L1), ip(lv.b1), lv.nc, dp(lv.B1), dp(lv.Dinv1), dp(lv.to_int(b)), dp(z), 2, 2, 4) == 0
+    err = np.max(np.abs(lv.to_lex(z) - ref)) / np.max(np.abs(ref))
+    assert 1e-9 < err < 2e-5  # FP32 rounding is visible, and small

@@ -235,6 +235,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain single-RHS FP64 comparison solve")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
+    ap.add_argument("--levels", type=int, default=2, choices=[2, 3],
+                    help="3: the recursion to a third level (level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -265,6 +267,9 @@ def main():
                                   outer=ddamg.OUTER_REFINE if args.outer == "refine" else ddamg.OUTER_DW, cycle_tol=args.cycle_tol)
     t = time.perf_counter()
     solver = ddamg.Solver(dims, U, m0, C_SW, params, setup=True)
+    if args.levels == 3:
+        n1 = ddamg.ml_default_params().n_vec1
+        solver.ml_setup(synth.gaussian_coarse(solver.n_coarse, solver.coarse_dof, n1, seed=w["seed"] + 11))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t
     del U
@@ -275,10 +280,12 @@ def main():
     b = torch.from_numpy(bh).to("cuda")
     z = torch.zeros_like(b)
 
+    solve_fn = solver.ml_solve if args.levels == 3 else solver.solve
+
     def step():
         with torch.cuda.stream(stream):
             z.zero_()
-        zz, st, rc = solver.solve(b, z)
+        zz, st, rc = solve_fn(b, z)
         if rc != 0:
             raise RuntimeError(f"solve status {rc}")
         return st
@@ -326,12 +333,12 @@ def main():
         bhost = torch.from_numpy(bh).pin_memory()
         zhost = torch.zeros_like(bhost).pin_memory()
         solver.set_stream(None)
-        solver.solve(bhost.numpy(), zhost.numpy())
+        solve_fn(bhost.numpy(), zhost.numpy())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             zhost.zero_()
-            solver.solve(bhost.numpy(), zhost.numpy())
+            solve_fn(bhost.numpy(), zhost.numpy())
         e2e_s = time.perf_counter() - t0
         nbytes = bh.nbytes
         e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
@@ -370,7 +377,7 @@ def main():
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": workload_description(args.workload, w, m0),
-                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision,
+                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision, "levels": args.levels,
                    "outer": (f"FP32 FGMRES cycles to {args.cycle_tol:g} + FP64 residual correction" if args.outer == "refine"
                              and args.precision != "double" else "double-word FGMRES" if args.precision != "double" else "FP64 FGMRES")},
         "roofline": roof,

@@ -358,19 +358,24 @@ class Solver:
     def ml_vcycle(self, r, inner_fixed_iters: int = 0):
         return self._ml_op(lib.ddamg_ml_vcycle, r, (self.V, 4, 3), int(inner_fixed_iters))
 
-    def ml_solve(self, b, tol: float = 1e-10, allow_fail: bool = False):
-        """Three-level solve of D z = b for b[n_rhs, V, 4, 3] from z = 0 (the outer scheme of the
-        handle's precision, as solve)."""
+    def ml_solve(self, b, z=None, tol: float = 0.0, allow_fail: bool = False):
+        """Three-level solve of D z = b for b[n_rhs, V, 4, 3] (the outer scheme of the handle's
+        precision, as solve; z is the initial guess, zero when not given)."""
         b = _host(b, np.complex128)
         nr = int(b.shape[0])
-        z = _empty_like(b, b.shape, np.complex128)
-        z[...] = 0
+        if z is None:
+            z = _empty_like(b, b.shape, np.complex128)
+            z[...] = 0
         st = (Stats * nr)()
         rc = lib.ddamg_ml_solve(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
         _check(rc, "ddamg_ml_solve", allow=(-4, -5) if allow_fail else ())
+        return z, [s.as_dict() for s in st], rc
+
+    def ml_counts(self):
+        """Counters of the last ml_solve."""
         cnt = (C.c_longlong * 3)()
-        lib.ddamg_ml_counts(self.h, cnt)
-        return z, [s.as_dict() for s in st], {"fgmres_steps_D1": cnt[0], "gmres_steps_D2": cnt[1], "vcycles1": cnt[2]}
+        _check(lib.ddamg_ml_counts(self.h, cnt), "ddamg_ml_counts")
+        return {"fgmres_steps_D1": cnt[0], "gmres_steps_D2": cnt[1], "vcycles1": cnt[2]}
 
     # -- continuous batching ------------------------------------------------------
     def slots_open(self, n_slots: int):

@@ -99,7 +99,9 @@ def test_three_level_solve(case):
     b = synth.gaussian_spinors(DIMS, 2, seed=118)
     ml = case["oracle"](coarse_tol=5e-2)
     with case["gpu"](coarse_tol=5e-2) as s:
-        z, st, counts = s.ml_solve(b)
+        z, st, rc = s.ml_solve(b)
+        counts = s.ml_counts()
+    assert rc == 0
     for q in range(2):
         assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
         zo, _ = ml.solve(b[q])
@@ -156,7 +158,9 @@ def test_three_level_solve_mixed_precision(case, prec):
         x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=123)
         ref = case["oracle"]().levels[1].sap
         assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < 2e-5
-        z, st, counts = s.ml_solve(b)
+        z, st, rc = s.ml_solve(b)
+        counts = s.ml_counts()
+    assert rc == 0
     for q in range(2):
         assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
     assert counts["fgmres_steps_D1"] > 0 and counts["gmres_steps_D2"] > 0

@@ -68,28 +68,52 @@ __host__ __device__ inline bool ml_selected(const MLView<T>& v, int c, int parit
     return true;
 }
 
-// y = b - D_1 x (b may be null: y = D_1 x), every site
+// right-hand sides are processed in chunks of ML_RC per thread, so that each matrix entry is read
+// once per chunk (the operator, not the vectors, dominates the traffic)
+constexpr int ML_RC = 8;
+
+// acc[k] += row `row` of the column-major block times the site vector of right-hand side r0 + k
+template <typename T>
+__host__ __device__ inline void ml_rowdot_rhs(cplx<T> (&acc)[ML_RC], const cplx<T>* blk, int nc, int row, const cplx<T>* x0, size_t fs,
+                                              int nk) {
+    for (int col = 0; col < nc; ++col) {
+        const cplx<T> b = blk[(size_t)col * nc + row];
+        for (int k = 0; k < nk; ++k) cmac(acc[k], b, x0[(size_t)k * fs + col]);
+    }
+}
+
+// y = b - D_1 x (b may be null: y = D_1 x), every site; one index per (site, row)
 template <typename T>
 struct MLFullApply {
     MLView<T> v;
     const cplx<T>* x;
     const cplx<T>* b;
     cplx<T>* y;
+    int nrhs;
     __host__ __device__ void operator()(long long i) const {
         const size_t fs = (size_t)v.NB * v.nc;
-        const int r = (int)(i / fs), c = (int)((i / v.nc) % v.NB), row = (int)(i % v.nc);
-        const cplx<T>* xr = x + r * fs;
-        cplx<T> acc = ml_rowdot(ml_block(v, c, 0), v.nc, row, xr + (size_t)c * v.nc);
-        for (int d = 0; d < 8; ++d) {
-            const int n = v.nbr1[(size_t)d * v.NB + c];
-            acc = acc + ml_rowdot(ml_block(v, c, 1 + d), v.nc, row, xr + (size_t)n * v.nc);
+        const int c = (int)(i / v.nc), row = (int)(i % v.nc);
+        for (int r0 = 0; r0 < nrhs; r0 += ML_RC) {
+            const int nk = nrhs - r0 < ML_RC ? nrhs - r0 : ML_RC;
+            cplx<T> acc[ML_RC];
+            for (int k = 0; k < ML_RC; ++k) acc[k] = czero<T>();
+            const cplx<T>* xr = x + (size_t)r0 * fs;
+            ml_rowdot_rhs(acc, ml_block(v, c, 0), v.nc, row, xr + (size_t)c * v.nc, fs, nk);
+            for (int d = 0; d < 8; ++d) {
+                const int n = v.nbr1[(size_t)d * v.NB + c];
+                ml_rowdot_rhs(acc, ml_block(v, c, 1 + d), v.nc, row, xr + (size_t)n * v.nc, fs, nk);
+            }
+            for (int k = 0; k < nk; ++k) {
+                const size_t o = (size_t)(r0 + k) * fs + i;
+                y[o] = b ? b[o] - acc[k] : acc[k];
+            }
         }
-        y[i] = b ? b[i] - acc : acc;
     }
 };
 
 // on the selected sites: dst = add + B_self self_src + sign * (in-block hops of hop_src);
 // elsewhere dst = 0 (zero_others) or unchanged.  Any of add, self_src, hop_src may be null.
+// One index per (site, row).
 template <typename T>
 struct MLHopsCombine {
     MLView<T> v;
@@ -100,29 +124,38 @@ struct MLHopsCombine {
     T sign;
     int parity_sel, colour;
     bool zero_others;
+    int nrhs;
     __host__ __device__ void operator()(long long i) const {
         const size_t fs = (size_t)v.NB * v.nc;
-        const int r = (int)(i / fs), c = (int)((i / v.nc) % v.NB), row = (int)(i % v.nc);
+        const int c = (int)(i / v.nc), row = (int)(i % v.nc);
         if (!ml_selected(v, c, parity_sel, colour)) {
-            if (zero_others) dst[i] = czero<T>();
+            if (zero_others)
+                for (int r = 0; r < nrhs; ++r) dst[(size_t)r * fs + i] = czero<T>();
             return;
         }
-        cplx<T> acc = add ? add[i] : czero<T>();
-        if (self_src) acc = acc + ml_rowdot(ml_block(v, c, 0), v.nc, row, self_src + r * fs + (size_t)c * v.nc);
-        if (hop_src) {
-            cplx<T> h = czero<T>();
-            for (int d = 0; d < 8; ++d) {
-                if (!v.same[(size_t)d * v.NB + c]) continue;
-                const int n = v.nbr1[(size_t)d * v.NB + c];
-                h = h + ml_rowdot(ml_block(v, c, 1 + d), v.nc, row, hop_src + r * fs + (size_t)n * v.nc);
+        for (int r0 = 0; r0 < nrhs; r0 += ML_RC) {
+            const int nk = nrhs - r0 < ML_RC ? nrhs - r0 : ML_RC;
+            cplx<T> sacc[ML_RC], hacc[ML_RC];
+            for (int k = 0; k < ML_RC; ++k) sacc[k] = hacc[k] = czero<T>();
+            if (self_src) ml_rowdot_rhs(sacc, ml_block(v, c, 0), v.nc, row, self_src + (size_t)r0 * fs + (size_t)c * v.nc, fs, nk);
+            if (hop_src)
+                for (int d = 0; d < 8; ++d) {
+                    if (!v.same[(size_t)d * v.NB + c]) continue;
+                    const int n = v.nbr1[(size_t)d * v.NB + c];
+                    ml_rowdot_rhs(hacc, ml_block(v, c, 1 + d), v.nc, row, hop_src + (size_t)r0 * fs + (size_t)n * v.nc, fs, nk);
+                }
+            for (int k = 0; k < nk; ++k) {
+                const size_t o = (size_t)(r0 + k) * fs + i;
+                cplx<T> acc = add ? add[o] : czero<T>();
+                acc = acc + sacc[k];
+                dst[o] = acc + sign * hacc[k];
             }
-            acc = acc + sign * h;
         }
-        dst[i] = acc;
     }
 };
 
-// on the selected even sites: dst = Dinv_1 src; elsewhere 0 (zero_others) or unchanged
+// on the selected even sites: dst = Dinv_1 src; elsewhere 0 (zero_others) or unchanged.
+// One index per (site, row).
 template <typename T>
 struct MLDinvApply {
     MLView<T> v;
@@ -130,14 +163,22 @@ struct MLDinvApply {
     cplx<T>* dst;
     int colour;
     bool zero_others;
+    int nrhs;
     __host__ __device__ void operator()(long long i) const {
         const size_t fs = (size_t)v.NB * v.nc;
-        const int r = (int)(i / fs), c = (int)((i / v.nc) % v.NB), row = (int)(i % v.nc);
+        const int c = (int)(i / v.nc), row = (int)(i % v.nc);
         if (!ml_selected(v, c, ML_EVEN, colour)) {
-            if (zero_others) dst[i] = czero<T>();
+            if (zero_others)
+                for (int r = 0; r < nrhs; ++r) dst[(size_t)r * fs + i] = czero<T>();
             return;
         }
-        dst[i] = ml_rowdot(v.Dinv1 + (size_t)c * v.nc * v.nc, v.nc, row, src + r * fs + (size_t)c * v.nc);
+        for (int r0 = 0; r0 < nrhs; r0 += ML_RC) {
+            const int nk = nrhs - r0 < ML_RC ? nrhs - r0 : ML_RC;
+            cplx<T> acc[ML_RC];
+            for (int k = 0; k < ML_RC; ++k) acc[k] = czero<T>();
+            ml_rowdot_rhs(acc, v.Dinv1 + (size_t)c * v.nc * v.nc, v.nc, row, src + (size_t)r0 * fs + (size_t)c * v.nc, fs, nk);
+            for (int k = 0; k < nk; ++k) dst[(size_t)(r0 + k) * fs + i] = acc[k];
+        }
     }
 };
 
@@ -286,22 +327,29 @@ struct MLProlong {
 };
 
 // the couplings in direction `dir` that leave the block: dst = B_{1+dir} x[nbr] where the
-// neighbour lies in another block, 0 elsewhere
+// neighbour lies in another block, 0 elsewhere.  One index per (site, row).
 template <typename T>
 struct MLCrossHop {
     MLView<T> v;
     const cplx<T>* x;
     cplx<T>* dst;
     int dir;
+    int nrhs;
     __host__ __device__ void operator()(long long i) const {
         const size_t fs = (size_t)v.NB * v.nc;
-        const int r = (int)(i / fs), c = (int)((i / v.nc) % v.NB), row = (int)(i % v.nc);
+        const int c = (int)(i / v.nc), row = (int)(i % v.nc);
         if (v.same[(size_t)dir * v.NB + c]) {
-            dst[i] = czero<T>();
+            for (int r = 0; r < nrhs; ++r) dst[(size_t)r * fs + i] = czero<T>();
             return;
         }
         const int n = v.nbr1[(size_t)dir * v.NB + c];
-        dst[i] = ml_rowdot(ml_block(v, c, 1 + dir), v.nc, row, x + r * fs + (size_t)n * v.nc);
+        for (int r0 = 0; r0 < nrhs; r0 += ML_RC) {
+            const int nk = nrhs - r0 < ML_RC ? nrhs - r0 : ML_RC;
+            cplx<T> acc[ML_RC];
+            for (int k = 0; k < ML_RC; ++k) acc[k] = czero<T>();
+            ml_rowdot_rhs(acc, ml_block(v, c, 1 + dir), v.nc, row, x + (size_t)r0 * fs + (size_t)n * v.nc, fs, nk);
+            for (int k = 0; k < nk; ++k) dst[(size_t)(r0 + k) * fs + i] = acc[k];
+        }
     }
 };
 
@@ -395,26 +443,26 @@ struct MLSapWork {
 // back-substituted, and z += the block solution.
 template <class X, typename T>
 int ml_sap(const X& ex, const MLView<T>& v, const cplx<T>* b, cplx<T>* z, int nrhs, int nu, int mr_steps, const MLSapWork<T>& w) {
-    const long long nf = (long long)nrhs * v.NB * v.nc;
+    const long long nf = (long long)nrhs * v.NB * v.nc, ns = (long long)v.NB * v.nc;
     for (int it = 0; it < nu; ++it)
         for (int col = 0; col < 2; ++col) {
             int rc;
-            if ((rc = ex.run(nf, MLFullApply<T>{v, z, b, w.r}))) return rc;
+            if ((rc = ex.run(ns, MLFullApply<T>{v, z, b, w.r, nrhs}))) return rc;
             // t_e = A_ee^{-1} r_e; rho = r_o - A_oe t_e; x = 0
-            if ((rc = ex.run(nf, MLDinvApply<T>{v, w.r, w.te, col, true}))) return rc;
-            if ((rc = ex.run(nf, MLHopsCombine<T>{v, w.rho, w.r, nullptr, w.te, T(-1), ML_ODD, col, true}))) return rc;
+            if ((rc = ex.run(ns, MLDinvApply<T>{v, w.r, w.te, col, true, nrhs}))) return rc;
+            if ((rc = ex.run(ns, MLHopsCombine<T>{v, w.rho, w.r, nullptr, w.te, T(-1), ML_ODD, col, true, nrhs}))) return rc;
             if ((rc = ex.run(nf, MLZero<T>{w.x}))) return rc;
             for (int k = 0; k < mr_steps; ++k) {
                 // s = S rho = A_oo rho - A_oe A_ee^{-1} A_eo rho
-                if ((rc = ex.run(nf, MLHopsCombine<T>{v, w.u, nullptr, nullptr, w.rho, T(1), ML_EVEN, col, true}))) return rc;
-                if ((rc = ex.run(nf, MLDinvApply<T>{v, w.u, w.w, col, true}))) return rc;
-                if ((rc = ex.run(nf, MLHopsCombine<T>{v, w.s, nullptr, w.rho, w.w, T(-1), ML_ODD, col, true}))) return rc;
+                if ((rc = ex.run(ns, MLHopsCombine<T>{v, w.u, nullptr, nullptr, w.rho, T(1), ML_EVEN, col, true, nrhs}))) return rc;
+                if ((rc = ex.run(ns, MLDinvApply<T>{v, w.u, w.w, col, true, nrhs}))) return rc;
+                if ((rc = ex.run(ns, MLHopsCombine<T>{v, w.s, nullptr, w.rho, w.w, T(-1), ML_ODD, col, true, nrhs}))) return rc;
                 if ((rc = ex.run((long long)nrhs * v.NB2, MLBlockAlpha<T>{v, w.s, w.rho, w.alpha, col}))) return rc;
                 if ((rc = ex.run(nf, MLMRUpdate<T>{v, w.alpha, w.s, w.rho, w.x, col}))) return rc;
             }
             // x_e = A_ee^{-1} (r_e - A_eo x_o); z += x on the blocks of this colour
-            if ((rc = ex.run(nf, MLHopsCombine<T>{v, w.u, w.r, nullptr, w.x, T(-1), ML_EVEN, col, true}))) return rc;
-            if ((rc = ex.run(nf, MLDinvApply<T>{v, w.u, w.x, col, false}))) return rc;
+            if ((rc = ex.run(ns, MLHopsCombine<T>{v, w.u, w.r, nullptr, w.x, T(-1), ML_EVEN, col, true, nrhs}))) return rc;
+            if ((rc = ex.run(ns, MLDinvApply<T>{v, w.u, w.x, col, false, nrhs}))) return rc;
             if ((rc = ex.run(nf, MLAddColour<T>{v, w.x, z, col}))) return rc;
         }
     return 0;
@@ -458,7 +506,7 @@ int ml_setup1_t(const X& ex, const MLView<T>& v, cplx<T>* vec, int n_inv, bool i
             if ((rc = vcycle(vec, u, N1))) return rc;  // v <- C v
             if ((rc = ex.run(nf, MLCopy<T>{u, vec}))) return rc;
         } else {
-            if ((rc = ex.run(nf, MLFullApply<T>{v, vec, vec, t}))) return rc;  // t = v - D_1 v
+            if ((rc = ex.run((long long)v.NB * v.nc, MLFullApply<T>{v, vec, vec, t, N1}))) return rc;  // t = v - D_1 v
             if ((rc = vcycle(t, u, N1))) return rc;                             // u = C t
             if ((rc = ex.run(nf, MLAdd<T>{vec, u, vec}))) return rc;           // v <- v + C (v - D_1 v)
         }
@@ -474,15 +522,15 @@ int ml_setup1_t(const X& ex, const MLView<T>& v, cplx<T>* vec, int n_inv, bool i
 template <class X, typename T>
 int ml_galerkin(const X& ex, const MLView<T>& v, cplx<T>* B2, cplx<T>* E, cplx<T>* W, cplx<T>* Y, cplx<T>* e) {
     const int nc2 = 2 * v.N1;
-    const long long n2 = (long long)nc2 * v.NB2 * nc2, n1 = (long long)nc2 * v.NB * v.nc;
+    const long long n2 = (long long)nc2 * v.NB2 * nc2, n1 = (long long)nc2 * v.NB * v.nc, ns = (long long)v.NB * v.nc;
     int rc;
     if ((rc = ex.run(n2, MLUnitColumns<T>{v.NB2, nc2, E}))) return rc;
     if ((rc = ex.run(n1, MLProlong<T>{v, E, W}))) return rc;
-    if ((rc = ex.run(n1, MLHopsCombine<T>{v, Y, nullptr, W, W, T(1), ML_ALL, -1, true}))) return rc;
+    if ((rc = ex.run(ns, MLHopsCombine<T>{v, Y, nullptr, W, W, T(1), ML_ALL, -1, true, nc2}))) return rc;
     if ((rc = ex.run(n2, MLRestrict<T>{v, Y, e}))) return rc;
     if ((rc = ex.run(n2, MLScatterB2<T>{v.NB2, nc2, 0, e, B2}))) return rc;
     for (int dir = 0; dir < 8; ++dir) {
-        if ((rc = ex.run(n1, MLCrossHop<T>{v, W, Y, dir}))) return rc;
+        if ((rc = ex.run(ns, MLCrossHop<T>{v, W, Y, dir, nc2}))) return rc;
         if ((rc = ex.run(n2, MLRestrict<T>{v, Y, e}))) return rc;
         if ((rc = ex.run(n2, MLScatterB2<T>{v.NB2, nc2, 1 + dir, e, B2}))) return rc;
     }

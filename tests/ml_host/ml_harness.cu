@@ -140,8 +140,8 @@ int mlh_prolong(const int* L1, const int* b1, int nc, int N1, const double* P1, 
 int mlh_apply(const int* L1, const int* b1, int nc, const double* B1, const double* x, double* y, int nrhs) {
     HostLevel L(L1, b1, nc, 1, B1, nullptr, nullptr);
     if (L.ok) return -1;
-    return MLHostExec{}.run((long long)nrhs * L.g.NB * nc,
-                            MLFullApply<double>{L.v, reinterpret_cast<const C*>(x), nullptr, reinterpret_cast<C*>(y)});
+    return MLHostExec{}.run((long long)L.g.NB * nc,
+                            MLFullApply<double>{L.v, reinterpret_cast<const C*>(x), nullptr, reinterpret_cast<C*>(y), nrhs});
 }
 
 int mlh_galerkin(const int* L1, const int* b1, int nc, int N1, const double* B1, const double* P1, double* B2) {

@@ -345,7 +345,17 @@ int ddamg_ml_build(ddamg_handle* h, const ddamg_ml_params* p, const double* v1);
  * start of every round and after the last.  v_out (may be null) receives the final vectors.
  * Errors as ddamg_ml_build. */
 int ddamg_ml_setup(ddamg_handle* h, const ddamg_ml_params* p, const double* v0, double* v_out);
-/* Release the third level (ddamg_destroy does it too). */
+/* A fourth (fifth, ...) level: the same construction applied to the current coarsest level, whose
+ * odd-even GMRES is then replaced by FGMRES(inner_kv) preconditioned by its own V-cycle (Sec. 7
+ * runs 2, 3 and 4 levels).  p->block1 and p->n_vec1 refer to the current coarsest level (its sites
+ * and 2 n_vec components per site); v holds its test vectors ([n_vec1][its sites lex][its
+ * components]): initial ones for the adaptive setup (setup != 0), or the vectors themselves
+ * (setup == 0).  v_out (may be null) receives the final vectors.  Errors as ddamg_ml_build;
+ * NOT_READY without a third level. */
+int ddamg_ml_add_level(ddamg_handle* h, const ddamg_ml_params* p, const double* v, int setup, double* v_out);
+/* Number of levels of the hierarchy: 2 without a third level. */
+int ddamg_ml_levels(const ddamg_handle* h);
+/* Release the levels beyond the second (ddamg_destroy does it too). */
 int ddamg_ml_release(ddamg_handle* h);
 /* out = M_SAP^(nu) in on level 1 (red-black SAP of D_1 over the level-1 blocks, MR block solves). */
 int ddamg_ml_apply_sap1(ddamg_handle* h, const double* in, double* out, int n_rhs, int nu);

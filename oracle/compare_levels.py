@@ -13,7 +13,9 @@ Timings of this FP64 numpy oracle say nothing about a GPU, so this script counts
 Both hierarchies share the level-0 setup (the two-level Algorithm 2 run), so the comparison isolates
 the coarse solve.  Writes paper_1303_1377_gb300/workloads.json["levels_study"] and prints it.
 
-usage: python -m oracle.compare_levels [--N 8] [--N1 8] [--n-inv 3]
+usage: python -m oracle.compare_levels [--N 8] [--N1 8] [--n-inv 3] [--workload lattice_8x8x8x8]
+       [--dims 16,16,16,16 --m0 -0.93 --key levels_study_16x16x16x16]   (another volume or mass of
+       the workload's ensemble parameters eps and seed)
 """
 from __future__ import annotations
 
@@ -39,9 +41,16 @@ def main():
     ap.add_argument("--N1", type=int, default=8)
     ap.add_argument("--n-inv", type=int, default=3)
     ap.add_argument("--workload", default="lattice_8x8x8x8")
+    ap.add_argument("--dims", default=None)
+    ap.add_argument("--m0", type=float, default=None)
+    ap.add_argument("--key", default="levels_study")
     a = ap.parse_args()
     rec = json.load(open(OUT))[a.workload]
     dims, eps, seed, m0 = tuple(rec["dims"]), rec["eps"], rec["seed"], rec["m0"]
+    if a.dims:
+        dims = tuple(int(d) for d in a.dims.split(","))
+    if a.m0 is not None:
+        m0 = a.m0
     D = DiracOperator(synth.gauge_field(dims, eps, seed), dims, m0, rec.get("c_sw", 1.0))
     blk = (2, 2, 2, 2)
     p0 = Params(N=a.N, agg_block=blk, sap_block=blk, n_inv=a.n_inv, nu=2)
@@ -69,8 +78,9 @@ def main():
     out["three_level"] = {"outer_iterations": int(info3["iters"]), "fgmres_steps_D1": int(ml.levels[0].coarse_iters),
                           "level1_vcycles": int(info3["vcycles_per_level"][1]), "gmres_steps_D2": int(info3["coarsest_iters"]),
                           "rel_residual": res3}
+    out["eps"], out["seed"] = eps, seed
     data = json.load(open(OUT))
-    data["levels_study"] = out
+    data[a.key] = out
     json.dump(data, open(OUT, "w"), indent=1)
     print(json.dumps(out))
 

@@ -156,6 +156,8 @@ def _load():
         "ddamg_ml_default_params": (None, [C.POINTER(MLParams)]),
         "ddamg_ml_build": (I, [P, C.POINTER(MLParams), P]),
         "ddamg_ml_setup": (I, [P, C.POINTER(MLParams), P, P]),
+        "ddamg_ml_add_level": (I, [P, C.POINTER(MLParams), P, I, P]),
+        "ddamg_ml_levels": (I, [P]),
         "ddamg_ml_release": (I, [P]),
         "ddamg_ml_apply_sap1": (I, [P, P, P, I, I]),
         "ddamg_ml_restrict1": (I, [P, P, P, I]),
@@ -326,6 +328,18 @@ class Solver:
         self.n_level2 = int(np.prod(nb1))
         self.level2_dof = 2 * self.ml_params.n_vec1
         return out
+
+    def ml_add_level(self, v, params: MLParams, setup: bool = True):
+        """One more level below the current coarsest one; v[N, its sites, its components] are the
+        initial vectors of its adaptive setup (setup=True) or the vectors themselves.  Returns the
+        final vectors."""
+        v = _host(v, np.complex128)
+        out = np.empty_like(v) if not _is_torch(v) else _empty_like(v, tuple(v.shape), np.complex128)
+        _check(lib.ddamg_ml_add_level(self.h, C.byref(params), _ptr(v), int(bool(setup)), _ptr(out)), "ddamg_ml_add_level")
+        return out
+
+    def ml_levels(self) -> int:
+        return int(lib.ddamg_ml_levels(self.h))
 
     def coarse_dims(self):
         return tuple(self.dims[m] // self.params.block[m] for m in range(4))

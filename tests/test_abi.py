@@ -117,3 +117,5 @@ def test_third_level_defaults_and_argument_checks(libpath):
     assert ddamg.lib.ddamg_ml_solve(None, None, None, 1, 1e-10, None) == -1
     assert ddamg.lib.ddamg_ml_release(None) == -1
     assert ddamg.lib.ddamg_ml_setup(None, ctypes.byref(p), None, None) == -1
+    assert ddamg.lib.ddamg_ml_add_level(None, ctypes.byref(p), None, 1, None) == -1
+    assert ddamg.lib.ddamg_ml_levels(None) == -1

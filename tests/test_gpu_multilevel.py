@@ -164,3 +164,33 @@ def test_three_level_solve_mixed_precision(case, prec):
     for q in range(2):
         assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
     assert counts["fgmres_steps_D1"] > 0 and counts["gmres_steps_D2"] > 0
+
+
+def test_four_levels():
+    """16^4 fine lattice, 2^4 blocks on every level, N = N_1 = N_2 = 2: levels 8^4, 4^4 and 2^4.  The
+    GPU hierarchy built from the oracle's vectors solves to a true residual of 1e-10 and agrees
+    with the oracle's four-level solve."""
+    from paper_1303_1377_gb300 import ddamg
+
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_field(dims, 0.5, seed=131)
+    D = DiracOperator(U, dims, M0, CSW)
+    v0 = synth.random_test_vectors(dims, 2, seed=132)
+    v1 = synth.gaussian_coarse(8 ** 4, 4, 2, seed=133)
+    v2 = synth.gaussian_coarse(4 ** 4, 4, 2, seed=134)
+    ps = [OParams(N=2, agg_block=BLK, sap_block=BLK, nu=2) for _ in range(3)]
+    ml = MultiLevel(D, ps)
+    ml.build([v0, v1, v2])
+    b = synth.gaussian_spinors(dims, 1, seed=135)
+    zo, _ = ml.solve(b[0])
+    p = ddamg.default_params(n_vec=2, block=BLK, precision=ddamg.PREC_DOUBLE, nu=2)
+    with ddamg.Solver(dims, U, M0, CSW, p, setup=False) as s:
+        s.setup_from_vectors(v0)
+        mp = ddamg.ml_default_params(block1=BLK, n_vec1=2, nu1=2)
+        s.ml_build(v1, mp)
+        s.ml_add_level(v2, mp, setup=False)
+        assert s.ml_levels() == 4
+        z, st, rc = s.ml_solve(b)
+    assert rc == 0
+    assert np.linalg.norm(b[0] - D.apply(z[0])) <= 1e-10 * np.linalg.norm(b[0])
+    assert np.linalg.norm(z[0] - zo) <= 1e-8 * np.linalg.norm(zo)

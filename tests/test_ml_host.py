@@ -257,3 +257,41 @@ def test_sap_in_fp32_stays_at_single_precision(lv):
     assert lv.lib.mlh_sap_f32(ip(lv.L1), ip(lv.b1), lv.nc, dp(lv.B1), dp(lv.Dinv1), dp(lv.to_int(b)), dp(z), 2, 2, 4) == 0
     err = np.max(np.abs(lv.to_lex(z) - ref)) / np.max(np.abs(ref))
     assert 1e-9 < err < 2e-5  # FP32 rounding is visible, and small
+
+
+@pytest.mark.parametrize("L1,b1", [((4, 2, 6, 4), (2, 1, 3, 2)), ((2, 4, 4, 8), (1, 2, 1, 2)), ((6, 6, 2, 4), (3, 3, 1, 2)),
+                                   ((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 4, 2, 2), (4, 2, 1, 1))])
+def test_blocking_of_asymmetric_lattices(lib, L1, b1):
+    """Internal order, neighbours, in-block flags, block membership (even sites first) and the next
+    level's order and neighbours against the oracle's lattice and blocking, for lattices and blocks of
+    unequal and odd extents."""
+    L1a, b1a = np.array(L1, dtype=np.int32), np.array(b1, dtype=np.int32)
+    sz = np.zeros(4, dtype=np.int32)
+    assert lib.mlh_geom_sizes(ip(L1a), ip(b1a), ip(sz)) == 0
+    NB, NB2, Vb1, Vb1e = (int(v) for v in sz)
+    g = {k: np.zeros(n, dtype=np.int32) for k, n in (("lex1", NB), ("nbr1", 8 * NB), ("sites", NB2 * Vb1), ("blk_of", NB),
+                                                     ("loc_of", NB), ("nbr2", 8 * NB2), ("lex2", NB2))}
+    same = np.zeros(8 * NB, dtype=np.uint8)
+    assert lib.mlh_geom_fill(ip(L1a), ip(b1a), *(g[k].ctypes.data_as(P_I) for k in ("lex1", "nbr1", "sites", "blk_of", "loc_of")),
+                             same.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), g["nbr2"].ctypes.data_as(P_I),
+                             g["lex2"].ctypes.data_as(P_I)) == 0
+    lat, blk = Lattice(L1), Blocking(Lattice(L1), b1)
+    lex1, lex2 = g["lex1"], g["lex2"]
+    assert NB == lat.V and NB2 == blk.nblocks and Vb1 == blk.bvol and Vb1e == Vb1 // 2
+    assert np.all(lat.parity[lex1[: NB // 2]] == 0) and np.all(lat.parity[lex1[NB // 2:]] == 1)
+    int1 = np.empty(NB, dtype=np.int64)
+    int1[lex1] = np.arange(NB)
+    for d in range(8):
+        mu, s = d >> 1, (-1 if d & 1 else 1)
+        assert np.array_equal(g["nbr1"].reshape(8, NB)[d], int1[lat.neighbour(mu, s)[lex1]])
+        assert np.array_equal(same.reshape(8, NB)[d].astype(bool), blk.same_block(mu, s)[lex1])
+    sites = g["sites"].reshape(NB2, Vb1)
+    for c2 in range(NB2):
+        assert set(lex1[sites[c2]]) == set(blk.sites[lex2[c2]])
+        assert np.all(lat.parity[lex1[sites[c2, :Vb1e]]] == 0) and np.all(lat.parity[lex1[sites[c2, Vb1e:]]] == 1)
+    lat2 = Lattice(blk.nb_dims)
+    int2 = np.empty(NB2, dtype=np.int64)
+    int2[lex2] = np.arange(NB2)
+    assert np.all(lat2.parity[lex2[: NB2 // 2]] == 0)
+    for d in range(8):
+        assert np.array_equal(g["nbr2"].reshape(8, NB2)[d], int2[lat2.neighbour(d >> 1, -1 if d & 1 else 1)[lex2]])

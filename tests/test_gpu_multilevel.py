@@ -109,19 +109,22 @@ def test_three_level_solve(case):
     assert counts["fgmres_steps_D1"] > 0 and counts["gmres_steps_D2"] > 0 and counts["vcycles1"] > 0
 
 
-def test_stale_third_level_and_precision_checks(case):
+def test_stale_third_level_and_argument_checks(case):
+    """A mass change makes the third level stale (NOT_READY until it is built again); level-1 blocks
+    that do not divide the level-1 lattice and too many level-1 vectors are refused."""
     ddamg = case["ddamg"]
     with case["gpu"]() as s:
         s.set_mass(M0 + 0.01)
         with pytest.raises(ddamg.DDAMGError) as e:
             s.ml_vcycle1(synth.gaussian_coarse(4 ** 4, 2 * N0, 1, seed=119))
         assert e.value.status == -7
-    p = ddamg.default_params(n_vec=N0, block=BLK, precision=ddamg.PREC_SINGLE, nu=2)
-    with ddamg.Solver(DIMS, synth.gauge_field(DIMS, 0.5, seed=111), M0, CSW, p, setup=False) as s:
-        s.setup_from_vectors(synth.random_test_vectors(DIMS, N0, seed=112))
-        with pytest.raises(ddamg.DDAMGError) as e:
-            s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1))
-        assert e.value.status == -1
+    with case["handle"]() as s:
+        v1 = synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113)
+        for kw in ({"block1": (3, 2, 2, 2), "n_vec1": N1}, {"block1": BLK1, "n_vec1": 2 ** 4 * N0 + 1}):
+            with pytest.raises(ddamg.DDAMGError) as e:
+                s.ml_build(v1, ddamg.ml_default_params(**kw))
+            assert e.value.status == -1
+        assert s.ml_levels() == 2
 
 
 @pytest.mark.parametrize("update", ["ddalpha", "idsetup"])

@@ -298,7 +298,7 @@ long long ddamg_launch_count(void);
 void ddamg_debug_fail_allocs(int n);
 
 /* ---- Recursion to a third level (Sec. 3: the two-level algorithm formulated again for the coarse
- * system, whose solve then needs only low accuracy; Sec. 7: 3 and 4 levels).  The paper prints no
+ * system, whose solve then needs only low accuracy; Sec. 6.4: 3 and 4 levels).  The paper prints no
  * algorithm for it; this one is:
  *   level 1 = the handle's coarse lattice and D_1 = D_c; its lattice blocks (block1) are the
  *   level-1 SAP domains and aggregates; P_1 is the ordered orthonormal basis of the level-1 test
@@ -346,7 +346,7 @@ int ddamg_ml_build(ddamg_handle* h, const ddamg_ml_params* p, const double* v1);
  * Errors as ddamg_ml_build. */
 int ddamg_ml_setup(ddamg_handle* h, const ddamg_ml_params* p, const double* v0, double* v_out);
 /* A fourth (fifth, ...) level: the same construction applied to the current coarsest level, whose
- * odd-even GMRES is then replaced by FGMRES(inner_kv) preconditioned by its own V-cycle (Sec. 7
+ * odd-even GMRES is then replaced by FGMRES(inner_kv) preconditioned by its own V-cycle (Sec. 6.4
  * runs 2, 3 and 4 levels).  p->block1 and p->n_vec1 refer to the current coarsest level (its sites
  * and 2 n_vec components per site); v holds its test vectors ([n_vec1][its sites lex][its
  * components]): initial ones for the adaptive setup (setup != 0), or the vectors themselves

@@ -1,6 +1,6 @@
 """Two levels against three on one near-critical lattice: iteration counts and coarse-level work.
 
-Test infrastructure only (the oracle).  Sec. 7 reports that going from two to three levels speeds
+Test infrastructure only (the oracle).  Sec. 6.4 reports that going from two to three levels speeds
 the solve up most near the critical mass, because the coarse system is the ill-conditioned part.
 Timings of this FP64 numpy oracle say nothing about a GPU, so this script counts work instead:
 

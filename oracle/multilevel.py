@@ -4,7 +4,7 @@ Test infrastructure only (the oracle): plain FP64 numpy, imported by tests alone
 
 Sec. 3 states that the coarse equation D_c e = P^H r can itself be solved by an algorithm of the
 same two-level kind, recursively, until the operator is small enough to solve directly, and that
-Gamma5-compatible aggregation (Sec. 3.2) is what keeps D_c fit for that recursion; Sec. 7 reports a
+Gamma5-compatible aggregation (Sec. 3.2) is what keeps D_c fit for that recursion; Sec. 6.4 reports a
 preliminary 2-, 3- and 4-level version.  The paper prints no algorithm for it, so this module fixes
 the following readings (each is listed with the other readings of the paper):
 

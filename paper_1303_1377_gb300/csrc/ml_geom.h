@@ -1,5 +1,5 @@
 // Blocking of the level-1 lattice for the recursion to a third level (Sec. 3: the two-level
-// method formulated again for the coarse system; Sec. 7: 3 and 4 levels).  Host-only C++.
+// method formulated again for the coarse system; Sec. 6.4: 3 and 4 levels).  Host-only C++.
 //
 // The level-1 lattice is the lattice of the fine aggregates, with the library's internal coarse
 // order: sites whose coordinate sum is even first, then odd, each group lexicographic (x0

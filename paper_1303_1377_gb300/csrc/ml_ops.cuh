@@ -1,5 +1,5 @@
 // Level-1 operations of the recursion to a third level (Sec. 3 applied to the coarse system;
-// Sec. 7): red-black SAP over blocks of level-1 sites with odd-even MR block solves (Sec. 2.3 and
+// Sec. 6.4): red-black SAP over blocks of level-1 sites with odd-even MR block solves (Sec. 2.3 and
 // Sec. 6 on D_1 = P^H D P), Gamma5-compatible aggregation of level-1 test vectors with ordered
 // local orthonormalisation (Sec. 3.1-3.2), restriction, prolongation and the Galerkin operator
 // D_2 = P_1^H D_1 P_1 as a nine-block stencil.

@@ -1,5 +1,5 @@
 """Pins of the oracle's multilevel recursion (the two-level method applied to its own coarse
-system, Sec. 3 and Sec. 7): the generic stencil level against the pinned fine classes and against
+system, Sec. 3 and Sec. 6.4): the generic stencil level against the pinned fine classes and against
 dense matrices, and the nested iteration matrix of the three-level V-cycle."""
 import numpy as np
 import pytest

@@ -238,6 +238,58 @@ int mlh_vcycle1(const int* L1, const int* b1, int nc, int N1, const double* B1, 
                         ex.data(), DenseCoarse{&inv, n2});
 }
 
+// the level-1 V-cycle in FP32 (SINGLE and HALF handles): inputs rounded to complex64, the exact
+// level-2 solve applied in FP32 too, the result returned as complex128
+int mlh_vcycle1_f32(const int* L1, const int* b1, int nc, int N1, const double* B1, const double* Dinv1, const double* P1, const double* D2inv,
+                    const double* r, double* x, int nrhs, int nu, int mr_steps) {
+    MLHostGeom g;
+    if (ml_build_geom(L1, b1, g)) return -1;
+    using F = cplx<float>;
+    auto to_f = [](const double* p, size_t n) {
+        std::vector<F> out(n);
+        for (size_t i = 0; i < n; ++i) out[i] = mk((float)p[2 * i], (float)p[2 * i + 1]);
+        return out;
+    };
+    const int n2 = g.NB2 * 2 * N1;
+    const size_t nf = (size_t)nrhs * g.NB * nc;
+    std::vector<F> Bf = to_f(B1, (size_t)g.NB * 9 * nc * nc), Df = to_f(Dinv1, (size_t)(g.NB / 2) * nc * nc),
+                   Pf = to_f(P1, (size_t)g.NB * nc * N1), If = to_f(D2inv, (size_t)n2 * n2), rf = to_f(r, nf), xf(nf);
+    MLView<float> v{};
+    v.NB = g.NB;
+    v.nc = nc;
+    v.half = nc / 2;
+    v.NB2 = g.NB2;
+    v.Vb1 = g.Vb1;
+    v.Vb1e = g.Vb1e;
+    v.N1 = N1;
+    v.nbr1 = g.nbr1.data();
+    v.sites = g.sites.data();
+    v.blk_of = g.blk_of.data();
+    v.loc_of = g.loc_of.data();
+    v.same = g.same.data();
+    v.B1 = Bf.data();
+    v.Dinv1 = Df.data();
+    v.P1 = Pf.data();
+    std::vector<F> r1(nf), te(nf), rho(nf), u(nf), w(nf), s(nf), x1(nf), alpha((size_t)nrhs * g.NB2), eb((size_t)nrhs * n2),
+        ex((size_t)nrhs * n2);
+    MLSapWork<float> wk{r1.data(), te.data(), rho.data(), u.data(), w.data(), s.data(), x1.data(), alpha.data()};
+    auto coarse = [&](const F* b2, F* x2, int nr) {
+        for (int q = 0; q < nr; ++q)
+            for (int i = 0; i < n2; ++i) {
+                F acc = czero<float>();
+                for (int j = 0; j < n2; ++j) cmac(acc, If[(size_t)i * n2 + j], b2[(size_t)q * n2 + j]);
+                x2[(size_t)q * n2 + i] = acc;
+            }
+        return 0;
+    };
+    const int rc = ml_vcycle1_t(MLHostExec{}, v, rf.data(), xf.data(), nrhs, nu, mr_steps, wk, eb.data(), ex.data(), coarse);
+    for (size_t i = 0; i < nf; ++i) {
+        x[2 * i] = xf[i].re;
+        x[2 * i + 1] = xf[i].im;
+    }
+    return rc;
+}
+
 // the level-1 setup from the initial vectors vec (returned updated), with exact level-2 solves;
 // P1 and B2 receive the final interpolation and D_2
 int mlh_setup1(const int* L1, const int* b1, int nc, int N1, const double* B1, const double* Dinv1, double* vec, int n_inv, int idsetup,

@@ -398,6 +398,8 @@ def main():
         "gauge_generation_seconds": t_gauge,
         "kernel_profile_first_step": prof_all,
     }
+    if args.levels == 3:
+        line["ml_counts_last_step"] = solver.ml_counts()  # FGMRES steps on D_1, GMRES steps on D_2, level-1 V-cycles
     solver.close()
     del b, z
     torch.cuda.empty_cache()

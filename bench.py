@@ -237,6 +237,8 @@ def main():
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
     ap.add_argument("--levels", type=int, default=2, choices=[2, 3],
                     help="3: the recursion to a third level (level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup)")
+    ap.add_argument("--ml-inner", default="fgmres", choices=["fgmres", "vcycle"],
+                    help="with --levels 3: the level-1 solve inside the fine V-cycle (FGMRES to 5e-2, or one level-1 V-cycle)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -268,8 +270,8 @@ def main():
     t = time.perf_counter()
     solver = ddamg.Solver(dims, U, m0, C_SW, params, setup=True)
     if args.levels == 3:
-        n1 = ddamg.ml_default_params().n_vec1
-        solver.ml_setup(synth.gaussian_coarse(solver.n_coarse, solver.coarse_dof, n1, seed=w["seed"] + 11))
+        mlp = ddamg.ml_default_params(inner=1 if args.ml_inner == "vcycle" else 0)
+        solver.ml_setup(synth.gaussian_coarse(solver.n_coarse, solver.coarse_dof, mlp.n_vec1, seed=w["seed"] + 11), mlp)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t
     del U
@@ -377,7 +379,7 @@ def main():
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": workload_description(args.workload, w, m0),
-                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision, "levels": args.levels,
+                   "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision, "levels": args.levels, **({"ml_inner": args.ml_inner} if args.levels == 3 else {}),
                    "outer": (f"FP32 FGMRES cycles to {args.cycle_tol:g} + FP64 residual correction" if args.outer == "refine"
                              and args.precision != "double" else "double-word FGMRES" if args.precision != "double" else "FP64 FGMRES")},
         "roofline": roof,

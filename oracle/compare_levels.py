@@ -16,6 +16,7 @@ the coarse solve.  Writes paper_1303_1377_gb300/workloads.json["levels_study"] a
 usage: python -m oracle.compare_levels [--N 8] [--N1 8] [--n-inv 3] [--workload lattice_8x8x8x8]
        [--dims 16,16,16,16 --m0 -0.93 --key levels_study_16x16x16x16]   (another volume or mass of
        the workload's ensemble parameters eps and seed)
+       [--inner vcycle | --inner-tol 0.1]   (the level-1 solve inside the fine V-cycle, reading ML4)
 """
 from __future__ import annotations
 
@@ -44,6 +45,8 @@ def main():
     ap.add_argument("--dims", default=None)
     ap.add_argument("--m0", type=float, default=None)
     ap.add_argument("--key", default="levels_study")
+    ap.add_argument("--inner", default="fgmres", choices=["fgmres", "vcycle"])
+    ap.add_argument("--inner-tol", type=float, default=5e-2)
     a = ap.parse_args()
     rec = json.load(open(OUT))[a.workload]
     dims, eps, seed, m0 = tuple(rec["dims"]), rec["eps"], rec["seed"], rec["m0"]
@@ -63,7 +66,7 @@ def main():
     x2, info2 = two.solve(b)
     res2 = float(np.linalg.norm(b - D.apply(x2)) / np.linalg.norm(b))
     # three levels on the same level 0: level-1 setup, then FGMRES on D_1 with the level-1 V-cycle
-    ml = MultiLevel(D, [p0, p1])
+    ml = MultiLevel(D, [p0, p1], inner=a.inner, inner_tol=a.inner_tol)
     ml.levels = [two]
     l1 = ml._next(0)
     ml.levels.append(l1)
@@ -78,7 +81,7 @@ def main():
     out["three_level"] = {"outer_iterations": int(info3["iters"]), "fgmres_steps_D1": int(ml.levels[0].coarse_iters),
                           "level1_vcycles": int(info3["vcycles_per_level"][1]), "gmres_steps_D2": int(info3["coarsest_iters"]),
                           "rel_residual": res3}
-    out["eps"], out["seed"] = eps, seed
+    out["eps"], out["seed"], out["inner"], out["inner_tol"] = eps, seed, a.inner, a.inner_tol
     data = json.load(open(OUT))
     data[a.key] = out
     json.dump(data, open(OUT, "w"), indent=1)

@@ -105,11 +105,19 @@ typedef struct {
     int precision;        /* ddamg_precision (DDAMG_PREC_SINGLE) */
     int rebuild_after_last; /* 1: rebuild P, D_c after the last setup update (1) */
     uint64_t seed;        /* seed of the initial random test vectors (1) */
-    double time_limit_s;  /* wall-clock limit per solve call, <= 0: none (0) */
+    double time_limit_s;  /* wall-clock limit per solve call (ddamg_solve, ddamg_solve_batch,
+                             ddamg_solve_batch_zero_guess, ddamg_ml_solve), <= 0: none (0).
+                             Checked on the host at every synchronisation of the outer
+                             iteration (each FGMRES step); once passed, z takes the current
+                             cycle's update and the call returns DDAMG_ERR_TIMEOUT with
+                             st[r].rel_residual the last residual estimate. */
     int outer;            /* ddamg_outer of SINGLE and HALF mode (DDAMG_OUTER_REFINE) */
     double cycle_tol;     /* residual reduction of one FP32 cycle of DDAMG_OUTER_REFINE, in (0, 1) (1e-5) */
     int setup_update;     /* ddamg_setup_update: test-vector update of the setup's second phase
                              (DDAMG_SETUP_DDALPHA) */
+    int smoother_fp16;    /* DDAMG_PREC_HALF only: 1 = the SAP smoother reads FP16 copies of the
+                             links and site terms (FP32 arithmetic); 0 = FP32 copies, so that only
+                             P, D_c and its inverses are stored in FP16 (1) */
 } ddamg_params;
 
 /* Statistics of one solve (the quantities reported in Tables 3-9). */
@@ -172,6 +180,13 @@ int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_s
  * space and stops at its own convergence; st (may be NULL) points to n_rhs stats. */
 int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol,
                       ddamg_stats* st);
+
+/* ddamg_solve_batch from the zero initial guess of Sec. 6 with z output only: z is
+ * neither read nor copied to the device (for host buffers this saves one field
+ * upload per right-hand side), and no initial residual product is formed.  Same
+ * arguments, statistics and errors as ddamg_solve_batch. */
+int ddamg_solve_batch_zero_guess(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol,
+                                 ddamg_stats* st);
 
 /* Continuous batching (no counterpart in the paper).  A handle keeps up to n_slots
  * right-hand sides in flight.  ddamg_slots_cycle runs one outer cycle (one FGMRES cycle
@@ -241,8 +256,12 @@ int ddamg_apply_Dc(ddamg_handle* h, const double* in, double* out, int n_rhs);
  *   precision, 8 single / 16 double); larger n_rhs fails with
  *   DDAMG_ERR_INVALID_ARG and a message giving the limit.  No cudaMalloc,
  *   cudaFree or other allocating call is made.
+ * The handle's device (current when the handle was created) must be the current
+ *   device; otherwise DDAMG_ERR_INVALID_ARG.
  * The first call on a device looks the array up with cudaGetSymbolAddress (with
  *   that device current); make that first call before any stream capture.
+ * The call is stream-ordered on the handle's stream and returns without waiting
+ *   for the GPU: out is complete once that stream reaches the call's last kernel.
  * All calls share the one array and it keeps the last call's contents; calls that
  *   overlap on the GPU (other host threads, other streams) race on it. */
 int ddamg_apply_Dc_noalloc(ddamg_handle* h, const double* in, double* out, int n_rhs);

@@ -14,6 +14,7 @@ struct ddamg_handle;
 
 namespace ddamg {
 int apply_Dc_into_scratch(ddamg_handle* h, const double* in, double* out, int n_rhs, void* scratch, size_t scratch_bytes);
+int handle_device(const ddamg_handle* h);
 }
 
 namespace {
@@ -30,11 +31,28 @@ void* g_scratch_addr[kMaxDevices] = {};
 }  // namespace
 
 extern "C" int ddamg_apply_Dc_noalloc(ddamg_handle* h, const double* in, double* out, int n_rhs) {
-    int dev = 0;
+    if (!h) {
+        ddamg::set_error("ddamg_apply_Dc_noalloc: null handle");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    // The kernels run on the handle's stream, which lives on the device the handle was created on;
+    // the scratch address must be that device's copy of the array.
+    const int hdev = ddamg::handle_device(h);
+    int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         ddamg::set_error(std::string("ddamg_apply_Dc_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return DDAMG_ERR_CUDA;
+    }
+    if (dev != hdev) {
+        ddamg::set_error("ddamg_apply_Dc_noalloc: the current device (" + std::to_string(dev) + ") is not the handle's device (" +
+                         std::to_string(hdev) + "); make the handle's device current first");
+        return DDAMG_ERR_INVALID_ARG;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        ddamg::set_error("ddamg_apply_Dc_noalloc: device index " + std::to_string(dev) + " is beyond the " +
+                         std::to_string(kMaxDevices) + " devices this entry point keeps a scratch address for");
+        return DDAMG_ERR_INVALID_ARG;
     }
     if (!g_scratch_addr[dev]) {
         // one-time set-up on this device (with this device current)

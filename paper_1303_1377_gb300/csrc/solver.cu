@@ -194,6 +194,7 @@ struct ddamg_handle {
     // geometry
     int L[4], b[4], nbk[4];
     int V, Vb, NB, N, nc;
+    int device = 0;  // the CUDA device current at creation: every allocation and stream of the handle is on it
     ddamg_params p;
     double m0, csw;
     cudaStream_t own_stream = nullptr, stream = nullptr;
@@ -535,7 +536,7 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
     for (int it = 0; it < nu; ++it)
         for (int colour = 0; colour < 2; ++colour) {
             // operator bytes at their stored size: FP16 links and site terms on the half-mode path
-            const bool f16 = std::is_same<T, float>::value && h->half() && sap_aos_supported(h->g, nrhs);
+            const bool f16 = std::is_same<T, float>::value && h->half() && h->p.smoother_fp16 && sap_aos_supported(h->g, nrhs);
             const double opb = f16 ? 2.0 : (double)sizeof(T);
             Prof pr(h, PF_SAP, (double)h->V / 2 * (36.0 * 2 * opb + 144.0 * opb + nrhs * 36.0 * 2 * sizeof(T)),
                     (double)h->V / 4 * nrhs * sap_pair_flops(h));
@@ -637,6 +638,8 @@ struct KrylovProblem {
     bool lean = false;     // FP32 basis: one Gram-Schmidt pass, a second one only on heavy cancellation
     double cycle_tol = 0;  // > 0: a cycle ends once every rhs has reduced its residual by this factor
     int max_cycles = 0;    // > 0: return after this many cycles (x updated, no closing residual)
+    bool has_deadline = false;  // wall-clock limit: checked at every host synchronisation of the iteration;
+    std::chrono::steady_clock::time_point deadline{};  // once passed, x takes the current cycle's update and the solve returns
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
     cplx<TZ>* Zb;          // [m][nrhs][n] when M is set
     cplx<TV>* w;           // [nrhs][n]
@@ -653,6 +656,7 @@ struct KrylovResult {
     int restarts = 0;
     bool nonfinite = false;
     bool converged = true;
+    bool timed_out = false;  // the wall-clock limit ended the iteration (x holds the last iterate)
 };
 
 // basis-space kernels (generic precisions / double-word)
@@ -810,6 +814,10 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             R.converged = false;
             break;
         }
+        if (P.has_deadline && std::chrono::steady_clock::now() >= P.deadline) {
+            R.timed_out = true;
+            break;
+        }
         int k = 0;
         for (; k < P.m; ++k) {
             cplx<TV>* Vk = P.Vb + (size_t)k * bstride;
@@ -883,7 +891,8 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             DD_CUDA(cudaStreamSynchronize(st));
             int na = 0;
             for (int r = 0; r < nr; ++r) na += kb.h_active[r];
-            if (na == 0 || total >= P.maxiter) {
+            if (na > 0 && P.has_deadline && std::chrono::steady_clock::now() >= P.deadline) R.timed_out = true;
+            if (na == 0 || total >= P.maxiter || R.timed_out) {
                 ++k;
                 break;
             }
@@ -912,7 +921,7 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             R.flags[r] |= kb.h_flags[r];
         }
         if (P.fixed && total >= P.maxiter) break;
-        if (R.nonfinite) break;
+        if (R.nonfinite || R.timed_out) break;
         ++ncycles;
         if (P.max_cycles > 0 && ncycles >= P.max_cycles) break;
         // restart: V0 = b - A x
@@ -1195,7 +1204,8 @@ static int ml_vcycle0(ddamg_handle* h, const cplx<T>* r, cplx<T>* x, int nrhs, i
 
 template <typename TZ, typename TV>
 static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int nrhs, double tol, bool x0_zero, KrylovResult& R,
-                   const int* enabled_host = nullptr, int max_cycles = 0) {
+                   const int* enabled_host = nullptr, int max_cycles = 0,
+                   const std::chrono::steady_clock::time_point* deadline = nullptr) {
     cudaStream_t st = h->stream;
     const size_t fld = (size_t)12 * h->V;
     const int m = h->p.n_kv;
@@ -1262,6 +1272,10 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     P.wB = sep ? h->ws_outer[4].as<cplx<double>>() : reinterpret_cast<cplx<double>*>(P.w);
     P.enabled_host = enabled_host;
     P.max_cycles = max_cycles;
+    if (deadline) {
+        P.has_deadline = true;
+        P.deadline = *deadline;
+    }
     if (std::is_same<TV, float>::value) {
         // refinement: FP32 cycles, each ended at cycle_tol relative reduction (or n_kv steps),
         // with the FP64 iterate updated and the FP64 true residual formed between cycles
@@ -1314,6 +1328,11 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
         return DDAMG_ERR_INVALID_ARG;
     }
     ddamg_handle* h = new ddamg_handle();
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        set_error("cudaGetDevice failed");
+        return DDAMG_ERR_CUDA;
+    }
     for (int m = 0; m < 4; ++m) {
         h->L[m] = lat->dims[m];
         h->b[m] = p.block[m];
@@ -1359,7 +1378,8 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             (rc = dalloc_n(&h->P16, V * 12 * N)))
             return fail(rc);
         h->tc = CoarseTC{h->Bh, h->Dh, h->d_bnbr, h->NB, (int)nc, Mt, Kta, Kth, Ktd};
-        if ((rc = dalloc_n(&h->Uaos16, V * 12)) || (rc = dalloc_n(&h->clov_aos16, V * 9)) || (rc = dalloc_n(&h->clovinv_aos16, V * 9)))
+        if (p.smoother_fp16 &&
+            ((rc = dalloc_n(&h->Uaos16, V * 12)) || (rc = dalloc_n(&h->clov_aos16, V * 9)) || (rc = dalloc_n(&h->clovinv_aos16, V * 9))))
             return fail(rc);
     } else if (h->single()) {
         if ((rc = dalloc_n(&h->P32, V * 12 * N)) || (rc = dalloc_n(&h->B32, (size_t)h->NB * 9 * nc * nc * 2)) ||
@@ -1380,7 +1400,7 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             (rc = clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream)) ||
             (rc = clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream)))
             return fail(rc);
-        if (h->half() && ((rc = links_to_aos16(h->U32, h->Uaos16, h->V, h->stream)) ||
+        if (h->half() && h->p.smoother_fp16 && ((rc = links_to_aos16(h->U32, h->Uaos16, h->V, h->stream)) ||
                           (rc = clover_to_aos16(h->clov32, h->clov_aos16, h->V, h->stream)) ||
                           (rc = clover_to_aos16(h->clovinv32, h->clovinv_aos16, h->V, h->stream))))
             return fail(rc);
@@ -1458,6 +1478,7 @@ void ddamg_default_params(ddamg_params* p) {
     p->outer = DDAMG_OUTER_REFINE;
     p->cycle_tol = 1e-5;
     p->setup_update = DDAMG_SETUP_DDALPHA;
+    p->smoother_fp16 = 1;
 }
 
 const char* ddamg_error_string(int s) {
@@ -1521,26 +1542,31 @@ int ddamg_get_vectors(const ddamg_handle* hc, double* V) {
     return fine_out<double>(h, h->V64, V, h->N);
 }
 
-static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, double tol, ddamg_stats* st) {
+// zero_guess: z is output only and the initial guess is 0 (the paper's choice): z is neither read
+// nor staged in, and no initial residual product is formed.
+static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, double tol, ddamg_stats* st, bool zero_guess = false) {
     DD_TRY(check_ready(h));
     if (!b || !z || nrhs < 1) {
         set_error("solve: null pointer or n_rhs < 1");
         return DDAMG_ERR_INVALID_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
+    const bool limited = h->p.time_limit_s > 0;
+    const auto deadline = t0 + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                   std::chrono::duration<double>(limited ? h->p.time_limit_s : 0.0));
     if (tol <= 0) tol = h->p.tol;
     const size_t fld = (size_t)12 * h->V;
     DD_TRY(h->ws_io[2].ensure(sizeof(cplx<double>) * fld * nrhs * 2));
     cplx<double>* bi = h->ws_io[2].as<cplx<double>>();
     cplx<double>* xi = bi + fld * nrhs;
     DD_TRY(fine_in<double>(h, b, nrhs, h->ws_io[0], bi));
-    DD_TRY(fine_in<double>(h, z, nrhs, h->ws_io[0], xi));
+    if (!zero_guess) DD_TRY(fine_in<double>(h, z, nrhs, h->ws_io[0], xi));
     h->coarse_iters = 0;
     h->vcycles = 0;
     h->coarse_seconds = 0;
     // a zero initial guess (the paper's choice) needs no initial residual product
-    bool x0_zero = false;
-    {
+    bool x0_zero = zero_guess;
+    if (!zero_guess) {
         DD_TRY(h->ko.alloc(std::max(nrhs, h->ko.nrhs), std::max(1, h->p.n_kv)));
         DD_TRY((multidot<double, double>(xi, 0, fld, 1, xi, fld, fld, nrhs, h->ko.nrm, 1, h->ko.dscr, h->stream)));
         std::vector<cplx<double>> zn(nrhs);
@@ -1551,17 +1577,19 @@ static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, d
             if (zn[r].re != 0.0) x0_zero = false;
     }
     KrylovResult R;
-    int rc = !h->single() ? solve_T<double, double>(h, bi, xi, nrhs, tol, x0_zero, R)
-             : h->p.outer == DDAMG_OUTER_REFINE ? solve_T<float, float>(h, bi, xi, nrhs, tol, x0_zero, R)
-                                                : solve_T<float, dwf>(h, bi, xi, nrhs, tol, x0_zero, R);
+    const auto* dl = limited ? &deadline : nullptr;
+    int rc = !h->single() ? solve_T<double, double>(h, bi, xi, nrhs, tol, x0_zero, R, nullptr, 0, dl)
+             : h->p.outer == DDAMG_OUTER_REFINE ? solve_T<float, float>(h, bi, xi, nrhs, tol, x0_zero, R, nullptr, 0, dl)
+                                                : solve_T<float, dwf>(h, bi, xi, nrhs, tol, x0_zero, R, nullptr, 0, dl);
     if (rc) return rc;
     DD_TRY(fine_out<double>(h, xi, z, nrhs));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int status = 0;
+    const int unconverged = R.timed_out ? DDAMG_ERR_TIMEOUT : DDAMG_ERR_NOT_CONVERGED;
     if (R.nonfinite) status = DDAMG_ERR_NONFINITE;
     else {
         for (int r = 0; r < nrhs; ++r)
-            if (!(R.resid[r] <= tol)) status = DDAMG_ERR_NOT_CONVERGED;
+            if (!(R.resid[r] <= tol)) status = unconverged;
     }
     if (st) {
         for (int r = 0; r < nrhs; ++r) {
@@ -1572,10 +1600,12 @@ static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, d
             st[r].rel_residual = R.resid[r];
             st[r].solve_seconds = secs;
             st[r].coarse_seconds = h->coarse_seconds;
-            st[r].status = (R.nonfinite ? DDAMG_ERR_NONFINITE : (R.resid[r] <= tol ? 0 : DDAMG_ERR_NOT_CONVERGED));
+            st[r].status = (R.nonfinite ? DDAMG_ERR_NONFINITE : (R.resid[r] <= tol ? 0 : unconverged));
         }
     }
     if (status == DDAMG_ERR_NOT_CONVERGED) set_error("iteration cap reached before the tolerance");
+    if (status == DDAMG_ERR_TIMEOUT)
+        set_error("time limit of " + std::to_string(h->p.time_limit_s) + " s reached before the tolerance (z holds the last iterate)");
     if (status == DDAMG_ERR_NONFINITE) set_error("non-finite residual");
     return status;
 }
@@ -1584,6 +1614,10 @@ int ddamg_solve(ddamg_handle* h, const double* b, double* z, double tol, ddamg_s
 
 int ddamg_solve_batch(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st) {
     return solve_common(h, b, z, n_rhs, tol, st);
+}
+
+int ddamg_solve_batch_zero_guess(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st) {
+    return solve_common(h, b, z, n_rhs, tol, st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -1858,10 +1892,10 @@ static int apply_Dc_scratch_T(ddamg_handle* h, const double* in, double* out, in
     cplx<T>* o = a + cn * n_rhs;
     DD_TRY((coarse_perm<T, double>(reinterpret_cast<const cplx<double>*>(in), a, h->d_clex_of, h->NB, h->nc, n_rhs, 1, h->stream)));
     DD_TRY(c_full<T>(h, a, o, n_rhs));
-    DD_TRY((coarse_perm<double, T>(o, reinterpret_cast<cplx<double>*>(out), h->d_clex_of, h->NB, h->nc, n_rhs, 0, h->stream)));
-    DD_CUDA(cudaStreamSynchronize(h->stream));
-    return 0;
+    return coarse_perm<double, T>(o, reinterpret_cast<cplx<double>*>(out), h->d_clex_of, h->NB, h->nc, n_rhs, 0, h->stream);
 }
+
+int handle_device(const ddamg_handle* h) { return h ? h->device : -1; }
 
 int apply_Dc_into_scratch(ddamg_handle* h, const double* in, double* out, int n_rhs, void* scratch, size_t scratch_bytes) {
     DD_TRY(check_ready(h));
@@ -1967,7 +2001,7 @@ int ddamg_set_mass(ddamg_handle* h, double m0) {
         DD_TRY(launch_to_dw(h->clov64, h->clovdw, (size_t)h->V * 72, h->stream));
         DD_TRY(clover_to_aos(h->clov32, h->clov_aos, h->V, h->stream));
         DD_TRY(clover_to_aos(h->clovinv32, h->clovinv_aos, h->V, h->stream));
-        if (h->half()) {
+        if (h->half() && h->p.smoother_fp16) {
             DD_TRY(clover_to_aos16(h->clov32, h->clov_aos16, h->V, h->stream));
             DD_TRY(clover_to_aos16(h->clovinv32, h->clovinv_aos16, h->V, h->stream));
         }

@@ -24,6 +24,7 @@ PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OUTER_DW, OUTER_REFINE = 0, 1
 SETUP_DDALPHA, SETUP_IDSETUP = 0, 1
 SLOT_FREE, SLOT_RUNNING, SLOT_DONE, SLOT_FAILED = 0, 1, 2, 3
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_READY, ERR_RANK = 0, -1, -2, -3, -4, -5, -6, -7, -8
 
 STATUS = {
     0: "OK",
@@ -68,6 +69,7 @@ class Params(C.Structure):
         ("outer", C.c_int),
         ("cycle_tol", C.c_double),
         ("setup_update", C.c_int),
+        ("smoother_fp16", C.c_int),
     ]
 
 
@@ -128,6 +130,7 @@ def _load():
         "ddamg_get_vectors": (I, [P, P]),
         "ddamg_solve": (I, [P, P, P, D, C.POINTER(Stats)]),
         "ddamg_solve_batch": (I, [P, P, P, I, D, C.POINTER(Stats)]),
+        "ddamg_solve_batch_zero_guess": (I, [P, P, P, I, D, C.POINTER(Stats)]),
         "ddamg_apply_D": (I, [P, P, P, I]),
         "ddamg_apply_D_f32": (I, [P, P, P, I]),
         "ddamg_apply_D_mixed": (I, [P, P, P, I]),
@@ -304,7 +307,18 @@ class Solver:
             z[...] = 0
         st = (Stats * nr)()
         rc = lib.ddamg_solve_batch(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
-        _check(rc, "ddamg_solve_batch", allow=(-4, -5) if allow_fail else ())
+        _check(rc, "ddamg_solve_batch", allow=(-4, -5, -6) if allow_fail else ())
+        return z, [s.as_dict() for s in st], rc
+
+    def solve_zero_guess(self, b, z=None, tol: float = 0.0, allow_fail: bool = False):
+        """Solve D z = b from the zero initial guess; z (optional) is output only and never read."""
+        b = _host(b, np.complex128)
+        nr = 1 if b.ndim == 3 else int(b.shape[0])
+        if z is None:
+            z = _empty_like(b, b.shape, np.complex128)
+        st = (Stats * nr)()
+        rc = lib.ddamg_solve_batch_zero_guess(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
+        _check(rc, "ddamg_solve_batch_zero_guess", allow=(-4, -5, -6) if allow_fail else ())
         return z, [s.as_dict() for s in st], rc
 
     # -- recursion to a third level ------------------------------------------------
@@ -471,8 +485,26 @@ class Solver:
         return self._coarse_op(lib.ddamg_apply_Dc, e)
 
     def apply_Dc_noalloc(self, e_dev, out_dev):
-        """D_c e without any allocation in the library: e_dev, out_dev are device tensors
-        [n_rhs, n_coarse, 2N] complex128; the library's fixed scratch array is used."""
+        """D_c e without any allocation in the library: e_dev, out_dev are contiguous CUDA tensors of
+        dtype complex128 and equal shape [n_rhs, n_coarse, 2N] (or [n_coarse, 2N]) on one device;
+        the library's fixed scratch array is used.  The call is ordered on the handle's stream and
+        does not wait for it."""
+        import torch
+
+        for name, t in (("e_dev", e_dev), ("out_dev", out_dev)):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda:
+                raise ValueError(f"apply_Dc_noalloc: {name} must be a CUDA tensor")
+            if t.dtype != torch.complex128:
+                raise ValueError(f"apply_Dc_noalloc: {name} must be complex128, got {t.dtype}")
+            if t.ndim not in (2, 3) or tuple(t.shape[-2:]) != (self.n_coarse, self.coarse_dof):
+                raise ValueError(f"apply_Dc_noalloc: {name} must have shape [n_rhs, {self.n_coarse}, {self.coarse_dof}], "
+                                 f"got {tuple(t.shape)}")
+            if not t.is_contiguous():
+                raise ValueError(f"apply_Dc_noalloc: {name} must be contiguous")
+        if tuple(out_dev.shape) != tuple(e_dev.shape):
+            raise ValueError(f"apply_Dc_noalloc: out_dev shape {tuple(out_dev.shape)} differs from e_dev {tuple(e_dev.shape)}")
+        if out_dev.device != e_dev.device:
+            raise ValueError("apply_Dc_noalloc: e_dev and out_dev are on different devices")
         nr = 1 if e_dev.ndim == 2 else int(e_dev.shape[0])
         return _check(lib.ddamg_apply_Dc_noalloc(self.h, _ptr(e_dev), _ptr(out_dev), nr), "ddamg_apply_Dc_noalloc")
 

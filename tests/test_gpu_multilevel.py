@@ -1,20 +1,16 @@
 """The three-level path of the CUDA library (ddamg_ml_*) against the oracle's multilevel recursion.
 
-Not yet run on a GPU: the module runs only with DDAMG_ML_GPU=1, so its first GPU run is a
-deliberate single call rather than part of an unattended suite.  The level-1 functors it drives are
-checked on the host in tests/test_ml_host.py.
+The level-1 functors it drives are also checked on the host in tests/test_ml_host.py.
 
 Case: 8^4 fine lattice, 2^4 blocks, N = 4 -> level 1 = 4^4 coarse sites of 8 components; level-1
 blocks 2^4, N_1 = 3 -> level 2 = 2^4 sites of 6 components.  DOUBLE precision throughout, so the
-stated tolerances are rounding-level (1e-12 for single applications, 1e-9 where a Krylov solve to
-1e-14 or a fixed number of FGMRES steps sits inside)."""
-import os
-
+stated tolerances are rounding-level: 1e-13 for single applications, 1e-9 where a tolerance-stopped
+Krylov solve (to 1e-14, whose step count can differ by one between the two sides) sits inside; FP32
+applications 1e-6."""
 import numpy as np
 import pytest
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("DDAMG_ML_GPU") != "1", reason="three-level GPU path: first run pending")]
+pytestmark = pytest.mark.gpu
 
 from oracle.dirac import DiracOperator  # noqa: E402
 from oracle.mg import Params as OParams  # noqa: E402
@@ -67,11 +63,11 @@ def test_level1_pieces(case):
     l1 = ml.levels[1]
     with case["gpu"]() as s:
         x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=114)
-        assert rel(s.ml_restrict1(x), np.stack([l1.agg.restrict(x[r]) for r in range(2)])) < 1e-12
+        assert rel(s.ml_restrict1(x), np.stack([l1.agg.restrict(x[r]) for r in range(2)])) < 1e-13
         e = synth.gaussian_coarse(2 ** 4, 2 * N1, 2, seed=115)
-        assert rel(s.ml_prolong1(e), np.stack([l1.agg.prolong(e[r]) for r in range(2)])) < 1e-12
-        assert rel(s.ml_apply_D2(e), np.stack([l1.Dc.apply(e[r]) for r in range(2)])) < 1e-12
-        assert rel(s.ml_apply_sap1(x, 2), np.stack([l1.sap.apply(x[r], 2) for r in range(2)])) < 1e-12
+        assert rel(s.ml_prolong1(e), np.stack([l1.agg.prolong(e[r]) for r in range(2)])) < 1e-13
+        assert rel(s.ml_apply_D2(e), np.stack([l1.Dc.apply(e[r]) for r in range(2)])) < 1e-13
+        assert rel(s.ml_apply_sap1(x, 2), np.stack([l1.sap.apply(x[r], 2) for r in range(2)])) < 1e-13
 
 
 def test_level1_vcycle(case):
@@ -160,7 +156,7 @@ def test_three_level_solve_mixed_precision(case, prec):
         s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2))
         x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=123)
         ref = case["oracle"]().levels[1].sap
-        assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < 2e-5
+        assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < 1e-6
         z, st, rc = s.ml_solve(b)
         counts = s.ml_counts()
     assert rc == 0

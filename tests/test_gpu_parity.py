@@ -1,9 +1,14 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances: FP64 operator applications 1e-13 relative (max-norm over the field
-relative to the field's max), FP32 1e-6 for single applications (2e-6 allowed
-for the Dslash, whose 8 hops each round), looser where an FP32 quantity is
-iterated (stated per test); solves to a true FP64 relative residual <= 1e-10.
+Tolerances (max-norm of the difference relative to the field's max): 1e-13 for
+every FP64 result and 1e-6 for every FP32 result, single applications and the
+iterated ones alike (SAP with MR steps, GMRES with a fixed step count, a
+V-cycle with a fixed coarse step count).  The oracle's own spread under one-ulp
+input perturbations (tests/golden/oracle_spread.json) is 2e-16..1e-15 (FP64)
+and 5e-8..1.2e-7 (FP32) for these quantities, so both bounds sit well above
+rounding yet far below any error of a wrong formula.  FP16-storage paths carry
+their stated tolerance per test; solves reach a true FP64 relative residual
+<= 1e-10.
 """
 import numpy as np
 import pytest
@@ -73,7 +78,7 @@ def test_dslash_fp64_fp32(name, dd):
     with c.solver(dd.PREC_SINGLE) as s:
         assert relerr(s.apply_D(x), ref) < 1e-13
         y32 = s.apply_D_f32(x.astype(np.complex64))
-        assert relerr(y32, ref) < 2e-6
+        assert relerr(y32, ref) < 1e-6
         # double-word path: exact FP32 input, FP64-accurate output
         x32 = x.astype(np.complex64)
         ref32 = np.stack([c.D.apply(x32[r].astype(np.complex128)) for r in range(6)])
@@ -88,9 +93,9 @@ def test_sap(name, nu, dd):
     b = synth.gaussian_spinors(c.dims, 2, seed=104)
     ref = np.stack([sap.apply(b[r], nu) for r in range(2)])
     with c.solver(dd.PREC_DOUBLE) as s:
-        assert relerr(s.apply_sap(b, nu), ref) < 1e-12
+        assert relerr(s.apply_sap(b, nu), ref) < 1e-13
     with c.solver(dd.PREC_SINGLE) as s:
-        assert relerr(s.apply_sap(b, nu), ref) < 2e-5  # FP32, iterated MR steps
+        assert relerr(s.apply_sap(b, nu), ref) < 1e-6
 
 
 def test_sap_four_rhs_lanes_with_partial_group(dd):
@@ -101,7 +106,7 @@ def test_sap_four_rhs_lanes_with_partial_group(dd):
     b = synth.gaussian_spinors(c.dims, 5, seed=114)
     ref = np.stack([sap.apply(b[r], 2) for r in range(5)])
     with c.solver(dd.PREC_SINGLE) as s:
-        assert relerr(s.apply_sap(b, 2), ref) < 2e-5
+        assert relerr(s.apply_sap(b, 2), ref) < 1e-6
 
 
 def test_sap_half_mode_fp16_operator(dd):
@@ -132,10 +137,10 @@ def test_transfer_and_coarse_stencil(name, dd):
     ref_c = np.stack([Dc.apply(e[r]) for r in range(2)])
     with c.solver(dd.PREC_DOUBLE) as s:
         B = s.coarse_stencil()
-        assert relerr(B, Dc.B) < 1e-12
+        assert relerr(B, Dc.B) < 1e-13
         assert relerr(s.restrict(x), ref_r) < 1e-13
         assert relerr(s.prolong(e), ref_p) < 1e-13
-        assert relerr(s.apply_Dc(e), ref_c) < 1e-12
+        assert relerr(s.apply_Dc(e), ref_c) < 1e-13
     with c.solver(dd.PREC_SINGLE) as s:
         assert relerr(s.restrict(x), ref_r) < 1e-6
         assert relerr(s.prolong(e), ref_p) < 1e-6
@@ -151,9 +156,9 @@ def test_coarse_solve_fixed_iterations(name, dd):
     for k in (3, 12, 35):  # 35 crosses a restart
         ref = np.stack([cs.solve(e[r], fixed_iters=k) for r in range(2)])
         with c.solver(dd.PREC_DOUBLE) as s:
-            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-10
+            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-13
         with c.solver(dd.PREC_SINGLE) as s:
-            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 2e-4  # FP32 Krylov recurrence
+            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-6
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -163,9 +168,32 @@ def test_vcycle_fixed_coarse_iterations(name, dd):
     r = synth.gaussian_spinors(c.dims, 2, seed=108)
     ref = np.stack([mg.vcycle(r[q], coarse_fixed_iters=10) for q in range(2)])
     with c.solver(dd.PREC_DOUBLE) as s:
-        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-10
+        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-13
     with c.solver(dd.PREC_SINGLE) as s:
-        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-4
+        assert relerr(s.vcycle(r, coarse_fixed_iters=10), ref) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("DOUBLE", 1e-13), ("SINGLE", 1e-6), ("HALF", 4e-3)])
+def test_headline_instance_transfers_and_coarse_stencil(prec, tol, dd):
+    """The kernel instances of the 32^3 x 64 benchmark on a lattice the oracle handles: 4^4 aggregates,
+    N = 20 (40 x 40 coarse blocks), 12 right-hand sides in one call (HALF: the tensor-core stencil with
+    12 right-hand sides, the tensor-core restriction and prolongation), element by element against
+    the oracle.  HALF keeps P, D_c and the fine operand of the restriction in FP16 (2^-11 relative
+    rounding per stored entry), stated tolerance 4e-3 relative to the field maximum."""
+    dims, block, N, nr = (8, 8, 8, 8), (4, 4, 4, 4), 20, 12
+    U = synth.gauge_field(dims, 0.5, seed=131)
+    D = DiracOperator(U, dims, -0.5, CSW)
+    v = synth.random_test_vectors(dims, N, seed=132)
+    agg = Aggregation(D.lat, block, v)
+    Dc = CoarseOperator(D, agg)
+    x = synth.gaussian_spinors(dims, nr, seed=133)
+    e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, nr, seed=134)
+    p = dd.default_params(n_vec=N, block=block, precision=getattr(dd, "PREC_" + prec))
+    with dd.Solver(dims, U, -0.5, CSW, p, setup=False) as s:
+        s.setup_from_vectors(v)
+        assert relerr(s.apply_Dc(e), np.stack([Dc.apply(e[r]) for r in range(nr)])) < tol
+        assert relerr(s.restrict(x), np.stack([agg.restrict(x[r]) for r in range(nr)])) < tol
+        assert relerr(s.prolong(e), np.stack([agg.prolong(e[r]) for r in range(nr)])) < tol
 
 
 def test_half_precision_operators(dd):
@@ -222,13 +250,23 @@ def test_gpu_setup_matches_oracle(prec, update, tol, dd):
     assert relerr(got, ref) < tol
 
 
-@pytest.mark.parametrize("prec", ["DOUBLE", "SINGLE", "HALF"])
-def test_gpu_setup_solve_8x8x8x8(prec, dd):
+def _config1_m0():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1303_1377_gb300", "workloads.json")
+    return float(json.load(open(path))["lattice_8x8x8x8"]["m0"])
+
+
+@pytest.mark.parametrize("prec,m0", [("DOUBLE", "tuned"), ("DOUBLE", 0.02), ("SINGLE", 0.02), ("HALF", 0.02)])
+def test_gpu_setup_solve_8x8x8x8(prec, m0, dd):
     """The 8^4 workload (aggregates 4^4, N = 20, nu = 3): GPU adaptive setup + solve;
-    the returned solution has FP64 relative residual <= 1e-10 under the oracle's D."""
+    the returned solution has FP64 relative residual <= 1e-10 under the oracle's D.  "tuned" is the
+    configuration's own mass, m0 = -Re lambda_L + 1e-3 (smallest |eig| of D about 1e-3, from the
+    oracle's ARPACK run recorded in workloads.json), solved all in FP64."""
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, 0.4, seed=1)
-    m0 = 0.02
+    m0 = _config1_m0() if m0 == "tuned" else m0
     D = DiracOperator(U, dims, m0, CSW)
     p = dd.default_params(nu=3, precision=getattr(dd, "PREC_" + prec))
     b = synth.gaussian_spinors(dims, 1, seed=2)
@@ -285,7 +323,7 @@ def test_full_size_dslash_sampled(dd):
     sites = np.concatenate([sites, [0, np.prod(dims) - 1]])
     ref = apply_at_sites(U, dims, m0, CSW, x[0], sites)
     assert relerr(y[0][sites], ref) < 1e-13
-    assert relerr(y32[0][sites], ref) < 2e-6
+    assert relerr(y32[0][sites], ref) < 1e-6
     a = np.vdot(x[0], gamma5_field(y[1]))
     b = np.conj(np.vdot(x[1], gamma5_field(y[0])))
     assert abs(a - b) < 1e-11 * abs(a)
@@ -304,9 +342,9 @@ def test_set_mass_reuses_interpolation(prec, dd):
     x = synth.gaussian_spinors(c.dims, 2, seed=112)
     with c.solver(getattr(dd, "PREC_" + prec)) as s:
         s.set_mass(m1)
-        assert relerr(s.coarse_stencil(), Dc1.B) < 1e-12
+        assert relerr(s.coarse_stencil(), Dc1.B) < 1e-13
         assert relerr(s.apply_D(x), np.stack([D1.apply(x[r]) for r in range(2)])) < 1e-13
-        tol = {"DOUBLE": 1e-12, "SINGLE": 1e-6, "HALF": 4e-3}[prec]
+        tol = {"DOUBLE": 1e-13, "SINGLE": 1e-6, "HALF": 4e-3}[prec]
         assert relerr(s.apply_Dc(e), np.stack([Dc1.apply(e[r]) for r in range(2)])) < tol
         z, st, rc = s.solve(x)
         assert rc == 0
@@ -325,7 +363,7 @@ def test_n_vec_24_coarse_blocks_48(dd):
     e = synth.gaussian_coarse(agg.blk.nblocks, agg.nc, 3, seed=123)
     ref = np.stack([Dc.apply(e[r]) for r in range(3)])
     b = synth.gaussian_spinors(dims, 2, seed=124)
-    for prec, tol in (("DOUBLE", 1e-12), ("SINGLE", 1e-6), ("HALF", 4e-3)):
+    for prec, tol in (("DOUBLE", 1e-13), ("SINGLE", 1e-6), ("HALF", 4e-3)):
         p = dd.default_params(n_vec=N, block=block, precision=getattr(dd, "PREC_" + prec))
         with dd.Solver(dims, U, 0.1, CSW, p, setup=False) as s:
             s.setup_from_vectors(v)
@@ -405,3 +443,26 @@ def test_error_statuses(dd):
         with pytest.raises(dd.DDAMGError) as e:
             s3.setup_from_vectors(v)
         assert e.value.status == -8
+
+
+def test_zero_guess_entry_and_time_limit(dd):
+    """ddamg_solve_batch_zero_guess never reads z (NaN on entry) and returns the solve from the zero
+    guess; params.time_limit_s: a limit already passed at the first check returns TIMEOUT with a
+    finite iterate, a generous one changes nothing."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 2, seed=119)
+    with c.solver(dd.PREC_SINGLE) as s:
+        z0, st0, rc0 = s.solve(b)
+        z1, st1, rc1 = s.solve_zero_guess(b, z=np.full_like(b, np.nan))
+    assert rc0 == 0 and rc1 == 0
+    assert np.all(np.isfinite(z1))
+    assert relerr(z1, z0) <= 1e-14
+    assert [q["iterations"] for q in st1] == [q["iterations"] for q in st0]
+    with c.solver(dd.PREC_SINGLE, time_limit_s=1e-9) as s:
+        z, st, rc = s.solve(b, allow_fail=True)
+    assert rc == dd.ERR_TIMEOUT and all(q["status"] == dd.ERR_TIMEOUT for q in st)
+    assert np.all(np.isfinite(z)) and all(q["rel_residual"] > 1e-10 for q in st)
+    assert "time limit" in dd.lib.ddamg_last_error().decode()
+    with c.solver(dd.PREC_SINGLE, time_limit_s=600.0) as s:
+        z2, st2, rc2 = s.solve_zero_guess(b)
+    assert rc2 == 0 and relerr(z2, z0) <= 1e-14

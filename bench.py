@@ -345,7 +345,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="run each hot kernel once on --dims (for ncu) and exit")
     ap.add_argument("--dims", default="24,24,24,24", help="with --profile-case: the lattice")
     ap.add_argument("--nrhs", type=int, default=12, help="with --profile-case: right-hand sides")
-    ap.add_argument("--m0", type=float, default=None, help="with --profile-case: the mass (default -0.93)")
+    ap.add_argument("--m0", type=float, default=None,
+                    help="override the workload's mass (with --profile-case: the mass, default -0.93)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
@@ -368,6 +369,8 @@ def main():
 
         dist.init_process_group("nccl")
     m0, _ = workload_m0(w)
+    if args.m0 is not None:
+        m0 = args.m0
     dims = w["dims"]
     V = int(np.prod(dims))
     t = time.perf_counter()
@@ -465,8 +468,20 @@ def main():
             e2e_step()
         e2e_s = time.perf_counter() - t0
         nbytes = bh.nbytes
+        # the host link alone: one pinned-memory copy of b in each direction, timed with CUDA events
+        dev = torch.empty_like(bhost, device="cuda")
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record()
+        dev.copy_(bhost, non_blocking=True)
+        c1.record()
+        zhost.copy_(dev, non_blocking=True)
+        c2.record()
+        torch.cuda.synchronize()
+        link = {"h2d_gbs": nbytes / c0.elapsed_time(c1) / 1e6, "d2h_gbs": nbytes / c1.elapsed_time(c2) / 1e6}
+        del dev
         e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": (1 if zero_guess else 2) * nbytes,
-               "d2h_bytes_per_step": nbytes, "entry": "ddamg_solve_batch_zero_guess" if zero_guess else "ddamg_ml_solve"}
+               "d2h_bytes_per_step": nbytes, "entry": "ddamg_solve_batch_zero_guess" if zero_guess else "ddamg_ml_solve",
+               "host_link_copy": link}
     # roofline of the dominant kernel: HBM-bound families against the measured copy bandwidth;
     # families whose algorithmic flops per byte exceed the FP32 ridge against the FP32 FMA peak
     # (SMs x 128 FP32 lanes x 2 flops x the maximum SM clock)

@@ -220,6 +220,12 @@ def _ptr(a):
     if _is_torch(a):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if a.is_cuda:
+            # the library works on its own stream: work that torch has queued on the tensor (on torch's
+            # current stream) must be complete before the library reads or writes it
+            import torch
+
+            torch.cuda.current_stream(a.device).synchronize()
         return C.c_void_p(a.data_ptr())
     if not a.flags["C_CONTIGUOUS"]:
         raise ValueError("array must be C-contiguous")

@@ -33,19 +33,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # lattice (L0 = time first), gauge eps/seed, right-hand sides, method parameters
-    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, m0_key="lattice_32x32x32x64"),
-    "16x16x16x16": dict(dims=(16, 16, 16, 16), eps=0.5, seed=1, nrhs=12, rhs="point", N=20, nu=2, m0_key="lattice_16x16x16x16"),
-    "8x8x8x8": dict(dims=(8, 8, 8, 8), eps=0.4, seed=1, nrhs=1, rhs="gaussian", N=20, nu=3, m0_key="lattice_8x8x8x8"),
+    # lattice (L0 = time first), gauge eps/seed, right-hand sides, method parameters, default V-cycle
+    # precision; m0_key: the mass record in workloads.json; oracle_m0_key: the mass of the 8^4
+    # counterpart that the CPU baseline times (the 8^4 lattice's own near-critical mass for the
+    # near-critical workloads)
+    # headline: near-critical mass from the lattice's own spectral edge (smallest |eig| ~ 1e-3)
+    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, precision="half",
+                        m0_key="lattice_32x32x32x64_critical", oracle_m0_key="lattice_8x8x8x8_eps0.5"),
+    # the same lattice at m0 = -0.9319 (smallest |eig| ~ 0.063: an easier system)
+    "32x32x32x64-m0.932": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, precision="half",
+                               m0_key="lattice_32x32x32x64", oracle_m0_key="lattice_32x32x32x64"),
+    # FP32 V-cycle, one Gaussian right-hand side, near-critical (the Dslash / SAP profile case)
+    "16x16x16x16": dict(dims=(16, 16, 16, 16), eps=0.5, seed=1, nrhs=1, rhs="gaussian", N=20, nu=2, precision="single",
+                        m0_key="lattice_16x16x16x16_critical", oracle_m0_key="lattice_8x8x8x8_eps0.5", oracle_seed=3,
+                        count_key="32x32x32x64"),
+    # the oracle's size, all FP64, nu = 3, smallest |eig| ~ 1e-3
+    "8x8x8x8": dict(dims=(8, 8, 8, 8), eps=0.4, seed=1, nrhs=1, rhs="gaussian", N=20, nu=3, precision="double",
+                    m0_key="lattice_8x8x8x8", oracle_m0_key="lattice_8x8x8x8"),
 }
 C_SW = 1.0
 WORKLOADS_JSON = os.path.join(ROOT, "paper_1303_1377_gb300", "workloads.json")
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
-def workload_m0(w):
+def workload_m0(w, key="m0_key"):
     data = json.load(open(WORKLOADS_JSON))
-    return float(data[w["m0_key"]]["m0"]), data[w["m0_key"]]
+    return float(data[w[key]]["m0"]), data[w[key]]
 
 
 def peaks():
@@ -121,15 +134,21 @@ class ClockSampler:
 
 
 def metric_name(workload):
-    if workload == "32x32x32x64":
+    if workload.startswith("32x32x32x64"):
         return "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)"
     return f"solves/s to rel. residual 1e-10 ({workload})"
 
 
 def workload_description(workload, w, m0):
     """The workload as both arms state it in config.workload."""
+    rec = json.load(open(WORKLOADS_JSON)).get(w["m0_key"], {})
+    lam = rec.get("lambda_L_m0_0") or rec.get("lambda_L_source")
+    edge = ""
+    if lam:
+        src = "measured on this lattice" if rec.get("source") else f"of {rec.get('derived_from', 'a smaller lattice')}"
+        edge = f" (leftmost eigenvalue of D(0) {lam[0]:.5f}{lam[1]:+.4f}i {src}: smallest |eig| of D ~ {abs(complex(lam[0] + m0, lam[1])):.1e})"
     return (f"{workload} lattice (L0={w['dims'][0]}), SU(3) links exp(i eps H) eps={w['eps']} seed={w['seed']}, c_sw={C_SW}, "
-            f"m0={m0:.6f}, {w['nrhs']} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
+            f"m0={m0:.6f}{edge}, {w['nrhs']} {w['rhs']} sources per step, N_v={w['N']}, 4^4 SAP blocks and aggregates, nu={w['nu']}, "
             f"MR(4), FGMRES(25) tol 1e-10, coarse GMRES(30) tol 5e-2")
 
 
@@ -159,7 +178,7 @@ def _oracle_build(w, m0):
     from paper_1303_1377_gb300 import synth
 
     sdims = (8, 8, 8, 8)
-    U = synth.gauge_field(sdims, w["eps"], w["seed"])
+    U = synth.gauge_field(sdims, w["eps"], w.get("oracle_seed", w["seed"]))
     D = DiracOperator(U, sdims, m0, C_SW)
     mg = TwoLevel(D, OParams(N=w["N"], nu=w["nu"]), vectors=synth.random_test_vectors(sdims, w["N"], seed=w["seed"] + 7))
     b = np.zeros((D.V, 4, 3), dtype=np.complex128)
@@ -198,7 +217,7 @@ class OracleBaseline:
     def __init__(self, w, m0, fgmres_iters_per_solve, cores=None):
         import multiprocessing as mp
 
-        self.w, self.iters_per_solve = w, fgmres_iters_per_solve
+        self.w, self.iters_per_solve, self.m0 = w, fgmres_iters_per_solve, m0
         self.cores = cores or host_cores()
         os.environ["OPENBLAS_NUM_THREADS"] = os.environ["OMP_NUM_THREADS"] = "1"  # one thread per worker
         self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_build, initargs=(w, m0))
@@ -210,10 +229,12 @@ class OracleBaseline:
         value = rate / scale / self.iters_per_solve
         n_it = sum(i for i, _ in res)
         info = (f"{n_it} oracle FGMRES iterations (one point source each, {self.cores} single-threaded worker processes, "
-                f"{seconds_budget:.0f} s each) on the 8^4 version of the workload (same eps, c_sw, m0, N_v={self.w['N']}, 4^4 blocks, "
-                f"nu={self.w['nu']}; P from seeded random vectors): {rate:.2f} iterations/s in aggregate, divided by the volume ratio "
-                f"{scale:.0f} and by {self.iters_per_solve} FGMRES iterations per solve (the oracle's own count on the 8^4 counterpart "
-                f"with the adaptive setup); an extrapolation, not a run at the workload's size")
+                f"{seconds_budget:.0f} s each) on the 8^4 version of the workload (same eps, c_sw, N_v={self.w['N']}, 4^4 blocks, "
+                f"seed={self.w.get('oracle_seed', self.w['seed'])}, "
+                f"nu={self.w['nu']}, m0={self.m0:.6f}; P from seeded random vectors): {rate:.2f} iterations/s in aggregate, "
+                f"divided by {self.iters_per_solve} FGMRES iterations per solve (the oracle's own count on that 8^4 lattice with "
+                f"the adaptive setup)" + (f" and by the volume ratio {scale:.0f}: an extrapolation to the workload's size, not a run "
+                                          f"at it" if scale != 1 else ": a run at the workload's size"))
         return value, info
 
     def close(self):
@@ -224,7 +245,7 @@ class OracleBaseline:
 def oracle_iterations(workload):
     """FGMRES iterations per solve of the oracle's full method (adaptive setup) on the workload's
     8^4 counterpart, as recorded by oracle/count_iterations.py."""
-    rec = json.load(open(WORKLOADS_JSON)).get("fgmres_iterations_8x8x8x8", {}).get(workload)
+    rec = json.load(open(WORKLOADS_JSON)).get("fgmres_iterations_8x8x8x8", {}).get(WORKLOADS[workload].get("count_key", workload))
     if not rec:
         return None, None
     return int(rec["iterations"]), f"oracle, 8^4 counterpart with the adaptive setup: {rec['iterations']} iterations"
@@ -236,12 +257,13 @@ def run_reference(args, w):
         return 0
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     m0, _ = workload_m0(w)
+    m0_oracle, _ = workload_m0(w, "oracle_m0_key")
     iters_per_solve, src = oracle_iterations(args.workload)
     if iters_per_solve is None:
         print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration count for {args.workload}: "
                           f"run python -m oracle.count_iterations for it"}), flush=True)
         return 0
-    base = OracleBaseline(w, m0, iters_per_solve)
+    base = OracleBaseline(w, m0_oracle, iters_per_solve)
     vals = []
     for k in range(args.warmup + args.steps):
         v, info = base.sample(4.0)
@@ -329,8 +351,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32x32x32x64", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="half", choices=["single", "half", "half32", "double"],
-                    help="V-cycle precision; half32 = half with the smoother's links and site terms kept in FP32")
+    ap.add_argument("--precision", default=None, choices=["single", "half", "half32", "double"],
+                    help="V-cycle precision (default: the workload's); half32 = half with the smoother's links and site terms "
+                         "kept in FP32")
     ap.add_argument("--outer", default="refine", choices=["refine", "dw"],
                     help="outer scheme of the mixed-precision modes: FP32 cycles + FP64 residual correction, or double-word FGMRES")
     ap.add_argument("--cycle-tol", type=float, default=1e-5)
@@ -349,8 +372,10 @@ def main():
                     help="override the workload's mass (with --profile-case: the mass, default -0.93)")
     args = ap.parse_args()
     if args.profile_case:
+        args.precision = args.precision or "half"
         return run_profile_case(args)
     w = WORKLOADS[args.workload]
+    args.precision = args.precision or w["precision"]
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -516,7 +541,8 @@ def main():
         "metric": metric_name(args.workload),
         "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "double": "f64"}[args.precision], "data": "synthetic",
+        "dtype": {"single": "f32+f64", "half": "f16-storage/f32+f64", "half32": "f16-storage/f32+f64",
+                  "double": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": workload_description(args.workload, w, m0),
                    "l2": "inputs larger than L2 (b: %.1f GB)" % (bh.nbytes / 1e9), "precision": args.precision, "levels": args.levels, **({"ml_inner": args.ml_inner} if args.levels == 3 else {}),
                    "outer": (f"FP32 FGMRES cycles to {args.cycle_tol:g} + FP64 residual correction" if args.outer == "refine"
@@ -571,7 +597,7 @@ def main():
         plain.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         n_or, _ = oracle_iterations(args.workload)
-        base = OracleBaseline(w, m0, n_or if n_or else max(iters))
+        base = OracleBaseline(w, workload_m0(w, "oracle_m0_key")[0], n_or if n_or else max(iters))
         v, info = base.sample(12.0)
         base.close()
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": base.cores, "kind": "oracle", "sample": info}

@@ -128,51 +128,114 @@ struct CVecT {
     int site0;
 };
 
+// ---------------------------------------------------------------------------
+// bulk copies by the TMA engine (cp.async.bulk, global -> shared) completing on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // make the initialised barrier visible to the copy engine
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of bar, giving up after about a second (returns false then)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (int n = 0; n < (1 << 20); ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(256);
+    }
+    return false;
+}
+
 // One CTA per coarse site, warp w owns m-tile w (rows 16w..16w+15 of [Re; Im]).
 //   acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)]; self = 0 / B_0 xself / xself;
 //   out = apply_inv ? Dinv acc : acc       (same modes as the CUDA-core kernel)
+// The site's FP16 matrix (the k-tiles this call uses, and D_ee^{-1} when applied) is brought into
+// shared memory by bulk copies issued first, so that HBM streams it while the CTA gathers the
+// right-hand sides of the neighbouring sites (L2 hits) and converts them to FP16.
 template <int NRP>
-__global__ void coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode, float hop_sign,
-                                 int apply_inv, CVecT<float> out, int nrhs) {
+__global__ void __launch_bounds__(256, 2) coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode,
+                                                          float hop_sign, int apply_inv, CVecT<float> out, int nrhs) {
     constexpr int NT = NRP / 4;  // n-tiles of 8 columns over [Re X | Im X] (2 NRP columns)
-    extern __shared__ unsigned char smem_raw[];
-    const int nc = op.nc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = op.nc, Mt = op.Mt;
     const int Kp = op.Kt_all * 16;
-    const int LDX = Kp + 8;                                             // halves per staged column (bank offset)
-    __half* XT = reinterpret_cast<__half*>(smem_raw);                   // [2 NRP][LDX]
-    float* Cs = reinterpret_cast<float*>(XT + (size_t)2 * NRP * LDX);   // [2nc][2 NRP]
+    const int LDX = Kp + 8;  // halves per staged column (bank offset)
+    const bool hops = hop_sign != 0.f;
+    const int kt0 = hops ? 0 : op.Kt_hops;
+    const int kt1 = self_mode == 1 ? op.Kt_all : op.Kt_hops;
+    const int nkt = kt1 - kt0;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+    int* snb = reinterpret_cast<int*>(smem_raw + 8);                       // [8] neighbouring sites
+    uint4* As = reinterpret_cast<uint4*>(smem_raw + 64);                    // [Mt][nkt][32]
+    uint4* Ds = As + (size_t)Mt * nkt * 32;                                 // [Mt][Kt_d][32]
+    __half* XT = reinterpret_cast<__half*>(Ds + (apply_inv ? (size_t)Mt * op.Kt_d * 32 : 0));  // [2 NRP][LDX]
+    float* Cs = reinterpret_cast<float*>(XT + (size_t)2 * NRP * LDX);      // [2nc][2 NRP]
     cplx<float>* Vs = reinterpret_cast<cplx<float>*>(Cs + (size_t)2 * nc * 2 * NRP);  // [nc][NRP]
     const int c = site_begin + blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const bool hops = hop_sign != 0.f;
-    // 1. stage [Re X | Im X]^T for the used K range
-    for (int q = threadIdx.x; q < NRP * Kp; q += blockDim.x) {
-        int kk = q % Kp, r = q / Kp;
-        cplx<float> v = czero<float>();
-        if (r < nrhs) {
-            if (kk < 8 * nc) {
-                if (hops) {
-                    int d = 1 + kk / nc, col = kk % nc;
-                    int n = __ldg(op.cnbr + (d - 1) * op.NB + c);
-                    v = hop_sign * xin.p[r * xin.rstride + (size_t)(n - xin.site0) * nc + col];
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x < 8) snb[threadIdx.x] = __ldg(op.cnbr + threadIdx.x * op.NB + c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned abytes = (unsigned)nkt * 512u, dbytes = apply_inv ? (unsigned)(Mt * op.Kt_d) * 512u : 0u;
+        mbar_arrive_expect_tx(bar, abytes * Mt + dbytes);
+        if (abytes)
+            for (int m = 0; m < Mt; ++m)
+                bulk_g2s(As + (size_t)m * nkt * 32, op.Bh + (((size_t)c * Mt + m) * op.Kt_all + kt0) * 32, abytes, bar);
+        if (dbytes) bulk_g2s(Ds, op.Dh + ((size_t)c * Mt * op.Kt_d) * 32, dbytes, bar);
+    }
+    // 1. stage [Re X | Im X]^T for the used K range, two complex entries (one float4) at a time
+    {
+        const int k0 = kt0 * 16, kw = nkt * 16, kh = kw / 2;
+        for (int q = threadIdx.x; q < NRP * kh; q += blockDim.x) {
+            const int kk = k0 + 2 * (q % kh), r = q / kh;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < nrhs) {
+                if (kk < 8 * nc) {
+                    const int d = kk / nc, col = kk - d * nc;  // nc even: kk, kk + 1 share the direction
+                    v = __ldg(reinterpret_cast<const float4*>(xin.p + r * xin.rstride + (size_t)(snb[d] - xin.site0) * nc + col));
+                    v.x *= hop_sign, v.y *= hop_sign, v.z *= hop_sign, v.w *= hop_sign;
+                } else if (kk < 9 * nc && self_mode == 1) {
+                    v = __ldg(reinterpret_cast<const float4*>(xself.p + r * xself.rstride + (size_t)(c - xself.site0) * nc + (kk - 8 * nc)));
                 }
-            } else if (kk < 9 * nc && self_mode == 1) {
-                v = xself.p[r * xself.rstride + (size_t)(c - xself.site0) * nc + (kk - 8 * nc)];
             }
+            *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = __floats2half2_rn(v.x, v.z);
+            *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = __floats2half2_rn(v.y, v.w);
         }
-        XT[(size_t)r * LDX + kk] = __float2half_rn(v.re);
-        XT[(size_t)(NRP + r) * LDX + kk] = __float2half_rn(v.im);
     }
     __syncthreads();
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!ok)) {  // the copy never completed: flag it, let it drain, leave
+        if (threadIdx.x == 0) {
+            atomicExch(op.err, 1);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
     float acc[NT][4];
 #pragma unroll
     for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const int kt0 = hops ? 0 : op.Kt_hops;
-    const int kt1 = self_mode == 1 ? op.Kt_all : op.Kt_hops;
-    const uint4* Ab = op.Bh + (((size_t)c * op.Mt + w) * op.Kt_all) * 32 + lane;
+    const uint4* Ab = As + (size_t)w * nkt * 32 + lane;
 #pragma unroll 4
     for (int kt = kt0; kt < kt1; ++kt) {
-        uint4 a = __ldg(Ab + (size_t)kt * 32);
+        const uint4 a = Ab[(size_t)(kt - kt0) * 32];
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
             const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
@@ -214,9 +277,9 @@ __global__ void coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, 
         __syncthreads();
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-        const uint4* Db = op.Dh + (((size_t)c * op.Mt + w) * op.Kt_d) * 32 + lane;
+        const uint4* Db = Ds + (size_t)w * op.Kt_d * 32 + lane;
         for (int kt = 0; kt < op.Kt_d; ++kt) {
-            uint4 a = __ldg(Db + (size_t)kt * 32);
+            const uint4 a = Db[(size_t)kt * 32];
 #pragma unroll
             for (int n = 0; n < NT; ++n) {
                 const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
@@ -241,15 +304,22 @@ __global__ void coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, 
     }
 }
 
+// dynamic shared memory of coarse_tc_kernel<NRP> for one call
+static size_t tc_smem(const CoarseTC& op, int nrp, int self_mode, float hop_sign, int apply_inv) {
+    const int Kp = op.Kt_all * 16;
+    const int nkt = (self_mode == 1 ? op.Kt_all : op.Kt_hops) - (hop_sign != 0.f ? 0 : op.Kt_hops);
+    return 64 + (size_t)op.Mt * (nkt + (apply_inv ? op.Kt_d : 0)) * 512 + (size_t)2 * nrp * (Kp + 8) * sizeof(__half) +
+           (size_t)2 * op.nc * 2 * nrp * sizeof(float) + (size_t)op.nc * nrp * sizeof(cplx<float>);
+}
+constexpr size_t kTcSmemMax = 227 * 1024;
+
 template <int NRP>
 static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<float> xin, CVecT<float> xself, int self_mode,
                          float hop_sign, int apply_inv, CVecT<float> out, int nrhs, cudaStream_t st) {
-    const int Kp = op.Kt_all * 16;
-    size_t smem = (size_t)2 * NRP * (Kp + 8) * sizeof(__half) + (size_t)2 * op.nc * 2 * NRP * sizeof(float) +
-                  (size_t)op.nc * NRP * sizeof(cplx<float>);
+    const size_t smem = tc_smem(op, NRP, self_mode, hop_sign, apply_inv);
     // set once per kernel instance (a function-local static initialiser is thread safe)
     static const bool attr = [] {
-        cudaFuncSetAttribute(coarse_tc_kernel<NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(coarse_tc_kernel<NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
         return true;
     }();
     (void)attr;
@@ -260,8 +330,16 @@ static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<f
 
 static int launch_tc(const CoarseTC& op, int site_begin, int nsites, CVecT<float> xin, CVecT<float> xself, int self_mode,
                      float hop_sign, int apply_inv, CVecT<float> out, int nrhs, cudaStream_t st) {
+    // right-hand sides per launch: up to 24, fewer where the site's matrix and the staged vectors
+    // would not fit in shared memory
+    int cap = 24;
+    while (cap > 4 && tc_smem(op, cap, self_mode, hop_sign, apply_inv) > kTcSmemMax) cap = cap > 16 ? 16 : cap > 12 ? 12 : cap - 4;
+    if (tc_smem(op, 4, self_mode, hop_sign, apply_inv) > kTcSmemMax) {
+        set_error("coarse stencil: the per-site FP16 matrix does not fit in shared memory (2N too large for half precision)");
+        return DDAMG_ERR_INVALID_ARG;
+    }
     while (nrhs > 0) {
-        int n = nrhs > 24 ? 24 : nrhs;
+        int n = nrhs > cap ? cap : nrhs;
         int rc;
         if (n <= 4) rc = launch_tc_nrp<4>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);
         else if (n <= 8) rc = launch_tc_nrp<8>(op, site_begin, nsites, xin, xself, self_mode, hop_sign, apply_inv, out, n, st);

@@ -122,8 +122,10 @@ struct Geom {
     int Vb;      // sites per block
     int NB;      // blocks = coarse sites
     int vb_shift;  // log2(Vb) when Vb is a power of two, else -1
+    int blk44;     // 1 when the blocks are 4^4 (the specialised SAP kernel applies)
     const int* lnbr;  // [8][Vb]: local index of the neighbour | (crosses block) << 16
     const int* bnbr;  // [8][NB]: neighbouring block
+    const int* blex;  // [NB]: internal index of the block of lexicographic index q (traversal order)
 };
 
 __device__ __forceinline__ int block_of(const Geom& g, int i) {

@@ -19,6 +19,80 @@ namespace ddamg {
 // restricted to its two 2x2 chiral blocks: [plane][half][s][t] (re, im)
 __constant__ double c_gg[6][2][2][2][2];
 
+// ---------------------------------------------------------------------------
+// 4^4 blocks.  Local order of a block (common.cuh): parity p (even first), then rank = lex >> 1
+// among the sites of that parity, lex = ((y0 * 4 + y1) * 4 + y2) * 4 + y3.  Neighbours follow from
+// the in-block lexicographic index and the (warp-uniform) neighbouring blocks, with no table load
+// per site.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lex44_of_local(int l) {
+    const int p = l >> 7, k = l & 127, row = k >> 1;  // row = y0 * 16 + y1 * 4 + y2
+    const int q = __popc(row & 0x15) & 1;             // parity of y0 + y1 + y2
+    return 4 * row + ((p ^ q) & 1) + 2 * (k & 1);     // y3 = (p - q) mod 2 + 2 (k mod 2)
+}
+// global index of the neighbour of local site (lex L, parity p) of block c in direction MU,
+// forward or backward; bn = the neighbouring block in that direction
+template <int MU, bool FWD>
+__device__ __forceinline__ int nbr44(int L, int p, int c, int bn) {
+    constexpr int SH = 2 * (3 - MU), S = 1 << SH;
+    const int y = (L >> SH) & 3;
+    const bool cross = FWD ? y == 3 : y == 0;
+    const int L2 = FWD ? (cross ? L - 3 * S : L + S) : (cross ? L + 3 * S : L - S);
+    return (cross ? bn : c) * 256 + (((p ^ 1) << 7) | (L2 >> 1));
+}
+
+template <int MU, typename T, typename Ts, typename UT>
+__device__ __forceinline__ void hop_pair_nb(const UT& U, const cplx<Ts>* __restrict__ in, int V, int i, int f, int bk, Spinor<T>& acc) {
+    cplx<T> W[9];
+    Spinor<T> pn;
+    load_link(W, U, V, MU, i);
+    load_spinor(pn, in, V, f);
+    hop_acc<MU, true>(acc, pn, W);
+    load_link(W, U, V, MU, bk);
+    load_spinor(pn, in, V, bk);
+    hop_acc<MU, false>(acc, pn, W);
+}
+
+// out = D in (RESID: out = b - D in) on 4^4 blocks.  CTA = 32 sites of one block x ry right-hand
+// sides (one warp per right-hand side, sharing the links and site terms through L1).  The CTAs walk
+// the blocks in lexicographic block order, red and black interleaved, so that a block and its
+// neighbours in three of the four directions are read close together in time and the neighbours'
+// spinors are still in L2.
+template <typename T, typename Ts, bool RESID>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 384 : 128, sizeof(T) == 4 ? 2 : 1)
+    dslash44_kernel(Geom g, FineOp<T> op, const int* __restrict__ blex, const cplx<Ts>* __restrict__ in, const cplx<T>* __restrict__ b,
+                    cplx<T>* __restrict__ out, int nrhs) {
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int q = blockIdx.x >> 3;
+    const int l = (blockIdx.x & 7) * 32 + threadIdx.x;
+    if (r >= nrhs) return;
+    const int c = __ldg(blex + q);
+    const int i = c * 256 + l;
+    const int L = lex44_of_local(l), p = l >> 7;
+    int bn[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) bn[d] = __ldg(g.bnbr + d * g.NB + c);
+    const size_t off = (size_t)r * 12 * g.V;
+    const cplx<Ts>* inr = in + off;
+    Spinor<T> acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    hop_pair_nb<0>(op.U, inr, g.V, i, nbr44<0, true>(L, p, c, bn[0]), nbr44<0, false>(L, p, c, bn[1]), acc);
+    hop_pair_nb<1>(op.U, inr, g.V, i, nbr44<1, true>(L, p, c, bn[2]), nbr44<1, false>(L, p, c, bn[3]), acc);
+    hop_pair_nb<2>(op.U, inr, g.V, i, nbr44<2, true>(L, p, c, bn[4]), nbr44<2, false>(L, p, c, bn[5]), acc);
+    hop_pair_nb<3>(op.U, inr, g.V, i, nbr44<3, true>(L, p, c, bn[6]), nbr44<3, false>(L, p, c, bn[7]), acc);
+    Spinor<T> x, y;
+    load_spinor(x, inr, g.V, i);
+    herm_apply(op.clov, g.V, i, x, y);
+    cplx<T>* o = out + off;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        cplx<T> d = y.v[k] - T(0.5) * acc.v[k];
+        if (RESID) d = b[off + (size_t)k * g.V + i] - d;
+        o[(size_t)k * g.V + i] = d;
+    }
+}
+
 template <int MU, typename T, typename Ts, typename UT>
 __device__ __forceinline__ void hop_pair(const Geom& g, const UT& U, const cplx<Ts>* __restrict__ in, int i, Spinor<T>& acc) {
     cplx<T> W[9];
@@ -68,6 +142,15 @@ template <typename T, typename Ts>
 int launch_dslash(const Geom& g, const FineOp<T>& op, const cplx<Ts>* in, const cplx<T>* b, cplx<T>* out, int nrhs,
                   cudaStream_t st) {
     const int ry = std::min(nrhs, sizeof(T) == 4 ? 12 : 4);  // right-hand sides per CTA
+    if (g.blk44 && g.blex) {
+        const dim3 grid((unsigned)g.NB * 8, (unsigned)ceil_div(nrhs, ry)), block(32, ry);
+        if (b)
+            dslash44_kernel<T, Ts, true><<<grid, block, 0, st>>>(g, op, g.blex, in, b, out, nrhs);
+        else
+            dslash44_kernel<T, Ts, false><<<grid, block, 0, st>>>(g, op, g.blex, in, b, out, nrhs);
+        DD_CHECK_LAUNCH();
+        return 0;
+    }
     const dim3 grid((unsigned)ceil_div(g.V, 32), (unsigned)ceil_div(nrhs, ry)), block(32, ry);
     if (b)
         dslash_kernel<T, Ts, true><<<grid, block, 0, st>>>(g, op, in, b, out, nrhs);
@@ -435,6 +518,213 @@ __global__ void __launch_bounds__(128 * R, (R == 1 ? 4 : 1)) sap_colour_lean_ker
     }
 }
 
+// ---------------------------------------------------------------------------
+// SAP block solve specialised to 4^4 blocks (H = 128 sites per parity) with four right-hand sides
+// in adjacent lanes.  Same algorithm and shared-memory state as sap_colour_lean_kernel; what the
+// fixed block shape buys:
+//  - in-block neighbours are computed from the site's lexicographic index inside the block, so a
+//    hop's shared-memory read and link load wait on no table load;
+//  - the MR step size is summed by one warp from the per-warp partials and broadcast through
+//    shared memory, instead of every thread summing all partials.
+// ---------------------------------------------------------------------------
+// in-block hops in direction MU of a site with in-block lexicographic index L; sm holds the field
+// on the neighbours' parity, indexed by rank; nb0 = global index of local site 0 of that parity.
+template <int MU, typename T, typename UT>
+__device__ __forceinline__ void hop_pair44(const UT& U, const cplx<T>* sm, int L, int nb0, int i, Spinor<T>& acc) {
+    constexpr int SH = 2 * (3 - MU), S = 1 << SH;
+    const int c = (L >> SH) & 3;
+    cplx<T> W[9];
+    Spinor<T> pn;
+    if (c < 3) {
+        const int n = (L + S) >> 1;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pn.v[k] = sm[k * 128 + n];
+        load_link(W, U, 0, MU, i);
+        hop_acc<MU, true>(acc, pn, W);
+    }
+    if (c > 0) {
+        const int n = (L - S) >> 1;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pn.v[k] = sm[k * 128 + n];
+        load_link(W, U, 0, MU, nb0 + n);
+        hop_acc<MU, false>(acc, pn, W);
+    }
+}
+template <typename T, typename UT>
+__device__ __forceinline__ void hops44(const UT& U, const cplx<T>* sm, int L, int nb0, int i, Spinor<T>& acc) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    hop_pair44<0>(U, sm, L, nb0, i, acc);
+    hop_pair44<1>(U, sm, L, nb0, i, acc);
+    hop_pair44<2>(U, sm, L, nb0, i, acc);
+    hop_pair44<3>(U, sm, L, nb0, i, acc);
+}
+
+// full D at local site (lex L, parity p) of block c with z read from global memory (residual)
+template <typename T, typename OpT>
+__device__ __forceinline__ void site_D44(const Geom& g, const OpT& op, const cplx<T>* __restrict__ z, int c, int L, int p, int i,
+                                         const int (&bn)[8], Spinor<T>& out) {
+    Spinor<T> acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.v[k] = czero<T>();
+    hop_pair_nb<0>(op.U, z, g.V, i, nbr44<0, true>(L, p, c, bn[0]), nbr44<0, false>(L, p, c, bn[1]), acc);
+    hop_pair_nb<1>(op.U, z, g.V, i, nbr44<1, true>(L, p, c, bn[2]), nbr44<1, false>(L, p, c, bn[3]), acc);
+    hop_pair_nb<2>(op.U, z, g.V, i, nbr44<2, true>(L, p, c, bn[4]), nbr44<2, false>(L, p, c, bn[5]), acc);
+    hop_pair_nb<3>(op.U, z, g.V, i, nbr44<3, true>(L, p, c, bn[6]), nbr44<3, false>(L, p, c, bn[7]), acc);
+    Spinor<T> x;
+    load_spinor(x, z, g.V, i);
+    herm_apply(op.clov, g.V, i, x, out);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out.v[k] = out.v[k] - T(0.5) * acc.v[k];
+}
+
+template <typename OpT>
+__global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cplx<float>* __restrict__ bsrc, cplx<float>* __restrict__ z,
+                                                       int colour, int nrhs, int mr_steps) {
+    using T = float;
+    constexpr int R = 4, H = 128, NW = 16;
+    extern __shared__ unsigned char smem_raw[];
+    const int slot = threadIdx.x % R;
+    const int t = threadIdx.x / R;
+    const int slot_stride = 36 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
+    cplx<T>* SE = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)slot * slot_stride;  // [12][H] even work vector
+    cplx<T>* SO = SE + 12 * H;                                                         // [12][H] rho
+    cplx<T>* SX = SO + 12 * H;                                                         // [12][H] x_o (first: r_o)
+    float4* red = reinterpret_cast<float4*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)R * slot_stride);  // [NW][R]
+    cplx<T>* salpha = reinterpret_cast<cplx<T>*>(red + NW * R);                                               // [R]
+    const int ngroups = (nrhs + R - 1) / R;
+    const int r = (blockIdx.x % ngroups) * R + slot;
+    const int blk = colour * (g.NB / 2) + blockIdx.x / ngroups;
+    const bool act = r < nrhs;
+    const int ie = blk * g.Vb + t, io = blk * g.Vb + H + t;
+    const int Le = lex44_of_local(t), Lo = lex44_of_local(H + t);
+    const int nb_even = blk * g.Vb, nb_odd = blk * g.Vb + H;  // global index of local site 0 of each parity
+    const size_t off = (size_t)(act ? r : 0) * 12 * g.V;
+    const cplx<T>* b = bsrc + off;
+    cplx<T>* zr = z + off;
+    {
+        int bn[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) bn[d] = __ldg(g.bnbr + d * g.NB + blk);
+        Spinor<T> tmp, tmp2;
+        if (act) {
+            site_D44(g, op, zr, blk, Le, 0, ie, bn, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) tmp.v[k] = b[(size_t)k * g.V + ie] - tmp.v[k];
+            herm_apply(op.clovinv, g.V, ie, tmp, tmp2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+            site_D44(g, op, zr, blk, Lo, 1, io, bn, tmp);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SX[k * H + t] = b[(size_t)k * g.V + io] - tmp.v[k];
+        }
+    }
+    __syncthreads();  // every read of z in this block is done: z may be updated from here on
+    if (act) {  // z_e += A_ee^{-1} r_e; rho = r_o - D_oe A_ee^{-1} r_e; x_o = 0
+#pragma unroll
+        for (int k = 0; k < 12; ++k) zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + SE[k * H + t];
+        Spinor<T> hs;
+        hops44(op.U, SE, Lo, nb_even, io, hs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            SO[k * H + t] = SX[k * H + t] + T(0.5) * hs.v[k];
+            SX[k * H + t] = czero<T>();
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < mr_steps; ++it) {
+        if (act) {  // even: SE = A_ee^{-1} D_eo rho
+            Spinor<T> hs, tmp2;
+            hops44(op.U, SO, Le, nb_odd, ie, hs);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) hs.v[k] = T(-0.5) * hs.v[k];
+            herm_apply(op.clovinv, g.V, ie, hs, tmp2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) SE[k * H + t] = tmp2.v[k];
+        }
+        __syncthreads();
+        T num_re = 0, num_im = 0, den = 0;
+        Spinor<T> sr;
+        if (act) {  // odd: S rho = A_oo rho + 1/2 hops(SE)
+            Spinor<T> rho, hs;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rho.v[k] = SO[k * H + t];
+            herm_apply(op.clov, g.V, io, rho, sr);
+            hops44(op.U, SE, Lo, nb_even, io, hs);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                sr.v[k] = sr.v[k] + T(0.5) * hs.v[k];
+                num_re += sr.v[k].re * rho.v[k].re + sr.v[k].im * rho.v[k].im;
+                num_im += sr.v[k].re * rho.v[k].im - sr.v[k].im * rho.v[k].re;
+                den += norm2(sr.v[k]);
+            }
+        }
+        // per-warp partial sums of each slot (lanes of equal slot), then warp 0 sums the warps
+#pragma unroll
+        for (int o = R; o < 32; o <<= 1) {
+            num_re += __shfl_xor_sync(0xffffffffu, num_re, o);
+            num_im += __shfl_xor_sync(0xffffffffu, num_im, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane < R) red[w * R + slot] = make_float4(num_re, num_im, den, 0.f);
+        __syncthreads();
+        if (w == 0) {  // lane = 4 q + slot (slot = lane % R): warps q and q + 8
+            const float4 a = red[lane], c = red[32 + lane];
+            float nr = a.x + c.x, ni = a.y + c.y, dd = a.z + c.z;
+#pragma unroll
+            for (int o = R; o < 32; o <<= 1) {
+                nr += __shfl_xor_sync(0xffffffffu, nr, o);
+                ni += __shfl_xor_sync(0xffffffffu, ni, o);
+                dd += __shfl_xor_sync(0xffffffffu, dd, o);
+            }
+            if (lane < R) salpha[lane] = dd > tiny_normal<T>() ? mk(nr / dd, ni / dd) : czero<T>();
+        }
+        __syncthreads();
+        if (act) {
+            const cplx<T> alpha = salpha[slot];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cplx<T> rv = SO[k * H + t];
+                cplx<T> xv = SX[k * H + t];
+                cmac(xv, alpha, rv);
+                SX[k * H + t] = xv;
+                SO[k * H + t] = rv - alpha * sr.v[k];
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {  // x_e = A_ee^{-1} (r_e - D_eo x_o); z += x
+        Spinor<T> hs, tmp2;
+        hops44(op.U, SX, Le, nb_odd, ie, hs);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) hs.v[k] = T(0.5) * hs.v[k];  // x_e = A_ee^{-1} r_e (added above) + A_ee^{-1} (1/2 hops x_o)
+        herm_apply(op.clovinv, g.V, ie, hs, tmp2);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + tmp2.v[k];
+            zr[(size_t)k * g.V + io] = zr[(size_t)k * g.V + io] + SX[k * H + t];
+        }
+    }
+}
+
+template <typename OpT>
+static int launch_sap44(const Geom& g, const OpT& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
+                        cudaStream_t st) {
+    constexpr int R = 4, H = 128, NW = 16;
+    const size_t smem = (size_t)R * (36 * H + 4) * sizeof(cplx<float>) + (size_t)NW * R * sizeof(float4) + R * sizeof(cplx<float>);
+    // set once per kernel instance (a function-local static initialiser is thread safe)
+    static const bool attr = [] {
+        cudaFuncSetAttribute(sap44_kernel<OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        return true;
+    }();
+    (void)attr;
+    const long long nblk = (long long)(g.NB / 2) * ((nrhs + R - 1) / R);
+    sap44_kernel<OpT><<<(unsigned)nblk, R * H, smem, st>>>(g, op, b, z, colour, nrhs, mr_steps);
+    DD_CHECK_LAUNCH();
+    return 0;
+}
+
 template <typename T, int R>
 static int launch_sap_r(const Geom& g, const FineOp<T>& op, const cplx<T>* b, cplx<T>* z, int colour, int nrhs, int mr_steps,
                         cudaStream_t st) {
@@ -489,7 +779,8 @@ bool sap_aos_supported(const Geom& g, int nrhs) {
 int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
                           cudaStream_t st) {
     const int H = g.Vb / 2;
-    if (nrhs >= 4 && H == 128) return launch_sap_lean<float, 4, FineOpAoS, 128>(g, op, b, z, colour, nrhs, mr_steps, st);  // 4^4 blocks
+    if (nrhs >= 4 && H == 128 && g.blk44) return launch_sap44(g, op, b, z, colour, nrhs, mr_steps, st);  // 4^4 blocks
+    if (nrhs >= 4 && H == 128) return launch_sap_lean<float, 4, FineOpAoS, 128>(g, op, b, z, colour, nrhs, mr_steps, st);
     if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<float, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
     if (H % 32 == 0) return launch_sap_lean<float, 1>(g, op, b, z, colour, nrhs, mr_steps, st);
     return -1;
@@ -498,6 +789,7 @@ int launch_sap_colour_aos(const Geom& g, const FineOpAoS& op, const cplx<float>*
 int launch_sap_colour_aos16(const Geom& g, const FineOpAoS16& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs,
                             int mr_steps, cudaStream_t st) {
     const int H = g.Vb / 2;
+    if (nrhs >= 4 && H == 128 && g.blk44) return launch_sap44(g, op, b, z, colour, nrhs, mr_steps, st);  // 4^4 blocks
     if (nrhs >= 4 && H == 128) return launch_sap_lean<float, 4, FineOpAoS16, 128>(g, op, b, z, colour, nrhs, mr_steps, st);
     if (nrhs >= 4 && (4 * H) % 32 == 0 && 4 * H <= 512) return launch_sap_lean<float, 4>(g, op, b, z, colour, nrhs, mr_steps, st);
     if (H % 32 == 0) return launch_sap_lean<float, 1>(g, op, b, z, colour, nrhs, mr_steps, st);

@@ -96,6 +96,7 @@ struct CoarseTC {
     const uint4* Dh;
     const int* cnbr;
     int NB, nc, Mt, Kt_all, Kt_hops, Kt_d;
+    int* err;  // set to 1 by a kernel whose bulk copy did not complete (read by the solve)
 };
 int tc_dims(int nc, int* Mt, int* Kt_all, int* Kt_hops, int* Kt_d);
 int pack_coarse_tc(const double* B64, const double* Dinv64, uint4* Bh, uint4* Dh, int NB, int nc, cudaStream_t st);

@@ -199,6 +199,7 @@ struct ddamg_handle {
     double m0, csw;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     std::vector<int> h_lex_of, h_clex_of;
+    int *d_blex = nullptr;
     int *d_lnbr = nullptr, *d_bnbr = nullptr, *d_lex_of = nullptr, *d_clex_of = nullptr, *d_sites = nullptr;
     int nsites[9];
     Geom g;
@@ -222,6 +223,7 @@ struct ddamg_handle {
     cplx<__half>* P16 = nullptr;          // half mode: FP16 interpolation
     CoarseTC tc{};
     int* d_flag = nullptr;
+    int* d_tc_err = nullptr;  // half mode: set by a coarse-stencil kernel whose bulk copy did not complete
     // workspaces
     Scratch ws_fine[6], ws_coarse[8], ws_io[3], ws_outer[5];
     Scratch ws_rmax;  // per right-hand-side field maxima of the tensor-core restriction
@@ -367,6 +369,8 @@ static int build_geometry(ddamg_handle* h) {
     DD_TRY(dalloc_n(&h->d_lex_of, h->h_lex_of.size()));
     DD_TRY(dalloc_n(&h->d_clex_of, h->h_clex_of.size()));
     DD_TRY(dalloc_n(&h->d_sites, sites.size()));
+    DD_TRY(dalloc_n(&h->d_blex, blex_to_int.size()));
+    DD_CUDA(cudaMemcpy(h->d_blex, blex_to_int.data(), blex_to_int.size() * 4, cudaMemcpyHostToDevice));
     DD_CUDA(cudaMemcpy(h->d_lnbr, lnbr.data(), lnbr.size() * 4, cudaMemcpyHostToDevice));
     DD_CUDA(cudaMemcpy(h->d_bnbr, bnbr.data(), bnbr.size() * 4, cudaMemcpyHostToDevice));
     DD_CUDA(cudaMemcpy(h->d_lex_of, h->h_lex_of.data(), h->h_lex_of.size() * 4, cudaMemcpyHostToDevice));
@@ -376,10 +380,12 @@ static int build_geometry(ddamg_handle* h) {
     h->g.Vb = vb;
     h->g.NB = nbt;
     h->g.vb_shift = -1;
+    h->g.blk44 = h->b[0] == 4 && h->b[1] == 4 && h->b[2] == 4 && h->b[3] == 4;
     for (int s = 0; s < 31; ++s)
         if ((1 << s) == vb) h->g.vb_shift = s;
     h->g.lnbr = h->d_lnbr;
     h->g.bnbr = h->d_bnbr;
+    h->g.blex = h->d_blex;
     return 0;
 }
 
@@ -1285,6 +1291,20 @@ static int solve_T(ddamg_handle* h, const cplx<double>* b, cplx<double>* x, int 
     return krylov<double, TV, TZ>(h, h->ko, P, R);
 }
 
+// half mode: a coarse-stencil kernel whose bulk copy of the site matrix never completed sets a
+// device flag (the kernel gives up after a bounded wait instead of hanging); report it as a CUDA error
+static int tc_check(ddamg_handle* h) {
+    if (!h->d_tc_err) return 0;
+    int f = 0;
+    DD_CUDA(cudaMemcpyAsync(&f, h->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    if (f) {
+        set_error("coarse stencil: a bulk copy of the site matrix did not complete within the kernel's wait limit");
+        return DDAMG_ERR_CUDA;
+    }
+    return 0;
+}
+
 static int check_ready(ddamg_handle* h) {
     if (!h) {
         set_error("null handle");
@@ -1377,7 +1397,9 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
         if ((rc = dalloc_n(&h->Bh, (size_t)h->NB * Mt * Kta * 32)) || (rc = dalloc_n(&h->Dh, (size_t)(h->NB / 2) * Mt * Ktd * 32)) ||
             (rc = dalloc_n(&h->P16, V * 12 * N)))
             return fail(rc);
-        h->tc = CoarseTC{h->Bh, h->Dh, h->d_bnbr, h->NB, (int)nc, Mt, Kta, Kth, Ktd};
+        if ((rc = dalloc_n(&h->d_tc_err, 1))) return fail(rc);
+        if (cudaMemset(h->d_tc_err, 0, sizeof(int)) != cudaSuccess) return fail(DDAMG_ERR_CUDA);
+        h->tc = CoarseTC{h->Bh, h->Dh, h->d_bnbr, h->NB, (int)nc, Mt, Kta, Kth, Ktd, h->d_tc_err};
         if (p.smoother_fp16 &&
             ((rc = dalloc_n(&h->Uaos16, V * 12)) || (rc = dalloc_n(&h->clov_aos16, V * 9)) || (rc = dalloc_n(&h->clovinv_aos16, V * 9))))
             return fail(rc);
@@ -1583,6 +1605,7 @@ static int solve_common(ddamg_handle* h, const double* b, double* z, int nrhs, d
                                                 : solve_T<float, dwf>(h, bi, xi, nrhs, tol, x0_zero, R, nullptr, 0, dl);
     if (rc) return rc;
     DD_TRY(fine_out<double>(h, xi, z, nrhs));
+    DD_TRY(tc_check(h));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int status = 0;
     const int unconverged = R.timed_out ? DDAMG_ERR_TIMEOUT : DDAMG_ERR_NOT_CONVERGED;
@@ -1828,7 +1851,8 @@ static int restrict_T(ddamg_handle* h, const double* in, double* out, int n_rhs)
     cplx<T>* o = a + fld * n_rhs;
     DD_TRY(fine_in<T>(h, in, n_rhs, h->ws_io[0], a));
     DD_TRY(restrict_<T>(h, a, o, n_rhs));
-    return coarse_out<T>(h, o, out, n_rhs);
+    DD_TRY(coarse_out<T>(h, o, out, n_rhs));
+    return tc_check(h);
 }
 
 extern "C" {
@@ -1872,7 +1896,8 @@ static int apply_Dc_T(ddamg_handle* h, const double* in, double* out, int n_rhs)
         Prof pr(h, PF_COARSE, (double)h->NB * 9 * h->nc * h->nc * sizeof(cplx<T>));
         DD_TRY(c_full<T>(h, a, o, n_rhs));
     }
-    return coarse_out<T>(h, o, out, n_rhs);
+    DD_TRY(coarse_out<T>(h, o, out, n_rhs));
+    return tc_check(h);
 }
 
 namespace ddamg {
@@ -1959,7 +1984,8 @@ static int coarse_solve_T(ddamg_handle* h, const double* in, double* out, int n_
     DD_TRY(coarse_in<T>(h, in, n_rhs, a));
     h->coarse_iters = 0;
     DD_TRY(coarse_solve<T>(h, a, o, n_rhs, fixed));
-    return coarse_out<T>(h, o, out, n_rhs);
+    DD_TRY(coarse_out<T>(h, o, out, n_rhs));
+    return tc_check(h);
 }
 
 extern "C" {
@@ -2098,6 +2124,7 @@ int ddamg_destroy(ddamg_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     ml_release(h);
     dfree(h->d_lnbr);
+    dfree(h->d_blex);
     dfree(h->d_bnbr);
     dfree(h->d_lex_of);
     dfree(h->d_clex_of);
@@ -2127,6 +2154,7 @@ int ddamg_destroy(ddamg_handle* h) {
     dfree(h->Dh);
     dfree(h->P16);
     dfree(h->d_flag);
+    dfree(h->d_tc_err);
     for (auto& s : h->ws_fine) s.release();
     for (auto& s : h->ws_coarse) s.release();
     for (auto& s : h->ws_io) s.release();

@@ -89,17 +89,25 @@ def edge(dims, eps, seed, shift, k=12, iters=20, res_tol=1e-4, solve_tol=1e-8, n
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--dims", required=True, help="L0,L1,L2,L3 (time first)")
-    ap.add_argument("--eps", type=float, required=True)
-    ap.add_argument("--seed", type=int, required=True)
-    ap.add_argument("--shift", type=float, required=True, help="mass m_s of the inverse iteration (D(m_s) must be nonsingular)")
+    ap.add_argument("--record", default=None, help="merge a record written by --out into workloads.json and exit")
+    ap.add_argument("--dims", help="L0,L1,L2,L3 (time first)")
+    ap.add_argument("--eps", type=float)
+    ap.add_argument("--seed", type=int)
+    ap.add_argument("--shift", type=float, help="mass m_s of the inverse iteration (D(m_s) must be nonsingular)")
     ap.add_argument("--gap", type=float, default=1e-3)
     ap.add_argument("--k", type=int, default=12)
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--out", default=None, help="also write the record (with its history) to this JSON file")
-    ap.add_argument("--name", required=True)
+    ap.add_argument("--name")
     ap.add_argument("--write", action="store_true", help="record the result in workloads.json")
     a = ap.parse_args()
+    if a.record:
+        data = json.load(open(WORKLOADS))
+        data.update(json.load(open(a.record)))
+        with open(WORKLOADS, "w") as f:
+            json.dump(data, f, indent=1)
+            f.write("\n")
+        return
     dims = tuple(int(v) for v in a.dims.split(","))
     r = edge(dims, a.eps, a.seed, a.shift, k=a.k, iters=a.iters)
     rec = {"dims": list(dims), "eps": a.eps, "seed": a.seed, "c_sw": 1.0, "m0": -r["lambda_L_m0_0"][0] + a.gap, "gap": a.gap,

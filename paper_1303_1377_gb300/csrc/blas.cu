@@ -517,10 +517,24 @@ int axpy_norm_dw(cplx<dwf>* w, const cplx<dwf>* A, size_t istride, size_t rstrid
 // ---------------------------------------------------------------------------
 constexpr int kFlush = 32;
 
+// The CTAs of one right-hand side leave their partial sums in `partial`; the last of them to finish
+// (counted by ticket[r]) adds them up in CTA order, so the result is the same as a separate
+// reduction launch (deterministic) without that launch.
+__device__ __forceinline__ bool last_cta_of_rhs(unsigned* ticket, int r, int ctas_per_rhs) {
+    __shared__ bool last;
+    __threadfence();  // every partial of this CTA is visible before the ticket is taken
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket + r, 1u) == (unsigned)ctas_per_rhs - 1u;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4* __restrict__ A, size_t istride4, size_t arstride4, int k,
                                                                    const float4* __restrict__ w, size_t wrstride4, size_t n4, int nrhs,
-                                                                   int ctas_per_rhs, double* __restrict__ partial,
+                                                                   int ctas_per_rhs, double* __restrict__ partial, unsigned* __restrict__ ticket,
+                                                                   cplx<double>* __restrict__ out, int ostride_i, cplx<double>* __restrict__ copy_last,
                                                                    const int* __restrict__ run_flag) {
     if (run_flag && !*run_flag) return;
     const int r = blockIdx.x % nrhs;
@@ -571,6 +585,18 @@ __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4*
         for (int ww = 0; ww < kDotThreads / 32; ++ww) s += red[ww][q];
         partial[((size_t)blockIdx.x) * 2 * k + q] = s;
     }
+    if (!last_cta_of_rhs(ticket, r, ctas_per_rhs)) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double re = 0, im = 0;
+        for (int p = 0; p < ctas_per_rhs; ++p) {
+            const double* src = partial + ((size_t)(p * nrhs + r)) * 2 * k;
+            re += __ldcg(src + 2 * i);
+            im += __ldcg(src + 2 * i + 1);
+        }
+        out[(size_t)i * ostride_i + r] = mk(re, im);
+        if (copy_last && i == k - 1) copy_last[r] = mk(re, im);
+    }
+    if (threadIdx.x == 0) ticket[r] = 0u;
 }
 
 static bool f32_layout_ok(const void* A, size_t istride, size_t arstride, const void* w, size_t wrstride, size_t n) {
@@ -578,55 +604,62 @@ static bool f32_layout_ok(const void* A, size_t istride, size_t arstride, const 
            ((uintptr_t)w & 15) == 0;
 }
 
+// CTAs per right-hand side of the FP32 basis kernels: about four resident CTAs per SM over all
+// right-hand sides, and at least 16 float4 per thread so the reduction is a small part of the work
+static int f32_ctas(size_t n4, int nrhs, int threads) {
+    long long by_work = (long long)(n4 / ((size_t)threads * 16));
+    long long target = 608 / nrhs;
+    long long c = std::min(by_work, target);
+    return (int)std::max(1LL, c);
+}
+
 int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, const cplx<float>* w, size_t wrstride, size_t n, int nrhs,
-                 cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st) {
+                 cplx<double>* out, int ostride_i, double* scratch, unsigned* ticket, cplx<double>* copy_last, const int* run_flag,
+                 cudaStream_t st) {
     if (!f32_layout_ok(A, istride, arstride, w, wrstride, n)) return -1;
     const size_t n4 = n / 2;
     int off = 0;
     while (off < k) {
         int kk = k - off;
         if (kk > 16) kk = 16;
-        int ctas = (int)((n4 + kDotThreads - 1) / kDotThreads);
-        int target = 1216 / nrhs;
-        if (target < 1) target = 1;
-        if (ctas > target) ctas = target;
+        const int ctas = f32_ctas(n4, nrhs, kDotThreads);
         const float4* Ab = reinterpret_cast<const float4*>(A + off * istride);
         const float4* w4 = reinterpret_cast<const float4*>(w);
         const unsigned grid = ctas * nrhs;
+        cplx<double>* o = out + (size_t)off * ostride_i;
+        cplx<double>* cl = off + kk == k ? copy_last : nullptr;
         if (kk <= 1)
-            multidot_f32_kernel<1><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+            multidot_f32_kernel<1><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch,
+                                                                 ticket, o, ostride_i, cl, run_flag);
         else if (kk <= 8)
-            multidot_f32_kernel<8><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
+            multidot_f32_kernel<8><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch,
+                                                                 ticket, o, ostride_i, cl, run_flag);
         else
-            multidot_f32_kernel<16><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch, run_flag);
-        DD_CHECK_LAUNCH();
-        multidot_finish<<<ceil_div((long long)nrhs * kk, 128), 128, 0, st>>>(scratch, kk, nrhs, ctas, out + (size_t)off * ostride_i,
-                                                                          ostride_i, run_flag);
+            multidot_f32_kernel<16><<<grid, kDotThreads, 0, st>>>(Ab, istride / 2, arstride / 2, kk, w4, wrstride / 2, n4, nrhs, ctas, scratch,
+                                                                  ticket, o, ostride_i, cl, run_flag);
         DD_CHECK_LAUNCH();
         off += kk;
     }
     return 0;
 }
 
-// coefficients alpha * coef[i][r] rounded to FP32
-__global__ void coef_to_f32_kernel(const cplx<double>* __restrict__ coef, int cstride_i, int k, int nrhs, double alpha,
-                                   float2* __restrict__ out, const int* __restrict__ run_flag) {
-    if (run_flag && !*run_flag) return;
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= k * nrhs) return;
-    int i = q / nrhs, r = q % nrhs;
-    cplx<double> c = coef[(size_t)i * cstride_i + r];
-    out[q] = make_float2((float)(alpha * c.re), (float)(alpha * c.im));
-}
-
-// w[r] += sum_i c[i][r] * A_i[r] in place (FP32), with ||w[r]||^2 of the result (FP64 sum)
+// w[r] += sum_i alpha c[i][r] * A_i[r] in place (FP32; the coefficients are rounded to FP32 in the
+// kernel), with ||w[r]||^2 of the result (FP64 sum) in norm_out[r].re
+constexpr int kAxpyMaxK = 64;
 __global__ void __launch_bounds__(kAxpyThreads) axpy_norm_f32_kernel(float4* __restrict__ wv, const float4* __restrict__ A, size_t istride4,
-                                                                     size_t rstride4, int k, const float2* __restrict__ cv, size_t n4,
-                                                                     int nrhs, int ctas_per_rhs, double* __restrict__ partial,
-                                                                     const int* __restrict__ run_flag) {
+                                                                     size_t rstride4, int k, const cplx<double>* __restrict__ coef,
+                                                                     int cstride_i, double alpha, size_t n4, int nrhs, int ctas_per_rhs,
+                                                                     double* __restrict__ partial, unsigned* __restrict__ ticket,
+                                                                     cplx<double>* __restrict__ norm_out, const int* __restrict__ run_flag) {
     if (run_flag && !*run_flag) return;
     const int r = blockIdx.x % nrhs;
     const int part = blockIdx.x / nrhs;
+    __shared__ float2 cs[kAxpyMaxK];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const cplx<double> c = coef[(size_t)i * cstride_i + r];
+        cs[i] = make_float2((float)(alpha * c.re), (float)(alpha * c.im));
+    }
+    __syncthreads();
     float4* wr = wv + r * rstride4;
     const float4* Ar = A + r * rstride4;
     double nrm = 0.0;
@@ -635,7 +668,7 @@ __global__ void __launch_bounds__(kAxpyThreads) axpy_norm_f32_kernel(float4* __r
         float4 acc = wr[e];
 #pragma unroll 4
         for (int i = 0; i < k; ++i) {
-            const float2 c = __ldg(cv + (size_t)i * nrhs + r);
+            const float2 c = cs[i];
             const float4 a = Ar[i * istride4 + e];
             acc.x = fmaf(c.x, a.x, fmaf(-c.y, a.y, acc.x));
             acc.y = fmaf(c.x, a.y, fmaf(c.y, a.x, acc.y));
@@ -652,26 +685,26 @@ __global__ void __launch_bounds__(kAxpyThreads) axpy_norm_f32_kernel(float4* __r
     if (threadIdx.x == 0) {
         double s = 0;
         for (int q = 0; q < kAxpyThreads / 32; ++q) s += red[q];
-        partial[blockIdx.x * 2] = s;
-        partial[blockIdx.x * 2 + 1] = 0.0;
+        partial[blockIdx.x] = s;
+    }
+    if (!last_cta_of_rhs(ticket, r, ctas_per_rhs)) return;
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int p = 0; p < ctas_per_rhs; ++p) s += __ldcg(partial + (size_t)p * nrhs + r);
+        norm_out[r] = mk(s, 0.0);
+        ticket[r] = 0u;
     }
 }
 
 int axpy_norm_f32(cplx<float>* w, const cplx<float>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
-                  size_t n, int nrhs, double alpha, float2* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                  size_t n, int nrhs, double alpha, double* scratch, unsigned* ticket, cplx<double>* norm_out, const int* run_flag,
                   cudaStream_t st) {
-    if (!f32_layout_ok(A, istride, rstride, w, rstride, n)) return -1;
-    coef_to_f32_kernel<<<ceil_div((long long)k * nrhs, 128), 128, 0, st>>>(coef, cstride_i, k, nrhs, alpha, coef_scratch, run_flag);
-    DD_CHECK_LAUNCH();
+    if (!f32_layout_ok(A, istride, rstride, w, rstride, n) || k > kAxpyMaxK) return -1;
     const size_t n4 = n / 2;
-    int ctas = (int)((n4 + kAxpyThreads - 1) / kAxpyThreads);
-    int target = 1216 / nrhs;
-    if (target < 1) target = 1;
-    if (ctas > target) ctas = target;
+    const int ctas = f32_ctas(n4, nrhs, kAxpyThreads);
     axpy_norm_f32_kernel<<<ctas * nrhs, kAxpyThreads, 0, st>>>(reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(A), istride / 2,
-                                                               rstride / 2, k, coef_scratch, n4, nrhs, ctas, scratch, run_flag);
-    DD_CHECK_LAUNCH();
-    multidot_finish<<<ceil_div((long long)nrhs, 128), 128, 0, st>>>(scratch, 1, nrhs, ctas, norm_out, nrhs, run_flag);
+                                                               rstride / 2, k, coef, cstride_i, alpha, n4, nrhs, ctas, scratch, ticket,
+                                                               norm_out, run_flag);
     DD_CHECK_LAUNCH();
     return 0;
 }

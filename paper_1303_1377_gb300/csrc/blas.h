@@ -45,11 +45,14 @@ int lincomb_dw(cplx<dwf>* out, size_t ors, int beta1, const cplx<dwf>* A, size_t
                int cstride_i, size_t n, int nrhs, double alpha, float4* coef_scratch, cudaStream_t st);
 int xupdate_dw(cplx<double>* x, const cplx<float>* Z, size_t istride, size_t n, int k, const cplx<double>* coef, int nrhs,
                float4* coef_scratch, cudaStream_t st);
-// FP32 basis (even n, 16-byte aligned vectors; -1 otherwise)
+// FP32 basis (even n, 16-byte aligned vectors; -1 otherwise).  ticket: nrhs zeroed counters (left
+// zeroed), used to let the last CTA of each right-hand side finish the reduction.  copy_last: also
+// receives the last of the k products (may be null).
 int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, const cplx<float>* w, size_t wrstride, size_t n, int nrhs,
-                 cplx<double>* out, int ostride_i, double* scratch, const int* run_flag, cudaStream_t st);
+                 cplx<double>* out, int ostride_i, double* scratch, unsigned* ticket, cplx<double>* copy_last, const int* run_flag,
+                 cudaStream_t st);
 int axpy_norm_f32(cplx<float>* w, const cplx<float>* A, size_t istride, size_t rstride, int k, const cplx<double>* coef, int cstride_i,
-                  size_t n, int nrhs, double alpha, float2* coef_scratch, double* scratch, cplx<double>* norm_out, const int* run_flag,
+                  size_t n, int nrhs, double alpha, double* scratch, unsigned* ticket, cplx<double>* norm_out, const int* run_flag,
                   cudaStream_t st);
 int scale_f32(cplx<float>* w, const cplx<double>* scale, size_t n, int nrhs, cudaStream_t st);
 int residual_f32(const cplx<double>* b, const cplx<double>* w, const cplx<float>* t, cplx<float>* out, size_t n, cudaStream_t st);

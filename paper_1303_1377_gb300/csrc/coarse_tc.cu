@@ -163,14 +163,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     return false;
 }
 
-// One CTA per coarse site, warp w owns m-tile w (rows 16w..16w+15 of [Re; Im]).
+// One CTA per coarse site with two warps per m-tile: warp w < Mt owns m-tile w (rows 16w..16w+15 of
+// [Re; Im]) in the tensor-core product; all 2 Mt warps gather and convert the right-hand sides and
+// write the result.
 //   acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)]; self = 0 / B_0 xself / xself;
 //   out = apply_inv ? Dinv acc : acc       (same modes as the CUDA-core kernel)
 // The site's FP16 matrix (the k-tiles this call uses, and D_ee^{-1} when applied) is brought into
 // shared memory by bulk copies issued first, so that HBM streams it while the CTA gathers the
 // right-hand sides of the neighbouring sites (L2 hits) and converts them to FP16.
 template <int NRP>
-__global__ void __launch_bounds__(256, 2) coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode,
+__global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode,
                                                           float hop_sign, int apply_inv, CVecT<float> out, int nrhs) {
     constexpr int NT = NRP / 4;  // n-tiles of 8 columns over [Re X | Im X] (2 NRP columns)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,23 +203,40 @@ __global__ void __launch_bounds__(256, 2) coarse_tc_kernel(CoarseTC op, int site
                 bulk_g2s(As + (size_t)m * nkt * 32, op.Bh + (((size_t)c * Mt + m) * op.Kt_all + kt0) * 32, abytes, bar);
         if (dbytes) bulk_g2s(Ds, op.Dh + ((size_t)c * Mt * op.Kt_d) * 32, dbytes, bar);
     }
-    // 1. stage [Re X | Im X]^T for the used K range, two complex entries (one float4) at a time
+    // 1. stage [Re X | Im X]^T for the used K range, two complex entries (one float4) at a time; the
+    //    loads of a batch are all issued before the first conversion, so their latencies overlap
     {
-        const int k0 = kt0 * 16, kw = nkt * 16, kh = kw / 2;
-        for (int q = threadIdx.x; q < NRP * kh; q += blockDim.x) {
-            const int kk = k0 + 2 * (q % kh), r = q / kh;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < nrhs) {
-                if (kk < 8 * nc) {
-                    const int d = kk / nc, col = kk - d * nc;  // nc even: kk, kk + 1 share the direction
-                    v = __ldg(reinterpret_cast<const float4*>(xin.p + r * xin.rstride + (size_t)(snb[d] - xin.site0) * nc + col));
-                    v.x *= hop_sign, v.y *= hop_sign, v.z *= hop_sign, v.w *= hop_sign;
-                } else if (kk < 9 * nc && self_mode == 1) {
-                    v = __ldg(reinterpret_cast<const float4*>(xself.p + r * xself.rstride + (size_t)(c - xself.site0) * nc + (kk - 8 * nc)));
+        constexpr int GB = 8;
+        const int k0 = kt0 * 16, kh = nkt * 8, tot = NRP * kh;
+        for (int q0 = 0; q0 < tot; q0 += GB * blockDim.x) {
+            float4 v[GB];
+#pragma unroll
+            for (int j = 0; j < GB; ++j) {
+                const int q = q0 + j * blockDim.x + threadIdx.x;
+                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < tot) {
+                    const int kk = k0 + 2 * (q % kh), r = q / kh;
+                    if (r < nrhs) {
+                        if (kk < 8 * nc) {
+                            const int d = kk / nc, col = kk - d * nc;  // nc even: kk, kk + 1 share the direction
+                            v[j] = __ldg(reinterpret_cast<const float4*>(xin.p + r * xin.rstride + (size_t)(snb[d] - xin.site0) * nc + col));
+                        } else if (kk < 9 * nc && self_mode == 1) {
+                            v[j] = __ldg(reinterpret_cast<const float4*>(xself.p + r * xself.rstride + (size_t)(c - xself.site0) * nc +
+                                                                         (kk - 8 * nc)));
+                        }
+                    }
                 }
             }
-            *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = __floats2half2_rn(v.x, v.z);
-            *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = __floats2half2_rn(v.y, v.w);
+#pragma unroll
+            for (int j = 0; j < GB; ++j) {
+                const int q = q0 + j * blockDim.x + threadIdx.x;
+                if (q < tot) {
+                    const int kk = k0 + 2 * (q % kh), r = q / kh;
+                    const float sg = kk < 8 * nc ? hop_sign : 1.f;
+                    *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = __floats2half2_rn(sg * v[j].x, sg * v[j].z);
+                    *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = __floats2half2_rn(sg * v[j].y, sg * v[j].w);
+                }
+            }
         }
     }
     __syncthreads();
@@ -232,20 +251,24 @@ __global__ void __launch_bounds__(256, 2) coarse_tc_kernel(CoarseTC op, int site
     float acc[NT][4];
 #pragma unroll
     for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const uint4* Ab = As + (size_t)w * nkt * 32 + lane;
+    const bool mma_warp = w < Mt;
+    if (mma_warp) {
+        const uint4* Ab = As + (size_t)w * nkt * 32 + lane;
 #pragma unroll 4
-    for (int kt = kt0; kt < kt1; ++kt) {
-        const uint4 a = Ab[(size_t)(kt - kt0) * 32];
+        for (int kt = kt0; kt < kt1; ++kt) {
+            const uint4 a = Ab[(size_t)(kt - kt0) * 32];
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
-            unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
-            unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
-            mma16816(acc[n], a, b0, b1);
+            for (int n = 0; n < NT; ++n) {
+                const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
+                unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
+                unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
+                mma16816(acc[n], a, b0, b1);
+            }
         }
     }
     // 2. recombine the planes into complex rows (+ identity self term)
     auto store_acc = [&]() {
+        if (!mma_warp) return;
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
             int r0 = w * 16 + g, col = n * 8 + 2 * t;
@@ -277,15 +300,17 @@ __global__ void __launch_bounds__(256, 2) coarse_tc_kernel(CoarseTC op, int site
         __syncthreads();
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-        const uint4* Db = Ds + (size_t)w * op.Kt_d * 32 + lane;
-        for (int kt = 0; kt < op.Kt_d; ++kt) {
-            const uint4 a = Db[(size_t)kt * 32];
+        if (mma_warp) {
+            const uint4* Db = Ds + (size_t)w * op.Kt_d * 32 + lane;
+            for (int kt = 0; kt < op.Kt_d; ++kt) {
+                const uint4 a = Db[(size_t)kt * 32];
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
-                unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
-                unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
-                mma16816(acc[n], a, b0, b1);
+                for (int n = 0; n < NT; ++n) {
+                    const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
+                    unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
+                    unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
+                    mma16816(acc[n], a, b0, b1);
+                }
             }
         }
         store_acc();
@@ -323,7 +348,7 @@ static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<f
         return true;
     }();
     (void)attr;
-    coarse_tc_kernel<NRP><<<nsites, 32 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
+    coarse_tc_kernel<NRP><<<nsites, 64 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;
 }

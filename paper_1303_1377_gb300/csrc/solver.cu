@@ -106,8 +106,11 @@ struct KrylovBufs {
     float4* coefdw = nullptr;       // [(m+2)][nrhs] double-word coefficients
     cplx<double>* nbefore = nullptr;  // [nrhs] ||w||^2 before orthogonalisation
     int* dflag = nullptr;             // device-side "second Gram-Schmidt pass" decision
+    unsigned* tickets = nullptr;      // [nrhs] last-CTA counters of the FP32 reductions (kept at zero between launches)
     double* dscr = nullptr;         // multidot scratch
     int* h_active = nullptr;        // pinned copy of active flags
+    int* h_active_lag[2] = {nullptr, nullptr};  // lagged convergence check: flags of steps k-1 and k
+    cudaEvent_t ev_lag[2] = {nullptr, nullptr};
     int* h_steps = nullptr;
     double* h_resid = nullptr;
     int* h_flags = nullptr;
@@ -139,12 +142,18 @@ struct KrylovBufs {
         DD_TRY(dalloc_n(&coefdw, (size_t)(mm + 2) * nr));
         DD_TRY(dalloc_n(&nbefore, nr));
         DD_TRY(dalloc_n(&dflag, 1));
+        DD_TRY(dalloc_n(&tickets, nr));
+        DD_CUDA(cudaMemset(tickets, 0, sizeof(unsigned) * nr));
         {
             std::vector<cplx<double>> one(nr, mk(1.0, 0.0));
             DD_CUDA(cudaMemcpy(ones, one.data(), sizeof(cplx<double>) * nr, cudaMemcpyHostToDevice));
         }
         DD_TRY(dalloc_n(&dscr, multidot_scratch_doubles(1) + multidot_scratch_doubles(nr)));
         DD_CUDA(cudaMallocHost(&h_active, sizeof(int) * nr));
+        for (int q = 0; q < 2; ++q) {
+            DD_CUDA(cudaMallocHost(&h_active_lag[q], sizeof(int) * nr));
+            DD_CUDA(cudaEventCreateWithFlags(&ev_lag[q], cudaEventDisableTiming));
+        }
         DD_CUDA(cudaMallocHost(&h_steps, sizeof(int) * nr));
         DD_CUDA(cudaMallocHost(&h_resid, sizeof(double) * nr));
         DD_CUDA(cudaMallocHost(&h_flags, sizeof(int) * nr));
@@ -171,8 +180,15 @@ struct KrylovBufs {
         dfree(coefdw);
         dfree(nbefore);
         dfree(dflag);
+        dfree(tickets);
         dfree(dscr);
         if (h_active) cudaFreeHost(h_active);
+        for (int q = 0; q < 2; ++q) {
+            if (h_active_lag[q]) cudaFreeHost(h_active_lag[q]);
+            if (ev_lag[q]) cudaEventDestroy(ev_lag[q]);
+            h_active_lag[q] = nullptr;
+            ev_lag[q] = nullptr;
+        }
         if (h_steps) cudaFreeHost(h_steps);
         if (h_resid) cudaFreeHost(h_resid);
         if (h_flags) cudaFreeHost(h_flags);
@@ -644,6 +660,9 @@ struct KrylovProblem {
     bool lean = false;     // FP32 basis: one Gram-Schmidt pass, a second one only on heavy cancellation
     double cycle_tol = 0;  // > 0: a cycle ends once every rhs has reduced its residual by this factor
     int max_cycles = 0;    // > 0: return after this many cycles (x updated, no closing residual)
+    bool lag_check = false;  // decide "all converged" from the flags of the previous step, without waiting for
+                             // the current one (the GPU keeps a step queued; a step after convergence changes
+                             // nothing, since inactive right-hand sides are frozen on the device)
     bool has_deadline = false;  // wall-clock limit: checked at every host synchronisation of the iteration;
     std::chrono::steady_clock::time_point deadline{};  // once passed, x takes the current cycle's update and the solve returns
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
@@ -702,11 +721,14 @@ int bfrom<dwf, double>(cplx<dwf>* out, const cplx<double>* in, size_t count, cud
 // one-pass Gram-Schmidt kernels of the double-word and FP32 bases (w in the V_{k+1} slot)
 template <typename TV>
 static int lean_multidot(const cplx<TV>* Vb, size_t bstride, size_t n, int k, const cplx<TV>* w, int nr, cplx<double>* out,
-                         KrylovBufs& kb, const int* flag, cudaStream_t st) {
+                         KrylovBufs& kb, const int* flag, cudaStream_t st, cplx<double>* copy_last = nullptr) {
     if constexpr (std::is_same<TV, dwf>::value) {
-        return multidot_dw(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, flag, st);
+        DD_TRY(multidot_dw(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, flag, st));
+        if (copy_last)
+            DD_CUDA(cudaMemcpyAsync(copy_last, out + (size_t)(k - 1) * nr, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToDevice, st));
+        return 0;
     } else if constexpr (std::is_same<TV, float>::value) {
-        if (multidot_f32(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, flag, st)) {
+        if (multidot_f32(Vb, bstride, n, k, w, n, n, nr, out, nr, kb.dscr, kb.tickets, copy_last, flag, st)) {
             set_error("FP32 basis: odd length or misaligned vector");
             return DDAMG_ERR_INVALID_ARG;
         }
@@ -722,7 +744,7 @@ static int lean_axpy_norm(cplx<TV>* w, const cplx<TV>* Vb, size_t bstride, size_
     if constexpr (std::is_same<TV, dwf>::value) {
         return axpy_norm_dw(w, Vb, bstride, n, k, coef, nr, n, nr, -1.0, kb.coefdw, kb.dscr, norm_out, flag, st);
     } else if constexpr (std::is_same<TV, float>::value) {
-        if (axpy_norm_f32(w, Vb, bstride, n, k, coef, nr, n, nr, -1.0, reinterpret_cast<float2*>(kb.coefdw), kb.dscr, norm_out, flag, st)) {
+        if (axpy_norm_f32(w, Vb, bstride, n, k, coef, nr, n, nr, -1.0, kb.dscr, kb.tickets, norm_out, flag, st)) {
             set_error("FP32 basis: odd length or misaligned vector");
             return DDAMG_ERR_INVALID_ARG;
         }
@@ -851,8 +873,8 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
                 DD_TRY(P.A(zk, wk));
                 const double vb = (double)sizeof(cplx<TV>) * n * nr;
                 Prof pr(h, PF_ORTHO, vb * (2 * (k + 1) + 6));
-                DD_TRY(lean_multidot(P.Vb, bstride, n, k + 2, wk, nr, kb.hcol, kb, nullptr, st));
-                DD_CUDA(cudaMemcpyAsync(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, sizeof(cplx<double>) * nr, cudaMemcpyDeviceToDevice, st));
+                // the last product is ||w||^2 before orthogonalisation, kept for the DGKS test
+                DD_TRY(lean_multidot(P.Vb, bstride, n, k + 2, wk, nr, kb.hcol, kb, nullptr, st, kb.nbefore));
                 DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, kb, kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
                 if (P.reorth) {
                     DD_TRY(dgks(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, s.active, nr, 1e-3, kb.dflag, st));
@@ -893,10 +915,23 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
                 }
                 continue;
             }
-            DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
-            DD_CUDA(cudaStreamSynchronize(st));
             int na = 0;
-            for (int r = 0; r < nr; ++r) na += kb.h_active[r];
+            if (P.lag_check) {
+                // flags after this step go to one pinned slot; the host waits only for those of the
+                // previous step, which the GPU has finished while this step is queued behind it
+                DD_CUDA(cudaMemcpyAsync(kb.h_active_lag[k & 1], s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+                DD_CUDA(cudaEventRecord(kb.ev_lag[k & 1], st));
+                if (k == 0) {
+                    na = 1;  // nothing to look at yet (the cycle started with an active right-hand side)
+                } else {
+                    DD_CUDA(cudaEventSynchronize(kb.ev_lag[(k - 1) & 1]));
+                    for (int r = 0; r < nr; ++r) na += kb.h_active_lag[(k - 1) & 1][r];
+                }
+            } else {
+                DD_CUDA(cudaMemcpyAsync(kb.h_active, s.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+                DD_CUDA(cudaStreamSynchronize(st));
+                for (int r = 0; r < nr; ++r) na += kb.h_active[r];
+            }
             if (na > 0 && P.has_deadline && std::chrono::steady_clock::now() >= P.deadline) R.timed_out = true;
             if (na == 0 || total >= P.maxiter || R.timed_out) {
                 ++k;
@@ -989,6 +1024,7 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     P.maxiter = fixed_iters > 0 ? fixed_iters : h->p.coarse_maxiter;
     P.reorth = false;
     P.lean = std::is_same<T, float>::value;  // FP32 kernels with the norm fused into the update
+    P.lag_check = true;
     P.Vb = basis;
     P.Zb = nullptr;
     P.w = w;

@@ -38,8 +38,10 @@ WORKLOADS = {
     # counterpart that the CPU baseline times (the 8^4 lattice's own near-critical mass for the
     # near-critical workloads)
     # headline: near-critical mass from the lattice's own spectral edge (smallest |eig| ~ 1e-3)
-    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, precision="half",
-                        m0_key="lattice_32x32x32x64_critical", oracle_m0_key="lattice_8x8x8x8_eps0.5"),
+    # (three levels, the recursion of Sec. 3, with one level-1 V-cycle as the coarse solve; the
+    # two-level solve of the same handle is reported beside it)
+    "32x32x32x64": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, precision="half", levels=3,
+                        ml_inner="vcycle", m0_key="lattice_32x32x32x64_critical", oracle_m0_key="lattice_8x8x8x8_eps0.5"),
     # the same lattice at m0 = -0.9319 (smallest |eig| ~ 0.063: an easier system)
     "32x32x32x64-m0.932": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, nrhs=12, rhs="point", N=20, nu=2, precision="half",
                                m0_key="lattice_32x32x32x64", oracle_m0_key="lattice_32x32x32x64"),
@@ -47,6 +49,13 @@ WORKLOADS = {
     "16x16x16x16": dict(dims=(16, 16, 16, 16), eps=0.5, seed=1, nrhs=1, rhs="gaussian", N=20, nu=2, precision="single",
                         m0_key="lattice_16x16x16x16_critical", oracle_m0_key="lattice_8x8x8x8_eps0.5", oracle_seed=3,
                         count_key="32x32x32x64"),
+    # memory-bound run: N_v = 24, FP16 interpolation and coarse blocks, FP32 smoother, FP64 outer
+    # residual; the setup updates the test vectors in groups of 8 and frees the FP64 vectors after
+    # (lean), FGMRES(10) (the paper's restart length at large volume), the 12 right-hand sides solved
+    # in three groups of four (what fits the device next to the operator)
+    "48x48x48x96": dict(dims=(96, 48, 48, 48), eps=0.55, seed=5, nrhs=12, rhs="point", N=24, nu=2, precision="half", n_kv=10,
+                        lean=1, setup_group=8, rhs_group=4, m0_key="lattice_48x48x48x96_critical",
+                        oracle_m0_key="lattice_8x8x8x8_eps0.55", count_key="48x48x48x96"),
     # the oracle's size, all FP64, nu = 3, smallest |eig| ~ 1e-3
     "8x8x8x8": dict(dims=(8, 8, 8, 8), eps=0.4, seed=1, nrhs=1, rhs="gaussian", N=20, nu=3, precision="double",
                     m0_key="lattice_8x8x8x8", oracle_m0_key="lattice_8x8x8x8"),
@@ -315,6 +324,44 @@ def run_profile_case(args):
     return 0
 
 
+def run_small(name, reps=3):
+    """Set up and solve one of the small workloads: setup seconds, median solve time of reps solves,
+    iteration counts, the FP64 relative residual, and (16^4) the Dslash and SAP kernel times."""
+    import torch
+
+    from paper_1303_1377_gb300 import ddamg, synth
+
+    w = WORKLOADS[name]
+    m0, _ = workload_m0(w)
+    prec = {"single": ddamg.PREC_SINGLE, "half": ddamg.PREC_HALF, "double": ddamg.PREC_DOUBLE}[w["precision"]]
+    U = synth.gauge_field(w["dims"], w["eps"], w["seed"])
+    t = time.perf_counter()
+    s = ddamg.Solver(w["dims"], U, m0, C_SW, ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=prec), setup=True)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t
+    b = torch.from_numpy(make_rhs(w, int(np.prod(w["dims"])))).to("cuda")
+    z, st, rc = s.solve_zero_guess(b)
+    times = []
+    s.profile(["dslash_fp32", "dslash_fp64", "sap_block_mr"])
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        z, st, rc = s.solve_zero_guess(b)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    prof = s.profile_read()
+    s.profile([])
+    r = b - s.apply_D(z)
+    rel = float((torch.linalg.vector_norm(r.reshape(b.shape[0], -1), dim=1) / torch.linalg.vector_norm(b.reshape(b.shape[0], -1), dim=1)).max())
+    s.close()
+    out = {"workload": workload_description(name, w, m0), "precision": w["precision"], "setup_seconds": t_setup,
+           "solves_per_s": b.shape[0] / float(np.median(times)), "solve_seconds_median": float(np.median(times)), "status": rc,
+           "fgmres_iterations": max(q["iterations"] for q in st), "coarse_iterations_per_solve": st[0]["coarse_iterations"],
+           "max_rel_residual": rel}
+    out["kernel_ms_per_solve"] = {k: v["total_ms"] / reps for k, v in prof.items()}
+    return out
+
+
 def measure_dslash(solver, b, hbm_peak, reps=10):
     """FP32 and FP64 Dslash (the fine D of Sec. 2.2) on the batch b (device, complex128): average launch
     time from the library's per-launch CUDA events and the algorithmic bytes per launch (links and site
@@ -360,10 +407,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain single-RHS FP64 comparison solve")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream (continuous batching over four operators)")
+    ap.add_argument("--serving-seconds", type=float, default=20.0)
+    ap.add_argument("--no-small", action="store_true", help="skip the 8^4 and 16^4 configurations")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
-    ap.add_argument("--levels", type=int, default=2, choices=[2, 3],
-                    help="3: the recursion to a third level (level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup)")
-    ap.add_argument("--ml-inner", default="fgmres", choices=["fgmres", "vcycle"],
+    ap.add_argument("--levels", type=int, default=None, choices=[2, 3],
+                    help="2 or 3 (the recursion to a third level: level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup); "
+                         "default: the workload's")
+    ap.add_argument("--ml-inner", default=None, choices=["fgmres", "vcycle"],
                     help="with --levels 3: the level-1 solve inside the fine V-cycle (FGMRES to 5e-2, or one level-1 V-cycle)")
     ap.add_argument("--profile-case", action="store_true", help="run each hot kernel once on --dims (for ncu) and exit")
     ap.add_argument("--dims", default="24,24,24,24", help="with --profile-case: the lattice")
@@ -376,6 +427,8 @@ def main():
         return run_profile_case(args)
     w = WORKLOADS[args.workload]
     args.precision = args.precision or w["precision"]
+    args.levels = args.levels or w.get("levels", 2)
+    args.ml_inner = args.ml_inner or w.get("ml_inner", "fgmres")
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -404,7 +457,8 @@ def main():
     prec = {"single": ddamg.PREC_SINGLE, "half": ddamg.PREC_HALF, "half32": ddamg.PREC_HALF, "double": ddamg.PREC_DOUBLE}[args.precision]
     params = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=prec,
                                   outer=ddamg.OUTER_REFINE if args.outer == "refine" else ddamg.OUTER_DW, cycle_tol=args.cycle_tol,
-                                  smoother_fp16=0 if args.precision == "half32" else 1)
+                                  smoother_fp16=0 if args.precision == "half32" else 1, n_kv=w.get("n_kv", 25),
+                                  lean=w.get("lean", 0), setup_group=w.get("setup_group", 0))
     t = time.perf_counter()
     solver = ddamg.Solver(dims, U, m0, C_SW, params, setup=True)
     if args.levels == 3:
@@ -420,17 +474,18 @@ def main():
     b = torch.from_numpy(bh).to("cuda")
     z = torch.zeros_like(b)
 
-    solve_fn = solver.ml_solve if args.levels == 3 else solver.solve
+    # the paper's zero initial guess: z is output only
+    solve_fn = solver.ml_solve_zero_guess if args.levels == 3 else solver.solve_zero_guess
 
-    def step():
-        if args.levels == 3:
-            with torch.cuda.stream(stream):
-                z.zero_()
-            zz, st, rc = solve_fn(b, z)
-        else:  # the paper's zero initial guess: z is output only
-            zz, st, rc = solver.solve_zero_guess(b, z)
-        if rc != 0:
-            raise RuntimeError(f"solve status {rc}")
+    group = w.get("rhs_group", nr)  # right-hand sides per solve call (all of them unless memory says otherwise)
+
+    def step(fn=None):
+        st = []
+        for g0 in range(0, nr, group):
+            zz, sg, rc = (fn or solve_fn)(b[g0:g0 + group], z[g0:g0 + group])
+            if rc != 0:
+                raise RuntimeError(f"solve status {rc}")
+            st += sg
         return st
 
     for _ in range(args.warmup):
@@ -440,7 +495,8 @@ def main():
     solver.profile_reset()
     step()
     prof_all = solver.profile_read()
-    dominant = max(prof_all, key=lambda k: prof_all[k]["total_ms"])
+    # the dominant kernel family (families recorded without bytes time whole recursion stages)
+    dominant = max((k for k in prof_all if prof_all[k]["bytes"] > 0), key=lambda k: prof_all[k]["total_ms"])
     solver.profile([dominant])
     solver.profile_reset()
     # timed region
@@ -468,11 +524,31 @@ def main():
     # whole-job throughput: solves summed over the replicas / slowest replica's time
     value, ms, _ = aggregate(ms, nr * args.steps, dist=dist, device="cuda")
     # residual check of the last solve, in FP64 through the library's D
-    r = b - solver.apply_D(z)
-    rel = (torch.linalg.vector_norm(r.reshape(nr, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nr, -1), dim=1)).max().item()
+    rel = 0.0
+    for g0 in range(0, nr, group):
+        r = b[g0:g0 + group] - solver.apply_D(z[g0:g0 + group])
+        ng = r.shape[0]
+        rel = max(rel, (torch.linalg.vector_norm(r.reshape(ng, -1), dim=1) /
+                        torch.linalg.vector_norm(b[g0:g0 + group].reshape(ng, -1), dim=1)).max().item())
+        del r
+    # the two-level solve on the same handle (the fine V-cycle with the odd-even GMRES on D_c), for
+    # comparison with the recursion
+    two_level = None
+    if args.levels == 3:
+        step(solver.solve_zero_guess)
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        st2 = [step(solver.solve_zero_guess) for _ in range(2)]
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        ms2 = t0e.elapsed_time(t1e) / 2
+        two_level = {"value": nr / (ms2 / 1e3), "unit": "solves/s", "ms_per_step": ms2, "steps": 2,
+                     "fgmres_iterations": max(q["iterations"] for q in st2[-1]),
+                     "coarse_iterations_per_solve": st2[-1][0]["coarse_iterations"],
+                     "coarse_solve": "odd-even GMRES(30) on D_c to 5e-2 (tensor-core stencil)"}
     # Dslash bandwidth at the workload's size and right-hand sides (half of the headline metric):
     # kernel time from CUDA events around each Dslash launch, algorithmic bytes per launch
-    dslash_rates = measure_dslash(solver, b, peaks()[0])
+    dslash_rates = measure_dslash(solver, b[:group], peaks()[0])
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region: b goes
     # in, z comes out; the zero-guess entry point never reads z (the paper's zero initial guess)
     e2e = None
@@ -480,12 +556,10 @@ def main():
         bhost = torch.from_numpy(bh).pin_memory()
         zhost = torch.empty_like(bhost).pin_memory()
         solver.set_stream(None)
-        zero_guess = args.levels == 2
         def e2e_step():
-            if zero_guess:
-                return solver.solve_zero_guess(bhost.numpy(), zhost.numpy())
-            zhost.zero_()
-            return solve_fn(bhost.numpy(), zhost.numpy())
+            bn, zn = bhost.numpy(), zhost.numpy()
+            for g0 in range(0, nr, group):
+                solve_fn(bn[g0:g0 + group], zn[g0:g0 + group])
         e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -504,8 +578,8 @@ def main():
         torch.cuda.synchronize()
         link = {"h2d_gbs": nbytes / c0.elapsed_time(c1) / 1e6, "d2h_gbs": nbytes / c1.elapsed_time(c2) / 1e6}
         del dev
-        e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": (1 if zero_guess else 2) * nbytes,
-               "d2h_bytes_per_step": nbytes, "entry": "ddamg_solve_batch_zero_guess" if zero_guess else "ddamg_ml_solve",
+        e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "entry": "ddamg_ml_solve_zero_guess" if args.levels == 3 else "ddamg_solve_batch_zero_guess",
                "host_link_copy": link}
     # roofline of the dominant kernel: HBM-bound families against the measured copy bandwidth;
     # families whose algorithmic flops per byte exceed the FP32 ridge against the FP32 FMA peak
@@ -565,6 +639,7 @@ def main():
         "gauge_generation_seconds": t_gauge,
         "kernel_profile_first_step": prof_all,
         "dslash": dslash_rates,
+        **({"two_level_same_handle": two_level} if two_level else {}),
     }
     if args.levels == 3:
         line["ml_counts_last_step"] = solver.ml_counts()  # FGMRES steps on D_1, GMRES steps on D_2, level-1 V-cycles
@@ -595,6 +670,17 @@ def main():
                                          "rel_residual": st1[0]["rel_residual"], "status": rc1, "setup_seconds": t_plain_setup,
                                          "speedup_of_value": value / (1.0 / tp)}
         plain.close()
+    # the smaller configurations, each set up and solved on its own: the oracle's 8^4 lattice (FP64
+    # throughout, nu = 3) and the 16^4 lattice (FP32 V-cycle, one Gaussian right-hand side)
+    if not args.no_small and world == 1 and args.workload.startswith("32x32x32x64"):
+        line["small_configs"] = {name: run_small(name) for name in ("8x8x8x8", "16x16x16x16")}
+    # the serving form: Poisson arrivals of 1-12 right-hand-side requests over four resident operators
+    if not args.no_serving and world == 1:
+        from paper_1303_1377_gb300.serve import run_stream
+
+        sv = run_stream(args.serving_seconds, 1.0, 5, ddamg.PREC_HALF, max_rhs=12)
+        line["serving"] = {k: sv[k] for k in ("requests", "solves", "wall_s", "solves_per_s", "latency_p50_s", "latency_p99_s",
+                                              "max_rel_residual", "arrival_rate_per_s", "rhs_per_request", "slots", "operators")}
     if rank == 0 and world == 1 and not args.no_cpu:
         n_or, _ = oracle_iterations(args.workload)
         base = OracleBaseline(w, workload_m0(w, "oracle_m0_key")[0], n_or if n_or else max(iters))

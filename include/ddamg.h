@@ -118,6 +118,13 @@ typedef struct {
     int smoother_fp16;    /* DDAMG_PREC_HALF only: 1 = the SAP smoother reads FP16 copies of the
                              links and site terms (FP32 arithmetic); 0 = FP32 copies, so that only
                              P, D_c and its inverses are stored in FP16 (1) */
+    int setup_group;      /* the setup updates the test vectors in groups of this many (the
+                             updates of one setup round are independent), bounding its work
+                             fields to 2 * setup_group fine fields; <= 0: all n_vec at once (0) */
+    int lean;             /* DDAMG_PREC_SINGLE / HALF: 1 = after each setup free the FP64 test
+                             vectors and FP64 interpolation (only the setup and ddamg_get_vectors
+                             use them; the V-cycle reads its FP32 / FP16 copies): 2 * n_vec FP64
+                             fields; ddamg_get_vectors then returns DDAMG_ERR_NOT_READY (0) */
 } ddamg_params;
 
 /* Statistics of one solve (the quantities reported in Tables 3-9). */
@@ -392,6 +399,9 @@ int ddamg_ml_vcycle(ddamg_handle* h, const double* in, double* out, int n_rhs, i
  * stats) with the fine V-cycle's coarse solve replaced by the recursion (coarse_iterations =
  * FGMRES steps on D_1). */
 int ddamg_ml_solve(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st);
+/* ddamg_ml_solve from the zero initial guess with z output only (as
+ * ddamg_solve_batch_zero_guess). */
+int ddamg_ml_solve_zero_guess(ddamg_handle* h, const double* b, double* z, int n_rhs, double tol, ddamg_stats* st);
 /* Counters of the last ddamg_ml_solve: out[0] FGMRES steps on D_1, out[1] GMRES steps on D_2,
  * out[2] level-1 V-cycles (per right-hand side). */
 int ddamg_ml_counts(const ddamg_handle* h, long long* out);

@@ -58,9 +58,11 @@ static void dfree(T*& p) {
     } while (0)
 
 // profiling families
-enum { PF_DSLASH64 = 0, PF_DSLASH32, PF_SAP, PF_COARSE, PF_RESTRICT, PF_PROLONG, PF_DSLASHDW, PF_ORTHO, PF_UPDATE, PF_COUNT };
-static const char* kPfNames[PF_COUNT] = {"dslash_fp64", "dslash_fp32", "sap_block_mr", "coarse_stencil", "restrict", "prolong",
-                                         "dslash_dw",   "krylov_ortho", "krylov_update"};
+// (the two ml_ families are wall time of whole recursion stages, recorded with zero bytes)
+enum { PF_DSLASH64 = 0, PF_DSLASH32, PF_SAP, PF_COARSE, PF_RESTRICT, PF_PROLONG, PF_DSLASHDW, PF_ORTHO, PF_UPDATE, PF_ML_VCYCLE,
+       PF_ML_COARSE, PF_COUNT };
+static const char* kPfNames[PF_COUNT] = {"dslash_fp64", "dslash_fp32",   "sap_block_mr", "coarse_stencil", "restrict",   "prolong",
+                                         "dslash_dw",   "krylov_ortho",  "krylov_update", "ml_vcycle1",   "ml_coarse2"};
 
 struct ProfRec {
     int fam;
@@ -1154,16 +1156,22 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
     cudaStream_t st = h->stream;
     const int N = h->N;
     const size_t fld = (size_t)12 * h->V;
-    DD_TRY(h->ws_fine[0].ensure(sizeof(cplx<T>) * fld * N));
-    DD_TRY(h->ws_fine[1].ensure(sizeof(cplx<T>) * fld * N));
+    // the vectors are processed in groups of G (each vector's update is independent of the others
+    // within a phase-1 step or a setup round), so the work fields hold 2 G fine fields
+    const int G = (h->p.setup_group > 0 && h->p.setup_group < N) ? h->p.setup_group : N;
+    DD_TRY(h->ws_fine[0].ensure(sizeof(cplx<T>) * fld * G));
+    DD_TRY(h->ws_fine[1].ensure(sizeof(cplx<T>) * fld * G));
     cplx<T>* t1 = h->ws_fine[0].as<cplx<T>>();
     cplx<T>* t2 = h->ws_fine[1].as<cplx<T>>();
     // phase 1: v_j <- M_SAP^(eta) v_j, eta = 1, 2, 3
-    for (int eta = 1; eta <= 3; ++eta) {
-        DD_CUDA(cudaMemsetAsync(t1, 0, sizeof(cplx<T>) * fld * N, st));
-        DD_TRY(sap<T>(h, v, t1, N, eta));
-        DD_CUDA(cudaMemcpyAsync(v, t1, sizeof(cplx<T>) * fld * N, cudaMemcpyDeviceToDevice, st));
-    }
+    for (int eta = 1; eta <= 3; ++eta)
+        for (int j0 = 0; j0 < N; j0 += G) {
+            const int g = std::min(G, N - j0);
+            cplx<T>* vg = v + (size_t)j0 * fld;
+            DD_CUDA(cudaMemsetAsync(t1, 0, sizeof(cplx<T>) * fld * g, st));
+            DD_TRY(sap<T>(h, vg, t1, g, eta));
+            DD_CUDA(cudaMemcpyAsync(vg, t1, sizeof(cplx<T>) * fld * g, cudaMemcpyDeviceToDevice, st));
+        }
     KrylovBufs& kb = h->ko;
     DD_TRY(kb.alloc(std::max(N, kb.nrhs), std::max(1, h->p.n_kv)));
     auto to64 = [&]() -> int {
@@ -1176,15 +1184,19 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
     for (int it = 0; it < h->p.n_inv; ++it) {
         DD_TRY(to64());
         DD_TRY(build_interpolation(h));
-        if (h->p.setup_update == DDAMG_SETUP_IDSETUP) {
-            // Algorithm 1: v_j <- C v_j
-            DD_TRY(vcycle<T>(h, v, t2, N, 0));
-            DD_CUDA(cudaMemcpyAsync(v, t2, sizeof(cplx<T>) * fld * N, cudaMemcpyDeviceToDevice, st));
-        } else {
-            // Algorithm 2: v_j <- v_j + C (v_j - D v_j)
-            DD_TRY((dslash<T, T>(h, v, v, t1, N)));
-            DD_TRY(vcycle<T>(h, t1, t2, N, 0));
-            DD_TRY((lincomb<T, T>(v, fld, 1.0, t2, 0, fld, 1, kb.ones, N, fld, N, nullptr, st)));
+        for (int j0 = 0; j0 < N; j0 += G) {
+            const int g = std::min(G, N - j0);
+            cplx<T>* vg = v + (size_t)j0 * fld;
+            if (h->p.setup_update == DDAMG_SETUP_IDSETUP) {
+                // Algorithm 1: v_j <- C v_j
+                DD_TRY(vcycle<T>(h, vg, t2, g, 0));
+                DD_CUDA(cudaMemcpyAsync(vg, t2, sizeof(cplx<T>) * fld * g, cudaMemcpyDeviceToDevice, st));
+            } else {
+                // Algorithm 2: v_j <- v_j + C (v_j - D v_j)
+                DD_TRY((dslash<T, T>(h, vg, vg, t1, g)));
+                DD_TRY(vcycle<T>(h, t1, t2, g, 0));
+                DD_TRY((lincomb<T, T>(vg, fld, 1.0, t2, 0, fld, 1, kb.ones, g, fld, g, nullptr, st)));
+            }
         }
         // v_j <- v_j / ||v_j||
         DD_TRY((multidot<T, T>(v, 0, fld, 1, v, fld, fld, N, kb.nrm, 1, kb.dscr, st)));
@@ -1207,10 +1219,25 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
     return 0;
 }
 
+// FP64 test vectors and interpolation, freed after the setup of a lean handle
+static int ensure_fp64_vectors(ddamg_handle* h) {
+    const size_t n = (size_t)12 * h->V * h->N;
+    if (!h->V64) DD_TRY(dalloc_n(&h->V64, n));
+    if (!h->P64) DD_TRY(dalloc_n(&h->P64, n));
+    return 0;
+}
+static void lean_release(ddamg_handle* h) {
+    if (!(h->p.lean && h->single())) return;
+    cudaStreamSynchronize(h->stream);  // cudaFree would wait too; an error here surfaces at the next call
+    dfree(h->V64);
+    dfree(h->P64);
+}
+
 static int run_setup(ddamg_handle* h, const double* v0) {
     cudaStream_t st = h->stream;
     const int N = h->N;
     const size_t fld = (size_t)12 * h->V;
+    DD_TRY(ensure_fp64_vectors(h));
     // initial vectors into V64 (internal order)
     if (v0) {
         const void* dv;
@@ -1233,6 +1260,7 @@ static int run_setup(ddamg_handle* h, const double* v0) {
         rc = run_setup_T<double>(h, v);
     }
     for (int q = 0; q < 3; ++q) h->ws_fine[q].release();
+    if (!rc) lean_release(h);
     return rc;
 }
 
@@ -1537,6 +1565,8 @@ void ddamg_default_params(ddamg_params* p) {
     p->cycle_tol = 1e-5;
     p->setup_update = DDAMG_SETUP_DDALPHA;
     p->smoother_fp16 = 1;
+    p->setup_group = 0;
+    p->lean = 0;
 }
 
 const char* ddamg_error_string(int s) {
@@ -1589,14 +1619,21 @@ int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N) {
     }
     const size_t fld = (size_t)12 * h->V;
     const void* dv;
+    DD_TRY(ensure_fp64_vectors(h));
     DD_TRY(stage_in(h, h->ws_io[0], V, sizeof(cplx<double>) * fld * N, &dv));
     DD_TRY((to_internal<double, double>(reinterpret_cast<const cplx<double>*>(dv), h->V64, h->d_lex_of, h->V, 12, N, h->stream)));
-    return build_interpolation(h);
+    DD_TRY(build_interpolation(h));
+    lean_release(h);
+    return 0;
 }
 
 int ddamg_get_vectors(const ddamg_handle* hc, double* V) {
     ddamg_handle* h = const_cast<ddamg_handle*>(hc);
     if (!h || !V) return DDAMG_ERR_INVALID_ARG;
+    if (!h->V64) {
+        set_error("ddamg_get_vectors: the handle is lean (params.lean): its FP64 test vectors were freed after the setup");
+        return DDAMG_ERR_NOT_READY;
+    }
     return fine_out<double>(h, h->V64, V, h->N);
 }
 

@@ -70,6 +70,8 @@ class Params(C.Structure):
         ("cycle_tol", C.c_double),
         ("setup_update", C.c_int),
         ("smoother_fp16", C.c_int),
+        ("setup_group", C.c_int),
+        ("lean", C.c_int),
     ]
 
 
@@ -169,6 +171,7 @@ def _load():
         "ddamg_ml_vcycle1": (I, [P, P, P, I]),
         "ddamg_ml_vcycle": (I, [P, P, P, I, I]),
         "ddamg_ml_solve": (I, [P, P, P, I, D, C.POINTER(Stats)]),
+        "ddamg_ml_solve_zero_guess": (I, [P, P, P, I, D, C.POINTER(Stats)]),
         "ddamg_ml_counts": (I, [P, C.POINTER(LL)]),
         "ddamg_destroy": (I, [P]),
     }
@@ -402,7 +405,18 @@ class Solver:
             z[...] = 0
         st = (Stats * nr)()
         rc = lib.ddamg_ml_solve(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
-        _check(rc, "ddamg_ml_solve", allow=(-4, -5) if allow_fail else ())
+        _check(rc, "ddamg_ml_solve", allow=(-4, -5, -6) if allow_fail else ())
+        return z, [s.as_dict() for s in st], rc
+
+    def ml_solve_zero_guess(self, b, z=None, tol: float = 0.0, allow_fail: bool = False):
+        """Three-level solve from the zero initial guess; z (optional) is output only."""
+        b = _host(b, np.complex128)
+        nr = int(b.shape[0])
+        if z is None:
+            z = _empty_like(b, b.shape, np.complex128)
+        st = (Stats * nr)()
+        rc = lib.ddamg_ml_solve_zero_guess(self.h, _ptr(b), _ptr(z), nr, float(tol), st)
+        _check(rc, "ddamg_ml_solve_zero_guess", allow=(-4, -5, -6) if allow_fail else ())
         return z, [s.as_dict() for s in st], rc
 
     def ml_counts(self):

@@ -8,7 +8,7 @@ joins work that is already on the GPU instead of waiting for a batch to drain. D
 operators run on different streams, and their cycles overlap on the device. A new operator is
 admitted only if its estimated device memory fits the free memory minus a reserve.
 
-usage: python -m paper_1303_1377_gb300.serve --bench [--duration 60] [--rate 1.0] [--max-rhs 4]
+usage: python -m paper_1303_1377_gb300.serve --bench [--duration 60] [--rate 1.0] [--max-rhs 12]
 prints one JSON line: p50/p99 latency and solves/s over a Poisson stream of requests on four
 resident operators (16^4, 24^4, 32^4, 32^3 x 64; distinct seeds and masses).
 """
@@ -209,7 +209,7 @@ STREAM_OPERATORS = [
 ]
 
 
-def run_stream(duration: float, rate: float, seed: int, precision: int, max_rhs: int = 4):
+def run_stream(duration: float, rate: float, seed: int, precision: int, max_rhs: int = 12):
     """Poisson arrivals at `rate` requests/s for `duration` s, each on a random operator with
     1..max_rhs Gaussian right-hand sides; returns the summary dict. Every operator serves one
     warm-up request right after its admission (its workspaces are allocated then), which is
@@ -275,7 +275,7 @@ def main():
     ap.add_argument("--bench", action="store_true")
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--rate", type=float, default=1.0)
-    ap.add_argument("--max-rhs", type=int, default=4)
+    ap.add_argument("--max-rhs", type=int, default=12)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--precision", default="half", choices=["single", "half"])
     a = ap.parse_args()

@@ -38,7 +38,8 @@ def _gram(A, B):
     return torch.matmul(A.reshape(k, -1).conj(), B.reshape(k, -1).transpose(0, 1)).cpu().numpy()
 
 
-def edge(dims, eps, seed, shift, k=12, iters=20, res_tol=1e-4, solve_tol=1e-8, n_vec=20, precision="half", c_sw=1.0, log=print):
+def edge(dims, eps, seed, shift, k=12, iters=20, res_tol=1e-4, solve_tol=1e-8, n_vec=20, precision="half", c_sw=1.0, log=print,
+         **params):
     import torch
 
     from . import ddamg, synth
@@ -46,7 +47,7 @@ def edge(dims, eps, seed, shift, k=12, iters=20, res_tol=1e-4, solve_tol=1e-8, n
     prec = {"single": ddamg.PREC_SINGLE, "half": ddamg.PREC_HALF, "double": ddamg.PREC_DOUBLE}[precision]
     t0 = time.perf_counter()
     U = synth.gauge_field(dims, eps, seed)
-    s = ddamg.Solver(dims, U, shift, c_sw, ddamg.default_params(n_vec=n_vec, precision=prec), setup=True)
+    s = ddamg.Solver(dims, U, shift, c_sw, ddamg.default_params(n_vec=n_vec, precision=prec, **params), setup=True)
     s.set_stream(torch.cuda.current_stream().cuda_stream)  # the library's work and torch's in one stream order
     del U
     t_setup = time.perf_counter() - t0
@@ -98,6 +99,10 @@ def main():
     ap.add_argument("--k", type=int, default=12)
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--out", default=None, help="also write the record (with its history) to this JSON file")
+    ap.add_argument("--n-vec", type=int, default=20)
+    ap.add_argument("--n-kv", type=int, default=25, help="FGMRES restart length of the solves")
+    ap.add_argument("--lean", type=int, default=0, help="free the FP64 test vectors after the setup (large lattices)")
+    ap.add_argument("--setup-group", type=int, default=0, help="test vectors per setup batch (0: all)")
     ap.add_argument("--name")
     ap.add_argument("--write", action="store_true", help="record the result in workloads.json")
     a = ap.parse_args()
@@ -109,7 +114,7 @@ def main():
             f.write("\n")
         return
     dims = tuple(int(v) for v in a.dims.split(","))
-    r = edge(dims, a.eps, a.seed, a.shift, k=a.k, iters=a.iters)
+    r = edge(dims, a.eps, a.seed, a.shift, k=a.k, iters=a.iters, n_vec=a.n_vec, n_kv=a.n_kv, lean=a.lean, setup_group=a.setup_group)
     rec = {"dims": list(dims), "eps": a.eps, "seed": a.seed, "c_sw": 1.0, "m0": -r["lambda_L_m0_0"][0] + a.gap, "gap": a.gap,
            "source": "GPU shift-invert subspace iteration (paper_1303_1377_gb300/spectral_edge.py)", **r}
     print(json.dumps({k: v for k, v in rec.items() if k != "history"}))

@@ -466,3 +466,30 @@ def test_zero_guess_entry_and_time_limit(dd):
     with c.solver(dd.PREC_SINGLE, time_limit_s=600.0) as s:
         z2, st2, rc2 = s.solve_zero_guess(b)
     assert rc2 == 0 and relerr(z2, z0) <= 1e-14
+
+
+def test_grouped_setup_and_lean_handle(dd):
+    """The setup processed in groups of test vectors (setup_group) gives the vectors of the
+    all-at-once setup (each vector's update is independent within a round); a lean handle frees
+    its FP64 vectors after the setup, refuses ddamg_get_vectors and solves as before."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 2, seed=125)
+    base = dict(n_vec=8, block=c.block, precision=dd.PREC_HALF, nu=2, n_inv=2)
+    with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(**base), setup=False) as s:
+        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
+        v_all = s.vectors()
+        z_all, _, rc = s.solve(b)
+        assert rc == 0
+    with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(setup_group=3, **base), setup=False) as s:
+        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
+        assert relerr(s.vectors(), v_all) < 1e-12
+    with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(setup_group=3, lean=1, **base), setup=False) as s:
+        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
+        with pytest.raises(dd.DDAMGError) as e:
+            s.vectors()
+        assert e.value.status == dd.ERR_NOT_READY
+        z, st, rc = s.solve(b)
+    assert rc == 0
+    assert relerr(z, z_all) < 1e-12
+    for q in range(2):
+        assert np.linalg.norm(b[q] - c.D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])

@@ -605,12 +605,12 @@ static bool f32_layout_ok(const void* A, size_t istride, size_t arstride, const 
 }
 
 // CTAs per right-hand side of the FP32 basis kernels: about four resident CTAs per SM over all
-// right-hand sides, and at least 16 float4 per thread so the reduction is a small part of the work
+// right-hand sides (608 on 152 SMs) as long as every thread has a float4 to work on; short vectors
+// (the coarsest level) are spread thin rather than left to one CTA per right-hand side
 static int f32_ctas(size_t n4, int nrhs, int threads) {
-    long long by_work = (long long)(n4 / ((size_t)threads * 16));
-    long long target = 608 / nrhs;
-    long long c = std::min(by_work, target);
-    return (int)std::max(1LL, c);
+    const long long target = std::max(1, 608 / nrhs);
+    const long long by_len = (long long)((n4 + threads - 1) / threads);
+    return (int)std::max(1LL, std::min(target, by_len));
 }
 
 int multidot_f32(const cplx<float>* A, size_t istride, size_t arstride, int k, const cplx<float>* w, size_t wrstride, size_t n, int nrhs,

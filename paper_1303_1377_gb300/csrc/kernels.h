@@ -74,10 +74,10 @@ int launch_restrict_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<f
 bool prolong_tc_supported(const Geom& g, int N);
 int launch_prolong_tc(const Geom& g, const cplx<__half>* P, int N, const cplx<float>* in, cplx<float>* out, int nrhs, cudaStream_t st);
 int launch_gram_schmidt(const Geom& g, cplx<double>* P, int N, int* rank_fail, cudaStream_t st);
-int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, cplx<double>* T,
+int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, int col0, int ncols, cplx<double>* T,
                       cudaStream_t st);
-int launch_block_project(const Geom& g, const cplx<double>* P, int N, const cplx<double>* T, const int* sites, int nsites,
-                         double* Bout, size_t site_stride, cudaStream_t st);
+int launch_block_project(const Geom& g, const cplx<double>* P, int N, const cplx<double>* T, int col0, int ncols, const int* sites,
+                         int nsites, double* Bout, size_t site_stride, cudaStream_t st);
 
 // ---- coarse.cu
 template <typename T, typename S>

@@ -70,7 +70,7 @@ __host__ __device__ inline bool ml_selected(const MLView<T>& v, int c, int parit
 
 // right-hand sides are processed in chunks of ML_RC per thread, so that each matrix entry is read
 // once per chunk (the operator, not the vectors, dominates the traffic)
-constexpr int ML_RC = 8;
+constexpr int ML_RC = 12;  // the twelve point sources of a batch in one pass
 
 // acc[k] += row `row` of the column-major block times the site vector of right-hand side r0 + k
 template <typename T>
@@ -426,7 +426,19 @@ struct MLHostExec {
         for (long long i = 0; i < n; ++i) f(i);
         return 0;
     }
+    // no fused colour step on the host: ml_sap runs the functor sequence
+    template <typename T>
+    int sap_colour(const MLView<T>&, const cplx<T>*, cplx<T>*, int, int, int) const {
+        return 1;
+    }
 };
+
+// one SAP colour step of ml_sap as a single kernel (ml_sap.cu): FP32, blocks with as many even as
+// odd sites, at most 384 (block-half sites x components) threads and the six half-block MR vectors
+// of 12 right-hand sides within shared memory
+bool ml_sap_fused_supported(const MLView<float>& v);
+int launch_ml_sap_fused(const MLView<float>& v, const cplx<float>* b, cplx<float>* z, int nrhs, int colour, int mr_steps,
+                        cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // orchestration
@@ -446,7 +458,9 @@ int ml_sap(const X& ex, const MLView<T>& v, const cplx<T>* b, cplx<T>* z, int nr
     const long long nf = (long long)nrhs * v.NB * v.nc, ns = (long long)v.NB * v.nc;
     for (int it = 0; it < nu; ++it)
         for (int col = 0; col < 2; ++col) {
-            int rc;
+            int rc = ex.sap_colour(v, b, z, nrhs, col, mr_steps);  // 0: done by the executor's fused step
+            if (rc < 0) return rc;
+            if (rc == 0) continue;
             if ((rc = ex.run(ns, MLFullApply<T>{v, z, b, w.r, nrhs}))) return rc;
             // t_e = A_ee^{-1} r_e; rho = r_o - A_oe t_e; x = 0
             if ((rc = ex.run(ns, MLDinvApply<T>{v, w.r, w.te, col, true, nrhs}))) return rc;

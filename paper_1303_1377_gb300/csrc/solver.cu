@@ -1083,16 +1083,21 @@ static int build_interpolation(ddamg_handle* h) {
         set_error("test vectors are linearly dependent on an aggregate");
         return DDAMG_ERR_RANK;
     }
+    // D_c = P^H D P direction by direction, over the 2N columns of P in chunks (setup_group columns,
+    // all 2N when not set), so that the scratch of D P holds a chunk of FP64 fine fields
+    const int chunk = (h->p.setup_group > 0 && h->p.setup_group < 2 * N) ? h->p.setup_group : 2 * N;
     Scratch tscr;
-    DD_TRY(tscr.ensure(sizeof(cplx<double>) * fld * 2 * N));
+    DD_TRY(tscr.ensure(sizeof(cplx<double>) * fld * chunk));
     FineOp<double> op64{h->U64, h->clov64, h->clovinv64};
     int rc = 0;
-    for (int dir = 0; dir < 9 && !rc; ++dir) {
-        rc = launch_assemble_T(h->g, op64, h->P64, N, dir, tscr.as<cplx<double>>(), st);
-        if (!rc)
-            rc = launch_block_project(h->g, h->P64, N, tscr.as<cplx<double>>(), h->d_sites + (size_t)dir * h->Vb, h->nsites[dir],
-                                      h->B64 + (size_t)dir * nc * nc * 2, (size_t)9 * nc * nc, st);
-    }
+    for (int dir = 0; dir < 9 && !rc; ++dir)
+        for (int col0 = 0; col0 < 2 * N && !rc; col0 += chunk) {
+            const int ncols = std::min(chunk, 2 * N - col0);
+            rc = launch_assemble_T(h->g, op64, h->P64, N, dir, col0, ncols, tscr.as<cplx<double>>(), st);
+            if (!rc)
+                rc = launch_block_project(h->g, h->P64, N, tscr.as<cplx<double>>(), col0, ncols, h->d_sites + (size_t)dir * h->Vb,
+                                          h->nsites[dir], h->B64 + (size_t)dir * nc * nc * 2, (size_t)9 * nc * nc, st);
+        }
     DD_CUDA(cudaStreamSynchronize(st));
     tscr.release();
     if (rc) return rc;

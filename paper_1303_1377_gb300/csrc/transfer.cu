@@ -307,12 +307,12 @@ __device__ __forceinline__ void asm_hop(const Geom& g, const cplx<double>* __res
     }
 }
 
-__global__ void assemble_T_kernel(Geom g, FineOp<double> op, const cplx<double>* __restrict__ P, int N, int dir,
+__global__ void assemble_T_kernel(Geom g, FineOp<double> op, const cplx<double>* __restrict__ P, int N, int dir, int col0, int ncols,
                                   cplx<double>* __restrict__ Tout) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)g.V * 2 * N) return;
+    if (tid >= (long long)g.V * ncols) return;
     const int i = (int)(tid % g.V);
-    const int col = (int)(tid / g.V);
+    const int col = col0 + (int)(tid / g.V);
     const int h = col / N, j = col % N;
     const cplx<double>* pj = P + (size_t)j * 12 * g.V;
     const int c = block_of(g, i);
@@ -339,15 +339,17 @@ __global__ void assemble_T_kernel(Geom g, FineOp<double> op, const cplx<double>*
 #pragma unroll
         for (int k = 0; k < 12; ++k) out.v[k] = -0.5 * acc.v[k];
     }
-    cplx<double>* o = Tout + (size_t)col * 12 * g.V;
+    cplx<double>* o = Tout + (size_t)(col - col0) * 12 * g.V;
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[(size_t)k * g.V + i] = out.v[k];
 }
 
-int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, cplx<double>* T,
-                      cudaStream_t st) {
-    const long long n = (long long)g.V * 2 * N;
-    assemble_T_kernel<<<ceil_div(n, 128), 128, 0, st>>>(g, op, P, N, dir, T);
+// T[col - col0] = (the part of D in direction dir) applied to column col of P (split by chirality
+// half), for the columns col0 .. col0 + ncols - 1 of the 2N
+int launch_assemble_T(const Geom& g, const FineOp<double>& op, const cplx<double>* P, int N, int dir, int col0, int ncols,
+                      cplx<double>* T, cudaStream_t st) {
+    const long long n = (long long)g.V * ncols;
+    assemble_T_kernel<<<ceil_div(n, 128), 128, 0, st>>>(g, op, P, N, dir, col0, ncols, T);
     DD_CHECK_LAUNCH();
     return 0;
 }
@@ -358,14 +360,15 @@ constexpr int kProjThreads = 256;
 constexpr int kProjPerThread = 8;
 
 __global__ void __launch_bounds__(kProjThreads) block_project_kernel(Geom g, const cplx<double>* __restrict__ P, int N,
-                                                                     const cplx<double>* __restrict__ Tin,
+                                                                     const cplx<double>* __restrict__ Tin, int col0, int ncols,
                                                                      const int* __restrict__ sites, int nsites, int CH,
                                                                      double* __restrict__ Bout, size_t site_stride) {
     extern __shared__ unsigned char smem_raw[];
     const int nc = 2 * N;
     cplx<double>* Pc = reinterpret_cast<cplx<double>*>(smem_raw);  // [N][12][CH]
-    cplx<double>* Tc = Pc + (size_t)N * 12 * CH;                      // [2N][12][CH]
+    cplx<double>* Tc = Pc + (size_t)N * 12 * CH;                      // [ncols][12][CH]
     const int c = blockIdx.x;
+    // outputs o = (col - col0) * nc + row of this launch's columns
     const int o0 = blockIdx.y * kProjThreads * kProjPerThread;
     cplx<double> acc[kProjPerThread];
 #pragma unroll
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kProjThreads) block_project_kernel(Geom g, con
             if (s0 + s < nsites) v = P[((size_t)j * 12 + k) * g.V + (size_t)c * g.Vb + sites[s0 + s]];
             Pc[q] = v;
         }
-        for (int q = threadIdx.x; q < nc * 12 * CH; q += blockDim.x) {
+        for (int q = threadIdx.x; q < ncols * 12 * CH; q += blockDim.x) {
             int s = q % CH, k = (q / CH) % 12, col = q / (12 * CH);
             cplx<double> v = czero<double>();
             if (s0 + s < nsites) v = Tin[((size_t)col * 12 + k) * g.V + (size_t)c * g.Vb + sites[s0 + s]];
@@ -388,8 +391,8 @@ __global__ void __launch_bounds__(kProjThreads) block_project_kernel(Geom g, con
 #pragma unroll
         for (int m = 0; m < kProjPerThread; ++m) {
             int o = o0 + m * kProjThreads + threadIdx.x;
-            if (o >= nc * nc) break;
-            int col = o / nc, row = o % nc;
+            if (o >= ncols * nc) break;
+            int col = o / nc, row = o % nc;  // col relative to col0
             int hp = row / N, jp = row % N;
             const cplx<double>* pr = Pc + ((size_t)jp * 12 + 6 * hp) * CH;
             const cplx<double>* tc = Tc + ((size_t)col * 12 + 6 * hp) * CH;
@@ -399,23 +402,23 @@ __global__ void __launch_bounds__(kProjThreads) block_project_kernel(Geom g, con
 #pragma unroll
     for (int m = 0; m < kProjPerThread; ++m) {
         int o = o0 + m * kProjThreads + threadIdx.x;
-        if (o >= nc * nc) break;
-        double* b = Bout + ((size_t)c * site_stride + o) * 2;
+        if (o >= ncols * nc) break;
+        double* b = Bout + ((size_t)c * site_stride + (size_t)col0 * nc + o) * 2;
         b[0] = acc[m].re;
         b[1] = acc[m].im;
     }
 }
 
-int launch_block_project(const Geom& g, const cplx<double>* P, int N, const cplx<double>* T, const int* sites, int nsites,
-                         double* Bout, size_t site_stride, cudaStream_t st) {
+int launch_block_project(const Geom& g, const cplx<double>* P, int N, const cplx<double>* T, int col0, int ncols, const int* sites,
+                         int nsites, double* Bout, size_t site_stride, cudaStream_t st) {
     const int nc = 2 * N;
-    int CH = (int)((160 * 1024) / ((size_t)3 * N * 12 * sizeof(cplx<double>)));
+    int CH = (int)((160 * 1024) / ((size_t)(N + ncols) * 12 * sizeof(cplx<double>)));
     if (CH > 8) CH = 8;
     if (CH < 1) CH = 1;
-    size_t smem = (size_t)3 * N * 12 * CH * sizeof(cplx<double>);
+    size_t smem = (size_t)(N + ncols) * 12 * CH * sizeof(cplx<double>);
     cudaFuncSetAttribute(block_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    dim3 grid(g.NB, ceil_div((long long)nc * nc, kProjThreads * kProjPerThread));
-    block_project_kernel<<<grid, kProjThreads, smem, st>>>(g, P, N, T, sites, nsites, CH, Bout, site_stride);
+    dim3 grid(g.NB, ceil_div((long long)ncols * nc, kProjThreads * kProjPerThread));
+    block_project_kernel<<<grid, kProjThreads, smem, st>>>(g, P, N, T, col0, ncols, sites, nsites, CH, Bout, site_stride);
     DD_CHECK_LAUNCH();
     return 0;
 }

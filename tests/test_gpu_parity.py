@@ -469,27 +469,37 @@ def test_zero_guess_entry_and_time_limit(dd):
 
 
 def test_grouped_setup_and_lean_handle(dd):
-    """The setup processed in groups of test vectors (setup_group) gives the vectors of the
-    all-at-once setup (each vector's update is independent within a round); a lean handle frees
-    its FP64 vectors after the setup, refuses ddamg_get_vectors and solves as before."""
+    """setup_group: the FP64 assembly of D_c in column chunks equals the one-pass assembly (the same
+    sums per entry), and the setup run in groups of test vectors gives the all-at-once vectors up to
+    the FP32 V-cycle's rounding (its reductions are split over a different number of CTAs; the
+    updates themselves are independent within a round).  A lean handle frees its FP64 vectors
+    after the setup, refuses ddamg_get_vectors and solves exactly as the same handle kept whole."""
     c = case("8^4/4^4", dd)
     b = synth.gaussian_spinors(c.dims, 2, seed=125)
+    v0 = synth.random_test_vectors(c.dims, 8, seed=126)
+    with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(n_vec=8, block=c.block, precision=dd.PREC_DOUBLE), setup=False) as s:
+        s.setup_from_vectors(v0)
+        B_all = s.coarse_stencil()
+    with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(n_vec=8, block=c.block, precision=dd.PREC_DOUBLE, setup_group=3),
+                   setup=False) as s:
+        s.setup_from_vectors(v0)
+        assert relerr(s.coarse_stencil(), B_all) < 1e-15
     base = dict(n_vec=8, block=c.block, precision=dd.PREC_HALF, nu=2, n_inv=2)
     with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(**base), setup=False) as s:
-        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
+        s.run_setup(v0)
         v_all = s.vectors()
-        z_all, _, rc = s.solve(b)
-        assert rc == 0
     with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(setup_group=3, **base), setup=False) as s:
-        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
-        assert relerr(s.vectors(), v_all) < 1e-12
+        s.run_setup(v0)
+        assert relerr(s.vectors(), v_all) < 1e-4
+        z_g, _, rc = s.solve(b)
+        assert rc == 0
     with dd.Solver(c.dims, c.U, c.m0, CSW, dd.default_params(setup_group=3, lean=1, **base), setup=False) as s:
-        s.run_setup(synth.random_test_vectors(c.dims, 8, seed=126))
+        s.run_setup(v0)
         with pytest.raises(dd.DDAMGError) as e:
             s.vectors()
         assert e.value.status == dd.ERR_NOT_READY
         z, st, rc = s.solve(b)
     assert rc == 0
-    assert relerr(z, z_all) < 1e-12
+    assert relerr(z, z_g) < 1e-12
     for q in range(2):
         assert np.linalg.norm(b[q] - c.D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])

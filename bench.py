@@ -54,7 +54,7 @@ WORKLOADS = {
     # (lean), FGMRES(10) (the paper's restart length at large volume), the 12 right-hand sides solved
     # in three groups of four (what fits the device next to the operator)
     "48x48x48x96": dict(dims=(96, 48, 48, 48), eps=0.55, seed=5, nrhs=12, rhs="point", N=24, nu=2, precision="half", n_kv=10,
-                        lean=1, setup_group=8, rhs_group=4, levels=3, ml_inner="vcycle", m0_key="lattice_48x48x48x96_critical",
+                        lean=1, setup_group=8, rhs_group=4, levels=3, ml_inner="vcycle", m0_key="lattice_48x48x48x96_critical", gap=1e-3,
                         oracle_m0_key="lattice_8x8x8x8_eps0.55", count_key="48x48x48x96"),
     # the oracle's size, all FP64, nu = 3, smallest |eig| ~ 1e-3
     "8x8x8x8": dict(dims=(8, 8, 8, 8), eps=0.4, seed=1, nrhs=1, rhs="gaussian", N=20, nu=3, precision="double",
@@ -66,8 +66,12 @@ TRAFFIC_JSON = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
 def workload_m0(w, key="m0_key"):
+    """The workload's mass: the record's m0, or -Re(lambda_L) + the workload's own gap when it sets one."""
     data = json.load(open(WORKLOADS_JSON))
-    return float(data[w[key]]["m0"]), data[w[key]]
+    rec = data[w[key]]
+    if key == "m0_key" and "gap" in w:
+        return -float(rec["lambda_L_m0_0"][0]) + w["gap"], rec
+    return float(rec["m0"]), rec
 
 
 def peaks():
@@ -471,6 +475,7 @@ def main():
         solver.ml_setup(synth.gaussian_coarse(solver.n_coarse, solver.coarse_dof, mlp.n_vec1, seed=w["seed"] + 11), mlp)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t
+    print(f"[bench] setup done in {t_setup:.1f} s (m0 = {m0:.6f})", file=sys.stderr, flush=True)
     del U
     stream = torch.cuda.Stream()
     solver.set_stream(stream.cuda_stream)
@@ -493,8 +498,11 @@ def main():
             st += sg
         return st
 
-    for _ in range(args.warmup):
+    for k in range(args.warmup):
+        t_w = time.perf_counter()
         st = step()
+        print(f"[bench] warm-up step {k}: {time.perf_counter() - t_w:.2f} s, FGMRES iterations {max(q['iterations'] for q in st)}",
+              file=sys.stderr, flush=True)
     # identify the dominant kernel family on one profiled step
     solver.profile()
     solver.profile_reset()
@@ -638,6 +646,7 @@ def main():
         "coarse_iterations_per_solve": stats[-1][0]["coarse_iterations"],
         "max_rel_residual": rel,
         "setup_seconds": t_setup,
+        "setup_rounds": solver.setup_report()[0],
         # one setup serving one batch: the batch's solves over setup + one step's time
         "amortised_incl_setup": {"value": nr / (t_setup + ms / args.steps / 1e3), "unit": "solves/s",
                                  "per": f"one setup and one batch of {nr} right-hand sides"},

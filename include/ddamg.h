@@ -121,6 +121,12 @@ typedef struct {
     int setup_group;      /* the setup updates the test vectors in groups of this many (the
                              updates of one setup round are independent), bounding its work
                              fields to 2 * setup_group fine fields; <= 0: all n_vec at once (0) */
+    int n_inv_auto_rhs;   /* > 0: balance the setup against this many right-hand sides (Sec. 6.2,
+                             Table 4: more setup pays off over more solves).  n_inv becomes a cap;
+                             before every setup round after the first, four FGMRES iterations on
+                             a fixed random right-hand side estimate the iterations per solve,
+                             and the setup stops once the last round saved less solve time over
+                             n_inv_auto_rhs solves than it cost (0: n_inv rounds) */
     int lean;             /* DDAMG_PREC_SINGLE / HALF: 1 = after each setup free the FP64 test
                              vectors and FP64 interpolation (only the setup and ddamg_get_vectors
                              use them; the V-cycle reads its FP32 / FP16 copies): 2 * n_vec FP64
@@ -170,6 +176,12 @@ int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N);
 
 /* Copy the current test vectors (N spinor fields, FP64) into V. */
 int ddamg_get_vectors(const ddamg_handle* h, double* V);
+
+/* The last adaptive setup of the handle: *rounds = update rounds run (n_inv, or fewer when
+ * params.n_inv_auto_rhs stopped it, Sec. 6.2 / Table 4); est_iterations[k] (k < max) = the
+ * estimated FGMRES iterations per solve of the probe before round k (n_inv_auto_rhs > 0 only).
+ * Returns the number of probes (>= 0), or DDAMG_ERR_INVALID_ARG for a null handle or rounds. */
+int ddamg_setup_report(const ddamg_handle* h, int* rounds, double* est_iterations, int max);
 
 /* Solve D z = b to ||b - D z|| <= tol ||b|| by FGMRES(n_kv) right-preconditioned
  * with one V-cycle (Sec. 5); in SINGLE and HALF mode the FGMRES runs as the

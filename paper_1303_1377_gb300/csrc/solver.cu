@@ -265,6 +265,9 @@ struct ddamg_handle {
     ddamg::MLState* ml = nullptr;
     unsigned long long coarse_gen = 0;
     bool ml_route = false;  // set by ddamg_ml_solve: the fine V-cycle takes the recursive coarse solve
+    // last setup: update rounds run, and (n_inv_auto_rhs) the probes' estimated iterations per solve
+    int setup_rounds = 0;
+    std::vector<double> setup_est_iters;
 
     bool single() const { return p.precision != DDAMG_PREC_DOUBLE; }
     bool half() const { return p.precision == DDAMG_PREC_HALF; }
@@ -1156,6 +1159,8 @@ __global__ void gaussian_fill_kernel(double* out, size_t n, unsigned long long s
 }
 
 // Algorithm 2 (Algorithm 1 with the modified update) on vectors in precision T
+static int setup_probe(ddamg_handle* h, double* est_iters, double* sec_per_iter);
+
 template <typename T>
 static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
     cudaStream_t st = h->stream;
@@ -1186,9 +1191,30 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
             DD_TRY((convert<double, T>(reinterpret_cast<const T*>(v), reinterpret_cast<double*>(h->V64), 2 * fld * N, st)));
         return 0;
     };
+    // n_inv_auto_rhs: before every round after the first, a probe estimates the iterations per
+    // solve with the current interpolation; stop once the last round saved less solve time over
+    // n_inv_auto_rhs solves than it cost (P, D_c then stay those just built from the vectors)
+    const int auto_rhs = h->p.n_inv_auto_rhs;
+    double prev_est = -1.0, round_sec = 0.0;
+    bool stopped = false;
+    h->setup_rounds = 0;
+    h->setup_est_iters.clear();
     for (int it = 0; it < h->p.n_inv; ++it) {
+        const auto t_round = std::chrono::steady_clock::now();
         DD_TRY(to64());
         DD_TRY(build_interpolation(h));
+        if (auto_rhs > 0) {
+            double est = 0, sec_it = 0;
+            const auto t_probe = std::chrono::steady_clock::now();
+            DD_TRY(setup_probe(h, &est, &sec_it));
+            h->setup_est_iters.push_back(est);
+            if (prev_est > 0 && (double)auto_rhs * (prev_est - est) * sec_it < round_sec) {
+                stopped = true;
+                break;
+            }
+            prev_est = est;
+            round_sec = -std::chrono::duration<double>(std::chrono::steady_clock::now() - t_probe).count();
+        }
         for (int j0 = 0; j0 < N; j0 += G) {
             const int g = std::min(G, N - j0);
             cplx<T>* vg = v + (size_t)j0 * fld;
@@ -1218,7 +1244,12 @@ static int run_setup_T(ddamg_handle* h, cplx<T>* v) {
         }
         DD_CUDA(cudaMemcpyAsync(kb.scale, nn.data(), sizeof(cplx<double>) * N, cudaMemcpyHostToDevice, st));
         DD_TRY((lincomb<T, T>(v, fld, 0.0, v, 0, fld, 1, kb.scale, N, fld, N, nullptr, st)));
+        DD_CUDA(cudaStreamSynchronize(st));
+        ++h->setup_rounds;
+        // the round's cost: rebuild and updates (the probe's own time excluded)
+        round_sec += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_round).count();
     }
+    if (stopped) return 0;
     DD_TRY(to64());
     if (h->p.rebuild_after_last || h->p.n_inv == 0) DD_TRY(build_interpolation(h));
     return 0;
@@ -1371,6 +1402,38 @@ static int tc_check(ddamg_handle* h) {
         set_error("coarse stencil: a bulk copy of the site matrix did not complete within the kernel's wait limit");
         return DDAMG_ERR_CUDA;
     }
+    return 0;
+}
+
+// four FGMRES iterations of the handle's solver from the zero guess on a fixed Gaussian right-hand side
+// (seeded from params.seed): the residual reduction per iteration rho gives the estimated iterations
+// to params.tol, log(tol) / log(rho); sec_per_iter is the probe's wall time per iteration
+static int setup_probe(ddamg_handle* h, double* est_iters, double* sec_per_iter) {
+    constexpr int kProbeIters = 4;
+    const size_t fld = (size_t)12 * h->V;
+    Scratch bx;
+    DD_TRY(bx.ensure(sizeof(cplx<double>) * fld * 2));
+    cplx<double>* b = bx.as<cplx<double>>();
+    cplx<double>* x = b + fld;
+    gaussian_fill_kernel<<<1216, 256, 0, h->stream>>>(reinterpret_cast<double*>(b), 2 * fld, h->p.seed + 977);
+    DD_CHECK_LAUNCH();
+    const int saved = h->p.max_outer;
+    h->p.max_outer = kProbeIters;
+    KrylovResult R;
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = !h->single() ? solve_T<double, double>(h, b, x, 1, 1e-300, true, R)
+             : h->p.outer == DDAMG_OUTER_REFINE ? solve_T<float, float>(h, b, x, 1, 1e-300, true, R)
+                                                : solve_T<float, dwf>(h, b, x, 1, 1e-300, true, R);
+    DD_CUDA(cudaStreamSynchronize(h->stream));
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    h->p.max_outer = saved;
+    if (rc) return rc;
+    const double its = std::max<double>(1.0, (double)R.iters[0]);
+    const double red = R.resid[0] > 0 ? R.resid[0] : 1e-300;
+    const double rho = std::min(0.999999, std::pow(red, 1.0 / its));
+    *est_iters = std::log(h->p.tol) / std::log(rho);
+    *sec_per_iter = sec / its;
     return 0;
 }
 
@@ -1571,6 +1634,7 @@ void ddamg_default_params(ddamg_params* p) {
     p->setup_update = DDAMG_SETUP_DDALPHA;
     p->smoother_fp16 = 1;
     p->setup_group = 0;
+    p->n_inv_auto_rhs = 0;
     p->lean = 0;
 }
 
@@ -1630,6 +1694,14 @@ int ddamg_setup_from_vectors(ddamg_handle* h, const double* V, int N) {
     DD_TRY(build_interpolation(h));
     lean_release(h);
     return 0;
+}
+
+int ddamg_setup_report(const ddamg_handle* h, int* rounds, double* est_iterations, int max) {
+    if (!h || !rounds) return DDAMG_ERR_INVALID_ARG;
+    *rounds = h->setup_rounds;
+    const int n = (int)h->setup_est_iters.size();
+    for (int k = 0; k < n && k < max && est_iterations; ++k) est_iterations[k] = h->setup_est_iters[k];
+    return n;
 }
 
 int ddamg_get_vectors(const ddamg_handle* hc, double* V) {

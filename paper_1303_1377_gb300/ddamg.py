@@ -71,6 +71,7 @@ class Params(C.Structure):
         ("setup_update", C.c_int),
         ("smoother_fp16", C.c_int),
         ("setup_group", C.c_int),
+        ("n_inv_auto_rhs", C.c_int),
         ("lean", C.c_int),
     ]
 
@@ -130,6 +131,7 @@ def _load():
         "ddamg_run_setup": (I, [P, P]),
         "ddamg_setup_from_vectors": (I, [P, P, I]),
         "ddamg_get_vectors": (I, [P, P]),
+        "ddamg_setup_report": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_double), I]),
         "ddamg_solve": (I, [P, P, P, D, C.POINTER(Stats)]),
         "ddamg_solve_batch": (I, [P, P, P, I, D, C.POINTER(Stats)]),
         "ddamg_solve_batch_zero_guess": (I, [P, P, P, I, D, C.POINTER(Stats)]),
@@ -298,6 +300,16 @@ class Solver:
         out = np.empty((self.params.n_vec, self.V, 4, 3), dtype=np.complex128)
         _check(lib.ddamg_get_vectors(self.h, _ptr(out)), "ddamg_get_vectors")
         return out
+
+    def setup_report(self):
+        """(update rounds of the last setup, estimated iterations per solve before each round when
+        params.n_inv_auto_rhs balanced it)."""
+        rounds = C.c_int(0)
+        est = (C.c_double * 64)()
+        n = lib.ddamg_setup_report(self.h, C.byref(rounds), est, 64)
+        if n < 0:
+            _check(n, "ddamg_setup_report")
+        return rounds.value, [est[k] for k in range(min(n, 64))]
 
     def set_mass(self, m0: float):
         _check(lib.ddamg_set_mass(self.h, float(m0)), "ddamg_set_mass")

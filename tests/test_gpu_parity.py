@@ -503,3 +503,27 @@ def test_grouped_setup_and_lean_handle(dd):
     assert relerr(z, z_g) < 1e-12
     for q in range(2):
         assert np.linalg.norm(b[q] - c.D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])
+
+
+def test_n_inv_balanced_by_right_hand_sides(dd):
+    """params.n_inv_auto_rhs (Sec. 6.2, Table 4): without it the setup runs n_inv rounds and probes
+    nothing; with one right-hand side to amortise the setup over, the probe-driven setup stops no
+    later than with a million; both run at most n_inv rounds, report one probe per round started,
+    and the solve still reaches 1e-10."""
+    c = case("8^4/4^4", dd)
+    b = synth.gaussian_spinors(c.dims, 1, seed=127)
+    p = dd.default_params(n_vec=c.N, block=c.block, precision=dd.PREC_SINGLE, nu=2, n_inv=6)
+    with dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False) as s:
+        s.run_setup(c.v)
+        assert s.setup_report() == (6, [])
+    rounds = {}
+    for nrhs in (1, 10 ** 6):
+        p = dd.default_params(n_vec=c.N, block=c.block, precision=dd.PREC_SINGLE, nu=2, n_inv=6, n_inv_auto_rhs=nrhs)
+        with dd.Solver(c.dims, c.U, c.m0, CSW, p, setup=False) as s:
+            s.run_setup(c.v)
+            r, est = s.setup_report()
+            z, st, rc = s.solve(b)
+        assert rc == 0 and np.linalg.norm(b[0] - c.D.apply(z[0])) <= 1e-10 * np.linalg.norm(b[0])
+        assert 1 <= r <= 6 and len(est) in (r, r + 1) and all(e > 0 for e in est)
+        rounds[nrhs] = r
+    assert rounds[1] <= rounds[10 ** 6]

@@ -303,7 +303,9 @@ def run_reference(args, w):
 def run_profile_case(args):
     """Build D for a synthetic gauge field and an interpolation from seeded random test vectors, then
     apply one SAP iteration, three steps of the odd-even coarse GMRES, one double-word Dslash, one FP32
-    Dslash, one restriction and one prolongation to nrhs right-hand sides resident on the GPU."""
+    Dslash, one restriction and one prolongation to nrhs right-hand sides resident on the GPU; with
+    --levels 3 also a level 2 from seeded random level-1 vectors, one level-1 SAP iteration, two
+    level-1 restrictions, one level-2 operator product and one level-1 prolongation."""
     import torch
 
     from paper_1303_1377_gb300 import ddamg, synth
@@ -322,6 +324,13 @@ def run_profile_case(args):
         s.apply_D_mixed(x.to(torch.complex64))
         s.apply_D_f32(x.to(torch.complex64))
     s.prolong(s.restrict(x))
+    if args.levels == 3:  # level-1 SAP colour steps, restriction, prolongation and level-2 operator
+        mlp = ddamg.ml_default_params()
+        s.ml_build(synth.gaussian_coarse(s.n_coarse, s.coarse_dof, mlp.n_vec1, 6), mlp)
+        e = torch.from_numpy(synth.gaussian_coarse(s.n_coarse, s.coarse_dof, args.nrhs, 7)).cuda()
+        s.ml_apply_sap1(e, 1)
+        s.ml_apply_D2(s.ml_restrict1(e))
+        s.ml_prolong1(s.ml_restrict1(e))
     torch.cuda.synchronize()
     s.close()
     print("ok")
@@ -419,8 +428,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream (continuous batching over four operators)")
     ap.add_argument("--serving-seconds", type=float, default=20.0)
     ap.add_argument("--no-small", action="store_true", help="skip the 8^4 and 16^4 configurations")
+    ap.add_argument("--no-two-level", action="store_true", help="skip the two-level solve on the three-level handle")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
-    ap.add_argument("--levels", type=int, default=None, choices=[2, 3],
+    ap.add_argument("--levels", type=int, default=None, choices=[2, 3],  # with --profile-case: 3 adds the level-1 kernels
                     help="2 or 3 (the recursion to a third level: level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup); "
                          "default: the workload's")
     ap.add_argument("--ml-inner", default=None, choices=["fgmres", "vcycle"],
@@ -537,17 +547,19 @@ def main():
     # whole-job throughput: solves summed over the replicas / slowest replica's time
     value, ms, _ = aggregate(ms, nr * args.steps, dist=dist, device="cuda")
     # residual check of the last solve, in FP64 through the library's D
+    # (one right-hand side at a time on memory-lean workloads, beside the solver's resident work space)
     rel = 0.0
-    for g0 in range(0, nr, group):
-        r = b[g0:g0 + group] - solver.apply_D(z[g0:g0 + group])
+    chk = 1 if w.get("lean") else group
+    for g0 in range(0, nr, chk):
+        r = b[g0:g0 + chk] - solver.apply_D(z[g0:g0 + chk])
         ng = r.shape[0]
         rel = max(rel, (torch.linalg.vector_norm(r.reshape(ng, -1), dim=1) /
-                        torch.linalg.vector_norm(b[g0:g0 + group].reshape(ng, -1), dim=1)).max().item())
+                        torch.linalg.vector_norm(b[g0:g0 + chk].reshape(ng, -1), dim=1)).max().item())
         del r
     # the two-level solve on the same handle (the fine V-cycle with the odd-even GMRES on D_c), for
     # comparison with the recursion
     two_level = None
-    if args.levels == 3 and args.workload.startswith("32x32x32x64"):
+    if args.levels == 3 and args.workload.startswith("32x32x32x64") and not args.no_two_level:
         step(solver.solve_zero_guess)
         t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0e.record(stream)
@@ -561,7 +573,7 @@ def main():
                      "coarse_solve": "odd-even GMRES(30) on D_c to 5e-2 (tensor-core stencil)"}
     # Dslash bandwidth at the workload's size and right-hand sides (half of the headline metric):
     # kernel time from CUDA events around each Dslash launch, algorithmic bytes per launch
-    dslash_rates = measure_dslash(solver, b[:group], peaks()[0])
+    dslash_rates = measure_dslash(solver, b[:chk], peaks()[0])
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region: b goes
     # in, z comes out; the zero-guess entry point never reads z (the paper's zero initial guess)
     e2e = None

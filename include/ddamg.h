@@ -95,9 +95,9 @@ typedef struct {
     int n_vec;            /* test vectors N (20) */
     int block[4];         /* lattice-block of both the SAP domains and the aggregates (4,4,4,4) */
     double coarse_tol;    /* relative residual reduction of the coarse solve (5e-2) */
-    int coarse_restart;   /* GMRES restart length on the coarse system (30, Sec. 6) */
+    int coarse_restart;   /* GMRES restart length on the coarse system (30, Sec. 6; at most 64) */
     int coarse_maxiter;   /* cap on coarse GMRES steps per coarse solve (1000) */
-    int n_kv;             /* FGMRES restart length (25) */
+    int n_kv;             /* FGMRES restart length (25; at most 64) */
     double tol;           /* outer relative residual tolerance (1e-10) */
     int max_outer;        /* cap on FGMRES iterations per solve (10000) */
     int nu;               /* SAP post-smoothing iterations (2) */
@@ -359,11 +359,11 @@ typedef struct {
     int nu1;            /* SAP iterations of the level-1 V-cycle (2) */
     int mr_steps1;      /* MR steps of its block solver (4) */
     int inner;          /* 0: FGMRES on D_1 with the level-1 V-cycle; 1: one level-1 V-cycle (0) */
-    int inner_kv;       /* restart length of that FGMRES (10) */
+    int inner_kv;       /* restart length of that FGMRES (10; at most 64) */
     double inner_tol;   /* its relative residual target (5e-2) */
     int inner_maxiter;  /* cap on its iterations per solve (1000) */
     double coarse_tol;  /* relative residual target of the odd-even GMRES on D_2 (5e-2) */
-    int coarse_restart; /* its restart length (30) */
+    int coarse_restart; /* its restart length (30; at most 64) */
     int coarse_maxiter; /* cap on its iterations per solve (1000) */
     int n_inv1;         /* rounds of the level-1 setup of ddamg_ml_setup (6) */
     int setup_update1;  /* ddamg_setup_update of those rounds (DDAMG_SETUP_DDALPHA) */

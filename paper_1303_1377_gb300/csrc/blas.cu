@@ -225,53 +225,68 @@ int gauge_to_internal(const cplx<double>* in, cplx<double>* out, const int* lex_
 
 // Hessenberg bookkeeping of batched (F)GMRES: one thread per right-hand side.
 // Column k of H arrives in hcol[i * nrhs + r] (i <= k) with hnorm = ||w|| in hcol[(k+1) * nrhs + r].
-__global__ void arnoldi_update_kernel(KrylovState s, int k, const cplx<double>* __restrict__ hcol, cplx<double>* __restrict__ scale) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= s.nrhs) return;
+// One warp per right-hand side: the lanes fetch the new Hessenberg column and the stored rotations
+// side by side into shared memory, lane 0 applies the rotations in order (the only sequential part),
+// and the lanes write the column back.
+constexpr int kArnoldiMaxM = 64;
+__global__ void __launch_bounds__(32) arnoldi_update_kernel(KrylovState s, int k, const cplx<double>* __restrict__ hcol,
+                                                            cplx<double>* __restrict__ scale) {
+    const int r = blockIdx.x, lane = threadIdx.x;
     const int m = s.m;
     cplx<double>* H = s.H + (size_t)r * (m + 1) * m;  // H[i * m + k]
     if (!s.active[r]) {
-        scale[r] = mk(0.0, 0.0);
+        if (lane == 0) scale[r] = mk(0.0, 0.0);
         return;
     }
-    for (int i = 0; i <= k; ++i) H[i * m + k] = hcol[(size_t)i * s.nrhs + r];
-    double hk = sqrt(hcol[(size_t)(k + 1) * s.nrhs + r].re);
-    // apply the previous rotations
-    for (int i = 0; i < k; ++i) {
-        double c = s.cs[r * m + i];
-        cplx<double> sn = s.sn[r * m + i];
-        cplx<double> a = H[i * m + k], b = H[(i + 1) * m + k];
-        H[i * m + k] = c * a + sn * b;
-        H[(i + 1) * m + k] = c * b - conj(sn) * a;
+    __shared__ cplx<double> col[kArnoldiMaxM + 1], sn_s[kArnoldiMaxM];
+    __shared__ double cs_s[kArnoldiMaxM];
+    for (int i = lane; i <= k + 1; i += 32) col[i] = hcol[(size_t)i * s.nrhs + r];
+    for (int i = lane; i < k; i += 32) {
+        cs_s[i] = s.cs[r * m + i];
+        sn_s[i] = s.sn[r * m + i];
     }
-    cplx<double> a = H[k * m + k];
-    double na = sqrt(norm2(a));
-    double den = sqrt(na * na + hk * hk);
-    double c;
-    cplx<double> sn;
-    if (den == 0.0) {
-        c = 1.0;
-        sn = mk(0.0, 0.0);
-    } else if (na == 0.0) {
-        c = 0.0;
-        sn = mk(1.0, 0.0);
-    } else {
-        c = na / den;
-        sn = (hk / (na * den)) * a;  // (a/|a|) conj(hk)/den, hk real
+    __syncwarp();
+    if (lane == 0) {
+        const double hk = sqrt(col[k + 1].re);
+        // apply the previous rotations
+        for (int i = 0; i < k; ++i) {
+            const double c = cs_s[i];
+            const cplx<double> sn = sn_s[i];
+            const cplx<double> a = col[i], b = col[i + 1];
+            col[i] = c * a + sn * b;
+            col[i + 1] = c * b - conj(sn) * a;
+        }
+        const cplx<double> a = col[k];
+        const double na = sqrt(norm2(a));
+        const double den = sqrt(na * na + hk * hk);
+        double c;
+        cplx<double> sn;
+        if (den == 0.0) {
+            c = 1.0;
+            sn = mk(0.0, 0.0);
+        } else if (na == 0.0) {
+            c = 0.0;
+            sn = mk(1.0, 0.0);
+        } else {
+            c = na / den;
+            sn = (hk / (na * den)) * a;  // (a/|a|) conj(hk)/den, hk real
+        }
+        s.cs[r * m + k] = c;
+        s.sn[r * m + k] = sn;
+        col[k] = c * a + hk * sn;
+        const cplx<double> gk = s.g[r * (m + 1) + k];
+        s.g[r * (m + 1) + k + 1] = -1.0 * (conj(sn) * gk);
+        s.g[r * (m + 1) + k] = c * gk;
+        const double est = sqrt(norm2(s.g[r * (m + 1) + k + 1]));
+        s.steps[r] = k + 1;
+        s.resid[r] = est;
+        const bool nonfinite = !(est == est) || !(hk == hk);
+        if (nonfinite) s.flags[r] |= 2;
+        if (est <= s.ctarget[r] || nonfinite) s.active[r] = 0;
+        scale[r] = (hk > 0.0 && s.active[r]) ? mk(1.0 / hk, 0.0) : mk(0.0, 0.0);
     }
-    s.cs[r * m + k] = c;
-    s.sn[r * m + k] = sn;
-    H[k * m + k] = c * a + hk * sn;
-    cplx<double> gk = s.g[r * (m + 1) + k];
-    s.g[r * (m + 1) + k + 1] = -1.0 * (conj(sn) * gk);
-    s.g[r * (m + 1) + k] = c * gk;
-    double est = sqrt(norm2(s.g[r * (m + 1) + k + 1]));
-    s.steps[r] = k + 1;
-    s.resid[r] = est;
-    bool nonfinite = !(est == est) || !(hk == hk);
-    if (nonfinite) s.flags[r] |= 2;
-    if (est <= s.ctarget[r] || nonfinite) s.active[r] = 0;
-    scale[r] = (hk > 0.0 && s.active[r]) ? mk(1.0 / hk, 0.0) : mk(0.0, 0.0);
+    __syncwarp();
+    for (int i = lane; i <= k; i += 32) H[i * m + k] = col[i];
 }
 
 // y = H^{-1} g (upper triangular, steps[r] columns); y stored as coef[i * nrhs + r]
@@ -315,7 +330,8 @@ int arnoldi_start(const KrylovState& s, const cplx<double>* nrm2, cplx<double>* 
     return 0;
 }
 int arnoldi_update(const KrylovState& s, int k, const cplx<double>* hcol, cplx<double>* scale, cudaStream_t st) {
-    arnoldi_update_kernel<<<ceil_div(s.nrhs, 64), 64, 0, st>>>(s, k, hcol, scale);
+    if (s.m > kArnoldiMaxM || k >= s.m) return DDAMG_ERR_INVALID_ARG;
+    arnoldi_update_kernel<<<s.nrhs, 32, 0, st>>>(s, k, hcol, scale);
     DD_CHECK_LAUNCH();
     return 0;
 }
@@ -530,6 +546,26 @@ __device__ __forceinline__ bool last_cta_of_rhs(unsigned* ticket, int r, int cta
     return last;
 }
 
+// Reduce-scatter of NV = 2 KB per-lane FP32 values across a warp (NV a power of two, <= 32): on
+// return v[0] of lane l holds the sum over the 32 lanes of value (l mod NV).  Each halving step
+// sends the half of the live values that the partner lane keeps, so the whole reduction costs
+// NV - 1 shuffles (plus log2(32 / NV) for the lanes beyond NV) instead of 5 NV.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+    for (int s = NV / 2; s >= 1; s >>= 1) {
+        const bool upper = lane & s;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const float send = upper ? v[j] : v[j + s];
+            const float keep = upper ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+#pragma unroll
+    for (int s = NV; s < 32; s <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], s);
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4* __restrict__ A, size_t istride4, size_t arstride4, int k,
                                                                    const float4* __restrict__ w, size_t wrstride4, size_t n4, int nrhs,
@@ -537,48 +573,48 @@ __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4*
                                                                    cplx<double>* __restrict__ out, int ostride_i, cplx<double>* __restrict__ copy_last,
                                                                    const int* __restrict__ run_flag) {
     if (run_flag && !*run_flag) return;
+    constexpr int NV = 2 * KB;  // (re, im) of each product, interleaved: v[2 i], v[2 i + 1]
     const int r = blockIdx.x % nrhs;
     const int part = blockIdx.x / nrhs;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const float4* Ar = A + r * arstride4;
     const float4* wr = w + r * wrstride4;
-    float fr[KB], fi[KB];
-    double dr[KB], di[KB];
+    // every kFlush steps the warp's FP32 sums are reduce-scattered and lane (q mod NV) adds the sum of
+    // value q to its one FP64 accumulator: FP64 state is one register per lane, whatever KB
+    float f[NV];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) fr[q] = fi[q] = 0.f, dr[q] = di[q] = 0.0;
+    for (int q = 0; q < NV; ++q) f[q] = 0.f;
+    double acc = 0.0;
     const size_t stride = (size_t)ctas_per_rhs * blockDim.x;
-    int cnt = 0;
-    for (size_t e = (size_t)part * blockDim.x + threadIdx.x; e < n4; e += stride) {
-        const float4 wv = wr[e];
+    const size_t e0 = (size_t)part * blockDim.x + threadIdx.x;
+    // the trip count is uniform across the warp (the flush needs all 32 lanes): lanes past the end
+    // run the last trips with zero products
+    const size_t base = e0 - lane;
+    const size_t trips = base < n4 ? (n4 - base + stride - 1) / stride : 0;
+    for (size_t t = 0; t < trips;) {
+        const size_t tend = t + kFlush < trips ? t + kFlush : trips;
+        for (; t < tend; ++t) {
+            const size_t e = e0 + t * stride;
+            if (e < n4) {
+                const float4 wv = wr[e];
 #pragma unroll
-        for (int i = 0; i < KB; ++i) {
-            if (i < k) {
-                const float4 a = Ar[i * istride4 + e];  // conj(a) w for both complex numbers
-                // two independent products per component keep the accumulator chain two FMAs deep
-                fr[i] += fmaf(a.x, wv.x, a.y * wv.y) + fmaf(a.z, wv.z, a.w * wv.w);
-                fi[i] += fmaf(a.x, wv.y, -a.y * wv.x) + fmaf(a.z, wv.w, -a.w * wv.z);
+                for (int i = 0; i < KB; ++i) {
+                    if (i < k) {
+                        const float4 a = Ar[i * istride4 + e];  // conj(a) w for both complex numbers
+                        // two independent products per component keep the accumulator chain two FMAs deep
+                        f[2 * i] += fmaf(a.x, wv.x, a.y * wv.y) + fmaf(a.z, wv.z, a.w * wv.w);
+                        f[2 * i + 1] += fmaf(a.x, wv.y, -a.y * wv.x) + fmaf(a.z, wv.w, -a.w * wv.z);
+                    }
+                }
             }
         }
-        if (++cnt == kFlush) {
-            cnt = 0;
+        warp_reduce_scatter<NV>(f, lane);
+        acc += (double)f[0];
 #pragma unroll
-            for (int i = 0; i < KB; ++i) dr[i] += fr[i], di[i] += fi[i], fr[i] = fi[i] = 0.f;
-        }
+        for (int q = 0; q < NV; ++q) f[q] = 0.f;
     }
-#pragma unroll
-    for (int i = 0; i < KB; ++i) dr[i] += fr[i], di[i] += fi[i];
-    __shared__ double red[kDotThreads / 32][2 * KB];
-    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int i = 0; i < KB; ++i) {
-        if (i < k) {
-            double vr = warp_sum(dr[i]);
-            double vi = warp_sum(di[i]);
-            if (lane == 0) {
-                red[wi][2 * i] = vr;
-                red[wi][2 * i + 1] = vi;
-            }
-        }
-    }
+    __shared__ double red[kDotThreads / 32][NV];
+    if (lane < NV) red[wi][lane] = acc;
     __syncthreads();
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) {
         double s = 0;
@@ -586,15 +622,21 @@ __global__ void __launch_bounds__(kDotThreads) multidot_f32_kernel(const float4*
         partial[((size_t)blockIdx.x) * 2 * k + q] = s;
     }
     if (!last_cta_of_rhs(ticket, r, ctas_per_rhs)) return;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    // one warp per product: its lanes read the CTAs' partial sums side by side (fixed order, so the
+    // result does not depend on which CTA finished last)
+    for (int i = wi; i < k; i += kDotThreads / 32) {
         double re = 0, im = 0;
-        for (int p = 0; p < ctas_per_rhs; ++p) {
+        for (int p = lane; p < ctas_per_rhs; p += 32) {
             const double* src = partial + ((size_t)(p * nrhs + r)) * 2 * k;
             re += __ldcg(src + 2 * i);
             im += __ldcg(src + 2 * i + 1);
         }
-        out[(size_t)i * ostride_i + r] = mk(re, im);
-        if (copy_last && i == k - 1) copy_last[r] = mk(re, im);
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) {
+            out[(size_t)i * ostride_i + r] = mk(re, im);
+            if (copy_last && i == k - 1) copy_last[r] = mk(re, im);
+        }
     }
     if (threadIdx.x == 0) ticket[r] = 0u;
 }

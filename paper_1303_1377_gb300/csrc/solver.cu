@@ -1465,12 +1465,13 @@ static int create(const ddamg_lattice* lat, const double* U, double m0, double c
             return DDAMG_ERR_INVALID_ARG;
         }
     }
-    if (p.n_vec < 1 || p.n_vec > 32 || p.nu < 0 || p.mr_steps < 0 || p.n_kv < 1 || p.coarse_restart < 1 ||
+    if (p.n_vec < 1 || p.n_vec > 32 || p.nu < 0 || p.mr_steps < 0 || p.n_kv < 1 || p.n_kv > 64 || p.coarse_restart < 1 ||
+        p.coarse_restart > 64 ||
         p.precision < DDAMG_PREC_DOUBLE || p.precision > DDAMG_PREC_HALF || p.n_inv < 0 ||
         (p.outer != DDAMG_OUTER_DW && p.outer != DDAMG_OUTER_REFINE) ||
         (p.outer == DDAMG_OUTER_REFINE && !(p.cycle_tol > 0 && p.cycle_tol < 1)) ||
         (p.setup_update != DDAMG_SETUP_DDALPHA && p.setup_update != DDAMG_SETUP_IDSETUP)) {
-        set_error("parameter out of range (1 <= n_vec <= 32, n_kv >= 1, coarse_restart >= 1, nu, mr_steps, n_inv >= 0, "
+        set_error("parameter out of range (1 <= n_vec <= 32, 1 <= n_kv <= 64, 1 <= coarse_restart <= 64, nu, mr_steps, n_inv >= 0, "
                   "outer in {0, 1}, 0 < cycle_tol < 1, setup_update in {0, 1})");
         return DDAMG_ERR_INVALID_ARG;
     }

@@ -192,3 +192,35 @@ def test_four_levels():
     assert rc == 0
     assert np.linalg.norm(b[0] - D.apply(z[0])) <= 1e-10 * np.linalg.norm(b[0])
     assert np.linalg.norm(z[0] - zo) <= 1e-8 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("prec,tol", [("SINGLE", 1e-6), ("HALF", 4e-3)])
+def test_coarsest_operator_at_benchmark_shape(prec, tol):
+    """D_2 with 2 N_1 = 40 components per site and 12 right-hand sides, the shape of the benchmark's
+    coarsest level: a SINGLE handle applies it in FP32, a HALF handle through the FP16 tensor-core
+    stencil that its odd-even GMRES uses (one FP16 rounding per stored entry; stated tolerance 4e-3
+    relative to the field maximum, as for the level-1 stencil).  A three-level solve on the HALF
+    handle still reaches a true residual of 1e-10 under the oracle's D."""
+    from paper_1303_1377_gb300 import ddamg
+
+    blk, n0, n1, nr = (2, 2, 2, 2), 20, 20, 12
+    U = synth.gauge_field(DIMS, 0.5, seed=141)
+    D = DiracOperator(U, DIMS, M0, CSW)
+    v0 = synth.random_test_vectors(DIMS, n0, seed=142)
+    v1 = synth.gaussian_coarse(4 ** 4, 2 * n0, n1, seed=143)
+    ml = MultiLevel(D, [OParams(N=n0, agg_block=blk, sap_block=blk, nu=2), OParams(N=n1, agg_block=blk, sap_block=blk, nu=2)])
+    ml.build([v0, v1])
+    e = synth.gaussian_coarse(2 ** 4, 2 * n1, nr, seed=144)
+    ref = np.stack([ml.levels[1].Dc.apply(e[r]) for r in range(nr)])
+    p = ddamg.default_params(n_vec=n0, block=blk, precision=getattr(ddamg, "PREC_" + prec), nu=2)
+    b = synth.gaussian_spinors(DIMS, 4, seed=145)
+    with ddamg.Solver(DIMS, U, M0, CSW, p, setup=False) as s:
+        s.setup_from_vectors(v0)
+        s.ml_build(v1, ddamg.ml_default_params(block1=blk, n_vec1=n1, nu1=2))
+        assert rel(s.ml_apply_D2(e), ref) < tol
+        assert rel(s.ml_apply_D2(e[:5]), ref[:5]) < tol
+        z, st, rc = s.ml_solve(b)
+        counts = s.ml_counts()
+    assert rc == 0 and counts["gmres_steps_D2"] > 0
+    for q in range(4):
+        assert np.linalg.norm(b[q] - D.apply(z[q])) <= 1e-10 * np.linalg.norm(b[q])

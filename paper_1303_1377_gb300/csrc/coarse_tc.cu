@@ -166,15 +166,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 // One CTA per coarse site with two warps per m-tile: warp w < Mt owns m-tile w (rows 16w..16w+15 of
 // [Re; Im]) in the tensor-core product; all 2 Mt warps gather and convert the right-hand sides and
 // write the result.
+// SPLIT: each right-hand-side entry x is staged as two FP16 numbers, hi = fp16(x) and
+// lo = fp16(2^11 (x - hi)), and multiplied by both (P = A hi + 2^-11 A lo), so the product is that of
+// the FP16-rounded matrix with x to about 2^-22 relative instead of 2^-11.  The operator then stays
+// one fixed linear map, which a Krylov solver on an ill-conditioned coarsest level needs: with the
+// inputs rounded to FP16 its residual estimate and the true residual drift apart.
 //   acc = self + hop_sign * sum_{d=1..8} B_d(c) xin[nbr_d(c)]; self = 0 / B_0 xself / xself;
 //   out = apply_inv ? Dinv acc : acc       (same modes as the CUDA-core kernel)
 // The site's FP16 matrix (the k-tiles this call uses, and D_ee^{-1} when applied) is brought into
 // shared memory by bulk copies issued first, so that HBM streams it while the CTA gathers the
 // right-hand sides of the neighbouring sites (L2 hits) and converts them to FP16.
-template <int NRP>
+constexpr float kLoScale = 2048.f;  // 2^11: the low FP16 part of a split entry, scaled into the normal range
+
+// x -> (hi, lo) for the SPLIT staging of two values
+__device__ __forceinline__ void split_half2(float a, float b, __half2& hi, __half2& lo) {
+    hi = __floats2half2_rn(a, b);
+    const float2 h = __half22float2(hi);
+    lo = __floats2half2_rn((a - h.x) * kLoScale, (b - h.y) * kLoScale);
+}
+
+template <int NRP, bool SPLIT>
 __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site_begin, CVecT<float> xin, CVecT<float> xself, int self_mode,
                                                           float hop_sign, int apply_inv, CVecT<float> out, int nrhs) {
     constexpr int NT = NRP / 4;  // n-tiles of 8 columns over [Re X | Im X] (2 NRP columns)
+    constexpr int NPL = SPLIT ? 2 : 1;  // staged planes: hi (and lo)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = op.nc, Mt = op.Mt;
     const int Kp = op.Kt_all * 16;
@@ -187,8 +202,9 @@ __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site
     int* snb = reinterpret_cast<int*>(smem_raw + 8);                       // [8] neighbouring sites
     uint4* As = reinterpret_cast<uint4*>(smem_raw + 64);                    // [Mt][nkt][32]
     uint4* Ds = As + (size_t)Mt * nkt * 32;                                 // [Mt][Kt_d][32]
-    __half* XT = reinterpret_cast<__half*>(Ds + (apply_inv ? (size_t)Mt * op.Kt_d * 32 : 0));  // [2 NRP][LDX]
-    float* Cs = reinterpret_cast<float*>(XT + (size_t)2 * NRP * LDX);      // [2nc][2 NRP]
+    __half* XT = reinterpret_cast<__half*>(Ds + (apply_inv ? (size_t)Mt * op.Kt_d * 32 : 0));  // [NPL][2 NRP][LDX]
+    __half* XL = XT + (size_t)2 * NRP * LDX;                                // the lo plane (SPLIT)
+    float* Cs = reinterpret_cast<float*>(XT + (size_t)NPL * 2 * NRP * LDX);  // [2nc][2 NRP]
     cplx<float>* Vs = reinterpret_cast<cplx<float>*>(Cs + (size_t)2 * nc * 2 * NRP);  // [nc][NRP]
     const int c = site_begin + blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -233,8 +249,18 @@ __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site
                 if (q < tot) {
                     const int kk = k0 + 2 * (q % kh), r = q / kh;
                     const float sg = kk < 8 * nc ? hop_sign : 1.f;
-                    *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = __floats2half2_rn(sg * v[j].x, sg * v[j].z);
-                    *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = __floats2half2_rn(sg * v[j].y, sg * v[j].w);
+                    if constexpr (SPLIT) {
+                        __half2 h, l;
+                        split_half2(sg * v[j].x, sg * v[j].z, h, l);
+                        *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = h;
+                        *reinterpret_cast<__half2*>(XL + (size_t)r * LDX + kk) = l;
+                        split_half2(sg * v[j].y, sg * v[j].w, h, l);
+                        *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = h;
+                        *reinterpret_cast<__half2*>(XL + (size_t)(NRP + r) * LDX + kk) = l;
+                    } else {
+                        *reinterpret_cast<__half2*>(XT + (size_t)r * LDX + kk) = __floats2half2_rn(sg * v[j].x, sg * v[j].z);
+                        *reinterpret_cast<__half2*>(XT + (size_t)(NRP + r) * LDX + kk) = __floats2half2_rn(sg * v[j].y, sg * v[j].w);
+                    }
                 }
             }
         }
@@ -248,23 +274,39 @@ __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site
         }
         return;
     }
-    float acc[NT][4];
+    float acc[NT][4], acl[NT][4];
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = acl[n][0] = acl[n][1] = acl[n][2] = acl[n][3] = 0.f;
     const bool mma_warp = w < Mt;
-    if (mma_warp) {
-        const uint4* Ab = As + (size_t)w * nkt * 32 + lane;
+    // P += A X for the A fragments in As (k-tiles [ka, kb), staged columns from kx0 on); the lo plane
+    // goes to acl and is folded in by fold()
+    auto gemm = [&](const uint4* Ab, int nk, int kx0) {
 #pragma unroll 4
-        for (int kt = kt0; kt < kt1; ++kt) {
-            const uint4 a = Ab[(size_t)(kt - kt0) * 32];
+        for (int kt = 0; kt < nk; ++kt) {
+            const uint4 a = Ab[(size_t)kt * 32];
 #pragma unroll
             for (int n = 0; n < NT; ++n) {
-                const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
-                unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
-                unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
-                mma16816(acc[n], a, b0, b1);
+                const size_t xo = (size_t)(n * 8 + g) * LDX + (kx0 + kt) * 16 + 2 * t;
+                mma16816(acc[n], a, *reinterpret_cast<const unsigned*>(XT + xo), *reinterpret_cast<const unsigned*>(XT + xo + 8));
+                if constexpr (SPLIT)
+                    mma16816(acl[n], a, *reinterpret_cast<const unsigned*>(XL + xo), *reinterpret_cast<const unsigned*>(XL + xo + 8));
             }
         }
+    };
+    auto fold = [&]() {
+        if constexpr (SPLIT) {
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[n][i] += acl[n][i] * (1.f / kLoScale);
+                    acl[n][i] = 0.f;
+                }
+        }
+    };
+    if (mma_warp) {
+        gemm(As + (size_t)w * nkt * 32 + lane, nkt, kt0);
+        fold();
     }
     // 2. recombine the planes into complex rows (+ identity self term)
     auto store_acc = [&]() {
@@ -294,24 +336,20 @@ __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site
         for (int q = threadIdx.x; q < NRP * Kd; q += blockDim.x) {
             int kk = q % Kd, r = q / Kd;
             cplx<float> v = kk < nc ? Vs[kk * NRP + r] : czero<float>();
-            XT[(size_t)r * LDX + kk] = __float2half_rn(v.re);
-            XT[(size_t)(NRP + r) * LDX + kk] = __float2half_rn(v.im);
+            const __half hr = __float2half_rn(v.re), hi = __float2half_rn(v.im);
+            XT[(size_t)r * LDX + kk] = hr;
+            XT[(size_t)(NRP + r) * LDX + kk] = hi;
+            if constexpr (SPLIT) {
+                XL[(size_t)r * LDX + kk] = __float2half_rn((v.re - __half2float(hr)) * kLoScale);
+                XL[(size_t)(NRP + r) * LDX + kk] = __float2half_rn((v.im - __half2float(hi)) * kLoScale);
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
         if (mma_warp) {
-            const uint4* Db = Ds + (size_t)w * op.Kt_d * 32 + lane;
-            for (int kt = 0; kt < op.Kt_d; ++kt) {
-                const uint4 a = Db[(size_t)kt * 32];
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    const __half* xc = XT + (size_t)(n * 8 + g) * LDX + kt * 16 + 2 * t;
-                    unsigned b0 = *reinterpret_cast<const unsigned*>(xc);
-                    unsigned b1 = *reinterpret_cast<const unsigned*>(xc + 8);
-                    mma16816(acc[n], a, b0, b1);
-                }
-            }
+            gemm(Ds + (size_t)w * op.Kt_d * 32 + lane, op.Kt_d, 0);
+            fold();
         }
         store_acc();
         __syncthreads();
@@ -333,7 +371,7 @@ __global__ void __launch_bounds__(512, 2) coarse_tc_kernel(CoarseTC op, int site
 static size_t tc_smem(const CoarseTC& op, int nrp, int self_mode, float hop_sign, int apply_inv) {
     const int Kp = op.Kt_all * 16;
     const int nkt = (self_mode == 1 ? op.Kt_all : op.Kt_hops) - (hop_sign != 0.f ? 0 : op.Kt_hops);
-    return 64 + (size_t)op.Mt * (nkt + (apply_inv ? op.Kt_d : 0)) * 512 + (size_t)2 * nrp * (Kp + 8) * sizeof(__half) +
+    return 64 + (size_t)op.Mt * (nkt + (apply_inv ? op.Kt_d : 0)) * 512 + (size_t)(op.split ? 2 : 1) * 2 * nrp * (Kp + 8) * sizeof(__half) +
            (size_t)2 * op.nc * 2 * nrp * sizeof(float) + (size_t)op.nc * nrp * sizeof(cplx<float>);
 }
 constexpr size_t kTcSmemMax = 227 * 1024;
@@ -344,11 +382,20 @@ static int launch_tc_nrp(const CoarseTC& op, int site_begin, int nsites, CVecT<f
     const size_t smem = tc_smem(op, NRP, self_mode, hop_sign, apply_inv);
     // set once per kernel instance (a function-local static initialiser is thread safe)
     static const bool attr = [] {
-        cudaFuncSetAttribute(coarse_tc_kernel<NRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+        cudaFuncSetAttribute(coarse_tc_kernel<NRP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+        if constexpr (NRP <= 12) cudaFuncSetAttribute(coarse_tc_kernel<NRP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
         return true;
     }();
     (void)attr;
-    coarse_tc_kernel<NRP><<<nsites, 64 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
+    if constexpr (NRP <= 12) {  // split staging: at most 12 right-hand sides per launch (no register spills)
+        if (op.split) {
+            coarse_tc_kernel<NRP, true><<<nsites, 64 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out,
+                                                                          nrhs);
+            DD_CHECK_LAUNCH();
+            return 0;
+        }
+    }
+    coarse_tc_kernel<NRP, false><<<nsites, 64 * op.Mt, smem, st>>>(op, site_begin, xin, xself, self_mode, hop_sign, apply_inv, out, nrhs);
     DD_CHECK_LAUNCH();
     return 0;
 }
@@ -357,7 +404,7 @@ static int launch_tc(const CoarseTC& op, int site_begin, int nsites, CVecT<float
                      float hop_sign, int apply_inv, CVecT<float> out, int nrhs, cudaStream_t st) {
     // right-hand sides per launch: up to 24, fewer where the site's matrix and the staged vectors
     // would not fit in shared memory
-    int cap = 24;
+    int cap = op.split ? 12 : 24;
     while (cap > 4 && tc_smem(op, cap, self_mode, hop_sign, apply_inv) > kTcSmemMax) cap = cap > 16 ? 16 : cap > 12 ? 12 : cap - 4;
     if (tc_smem(op, 4, self_mode, hop_sign, apply_inv) > kTcSmemMax) {
         set_error("coarse stencil: the per-site FP16 matrix does not fit in shared memory (2N too large for half precision)");

@@ -96,7 +96,8 @@ struct CoarseTC {
     const uint4* Dh;
     const int* cnbr;
     int NB, nc, Mt, Kt_all, Kt_hops, Kt_d;
-    int* err;  // set to 1 by a kernel whose bulk copy did not complete (read by the solve)
+    int* err;       // set to 1 by a kernel whose bulk copy did not complete (read by the solve)
+    int split = 0;  // 1: right-hand sides enter as FP16 hi + lo pairs (about FP32 accuracy of the product)
 };
 int tc_dims(int nc, int* Mt, int* Kt_all, int* Kt_hops, int* Kt_d);
 int pack_coarse_tc(const double* B64, const double* Dinv64, uint4* Bh, uint4* Dh, int NB, int nc, cudaStream_t st);

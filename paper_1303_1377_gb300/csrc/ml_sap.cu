@@ -8,10 +8,11 @@
 // ml_sap (ml_ops.cuh), which is kept for other shapes and for the host check; this kernel replaces
 // its 27 launches per colour and their round trips of every MR vector through global memory.
 //
-// Thread (slot s, row a) owns component a of the block's s-th even site and of its s-th odd site,
-// for all right-hand sides of the CTA.  A block of D_1 is read by its nc row threads as one
-// coalesced column per step; the vector it multiplies is read from shared memory, one broadcast
-// per column and right-hand-side pair.
+// Thread (group h, slot s, row a) owns component a of the block's s-th even site and of its s-th odd
+// site, for the right-hand sides 6h..6h+5 of the CTA (two groups: twice the warps of one thread per
+// row, and half the accumulators per thread).  A block of D_1 is read by its nc row threads as one
+// coalesced column per step (the second group finds it in L1); the vector it multiplies is read
+// from shared memory, one broadcast per column and right-hand-side pair.
 #include "kernels.h"
 #include "ml_ops.cuh"
 
@@ -20,6 +21,8 @@ namespace ddamg {
 namespace {
 
 constexpr int kR = 12;  // right-hand sides per CTA
+constexpr int kT = 6;   // right-hand sides per thread (kR / kT thread groups)
+constexpr int kG = kR / kT;
 
 // shared-memory vector of one half block: [slot][component][kR]
 struct HalfVec {
@@ -28,18 +31,18 @@ struct HalfVec {
     __device__ __forceinline__ cplx<float>* at(int s, int a) const { return p + ((size_t)s * nc + a) * kR; }
 };
 
-// acc[r] += sum_col B[col][row] v[col][r] for the column-major nc x nc block B (global) and the
-// shared-memory vector v ([nc][kR]), r < kR
-__device__ __forceinline__ void row_times(cplx<float> (&acc)[kR], const cplx<float>* __restrict__ B, int nc, int row,
-                                          const cplx<float>* v, float sign = 1.f) {
+// acc[j] += sum_col B[col][row] v[col][q0 + j] for the column-major nc x nc block B (global) and the
+// shared-memory vector v ([nc][kR]), j < kT
+__device__ __forceinline__ void row_times(cplx<float> (&acc)[kT], const cplx<float>* __restrict__ B, int nc, int row,
+                                          const cplx<float>* v, int q0, float sign = 1.f) {
     const cplx<float>* bp = B + row;
 #pragma unroll 4
     for (int col = 0; col < nc; ++col) {
         const cplx<float> bv0 = ldg_c(bp + (size_t)col * nc);
         const cplx<float> bv = mk(sign * bv0.re, sign * bv0.im);
-        const float4* v4 = reinterpret_cast<const float4*>(v + (size_t)col * kR);
+        const float4* v4 = reinterpret_cast<const float4*>(v + (size_t)col * kR + q0);
 #pragma unroll
-        for (int q = 0; q < kR / 2; ++q) {
+        for (int q = 0; q < kT / 2; ++q) {
             const float4 x = v4[q];
             cmac(acc[2 * q], bv, mk(x.x, x.y));
             cmac(acc[2 * q + 1], bv, mk(x.z, x.w));
@@ -47,14 +50,14 @@ __device__ __forceinline__ void row_times(cplx<float> (&acc)[kR], const cplx<flo
     }
 }
 
-__device__ __forceinline__ void zero(cplx<float> (&acc)[kR]) {
+__device__ __forceinline__ void zero(cplx<float> (&acc)[kT]) {
 #pragma unroll
-    for (int r = 0; r < kR; ++r) acc[r] = czero<float>();
+    for (int r = 0; r < kT; ++r) acc[r] = czero<float>();
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, const cplx<float>* __restrict__ b,
+__global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, const cplx<float>* __restrict__ b,
                                                               cplx<float>* __restrict__ z, int nrhs, int colour, int mr_steps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = v.nc, He = v.Vb1e, Vb = v.Vb1;
@@ -63,8 +66,10 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
     const int r0 = blockIdx.y * kR;
     const int nr = min(kR, nrhs - r0);
     const int t = threadIdx.x;
-    const bool act = t < He * nc;
-    const int s = act ? t / nc : 0, row = act ? t % nc : 0;
+    const bool act = t < kG * He * nc;
+    const int hg = act ? t / (He * nc) : 0, tt = act ? t % (He * nc) : 0;
+    const int s = tt / nc, row = tt % nc;
+    const int q0 = hg * kT;  // this thread's first right-hand side within the CTA
 
     // shared memory: six half-block vectors, site tables, MR step sizes
     const size_t hv = (size_t)He * nc * kR;
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
     __syncthreads();
     const int ce = site[s], co = site[He + s];  // this thread's even and odd site
 
-    cplx<float> acc[kR];
+    cplx<float> acc[kT];
     // ---- residual r = b - D_1 z on the even (pass 0) and odd (pass 1) sites of the block; z of
     // out-of-block neighbours belongs to blocks of the other colour, which this launch leaves alone
     for (int pass = 0; pass < 2; ++pass) {
@@ -98,26 +103,26 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
                 Stg.at(ss, col)[r] = r < nr ? z[(size_t)(r0 + r) * fs + (size_t)n * nc + col] : czero<float>();
             }
             __syncthreads();
-            if (act) row_times(acc, ml_block(v, pass ? co : ce, d), nc, row, Stg.at(s, 0));
+            if (act) row_times(acc, ml_block(v, pass ? co : ce, d), nc, row, Stg.at(s, 0), q0);
             __syncthreads();
         }
         if (act) {
             const HalfVec& dst = pass ? So : Re;  // r_o parks in So until rho is formed
             const int c = pass ? co : ce;
-            cplx<float>* o = dst.at(s, row);
+            cplx<float>* o = dst.at(s, row) + q0;
 #pragma unroll
-            for (int r = 0; r < kR; ++r)
-                o[r] = r < nr ? b[(size_t)(r0 + r) * fs + (size_t)c * nc + row] - acc[r] : czero<float>();
+            for (int j = 0; j < kT; ++j)
+                o[j] = q0 + j < nr ? b[(size_t)(r0 + q0 + j) * fs + (size_t)c * nc + row] - acc[j] : czero<float>();
         }
     }
     __syncthreads();
     // ---- t_e = A_ee^{-1} r_e
     if (act) {
         zero(acc);
-        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, Re.at(s, 0));
-        cplx<float>* o = Te.at(s, row);
+        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, Re.at(s, 0), q0);
+        cplx<float>* o = Te.at(s, row) + q0;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) o[r] = acc[r];
+        for (int j = 0; j < kT; ++j) o[j] = acc[j];
     }
     __syncthreads();
     // ---- rho = r_o - A_oe t_e; x_o = 0
@@ -125,15 +130,15 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
         zero(acc);
         for (int d = 0; d < 8; ++d) {
             const int n = nbl[(He + s) * 8 + d];
-            if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), -1.f);
+            if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
         }
-        const cplx<float>* ro = So.at(s, row);
-        cplx<float>* o = Rho.at(s, row);
-        cplx<float>* xo = Xo.at(s, row);
+        const cplx<float>* ro = So.at(s, row) + q0;
+        cplx<float>* o = Rho.at(s, row) + q0;
+        cplx<float>* xo = Xo.at(s, row) + q0;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            o[r] = ro[r] + acc[r];
-            xo[r] = czero<float>();
+        for (int j = 0; j < kT; ++j) {
+            o[j] = ro[j] + acc[j];
+            xo[j] = czero<float>();
         }
     }
     __syncthreads();
@@ -143,31 +148,31 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
             zero(acc);
             for (int d = 0; d < 8; ++d) {
                 const int n = nbl[s * 8 + d];
-                if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Rho.at(n - He, 0));
+                if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Rho.at(n - He, 0), q0);
             }
-            cplx<float>* o = So.at(s, row);
+            cplx<float>* o = So.at(s, row) + q0;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) o[r] = acc[r];
+            for (int j = 0; j < kT; ++j) o[j] = acc[j];
         }
         __syncthreads();
         if (act) {  // t_e = A_ee^{-1} u_e
             zero(acc);
-            row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0));
-            cplx<float>* o = Te.at(s, row);
+            row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0), q0);
+            cplx<float>* o = Te.at(s, row) + q0;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) o[r] = acc[r];
+            for (int j = 0; j < kT; ++j) o[j] = acc[j];
         }
         __syncthreads();
         if (act) {  // s_o = A_oo rho - A_oe t_e
             zero(acc);
-            row_times(acc, ml_block(v, co, 0), nc, row, Rho.at(s, 0));
+            row_times(acc, ml_block(v, co, 0), nc, row, Rho.at(s, 0), q0);
             for (int d = 0; d < 8; ++d) {
                 const int n = nbl[(He + s) * 8 + d];
-                if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), -1.f);
+                if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
             }
-            cplx<float>* o = So.at(s, row);
+            cplx<float>* o = So.at(s, row) + q0;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) o[r] = acc[r];
+            for (int j = 0; j < kT; ++j) o[j] = acc[j];
         }
         __syncthreads();
         {  // alpha_r = <s, rho> / <s, s> over the block's odd sites: warp w sums right-hand side r = w, w + nwarps, ...
@@ -188,14 +193,14 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
         }
         __syncthreads();
         if (act) {  // x_o += alpha rho; rho -= alpha s
-            cplx<float>* xo = Xo.at(s, row);
-            cplx<float>* ro = Rho.at(s, row);
-            const cplx<float>* so = So.at(s, row);
+            cplx<float>* xo = Xo.at(s, row) + q0;
+            cplx<float>* ro = Rho.at(s, row) + q0;
+            const cplx<float>* so = So.at(s, row) + q0;
 #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const cplx<float> a = alpha[r];
-                cmac(xo[r], a, ro[r]);
-                ro[r] = ro[r] - a * so[r];
+            for (int j = 0; j < kT; ++j) {
+                const cplx<float> a = alpha[q0 + j];
+                cmac(xo[j], a, ro[j]);
+                ro[j] = ro[j] - a * so[j];
             }
         }
         __syncthreads();
@@ -205,25 +210,25 @@ __global__ void __launch_bounds__(384, 1) ml_sap_fused_kernel(MLView<float> v, c
         zero(acc);
         for (int d = 0; d < 8; ++d) {
             const int n = nbl[s * 8 + d];
-            if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Xo.at(n - He, 0), -1.f);
+            if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Xo.at(n - He, 0), q0, -1.f);
         }
-        const cplx<float>* re = Re.at(s, row);
-        cplx<float>* o = So.at(s, row);
+        const cplx<float>* re = Re.at(s, row) + q0;
+        cplx<float>* o = So.at(s, row) + q0;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) o[r] = re[r] + acc[r];
+        for (int j = 0; j < kT; ++j) o[j] = re[j] + acc[j];
     }
     __syncthreads();
     if (act) {
         zero(acc);
-        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0));
-        const cplx<float>* xo = Xo.at(s, row);
+        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0), q0);
+        const cplx<float>* xo = Xo.at(s, row) + q0;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            if (r < nr) {
-                cplx<float>* ze = z + (size_t)(r0 + r) * fs + (size_t)ce * nc + row;
-                cplx<float>* zo = z + (size_t)(r0 + r) * fs + (size_t)co * nc + row;
-                *ze = *ze + acc[r];
-                *zo = *zo + xo[r];
+        for (int j = 0; j < kT; ++j) {
+            if (q0 + j < nr) {
+                cplx<float>* ze = z + (size_t)(r0 + q0 + j) * fs + (size_t)ce * nc + row;
+                cplx<float>* zo = z + (size_t)(r0 + q0 + j) * fs + (size_t)co * nc + row;
+                *ze = *ze + acc[j];
+                *zo = *zo + xo[j];
             }
         }
     }
@@ -234,7 +239,7 @@ static size_t ml_sap_fused_smem(const MLView<float>& v) {
 }
 
 bool ml_sap_fused_supported(const MLView<float>& v) {
-    return v.Vb1 == 2 * v.Vb1e && v.Vb1e * v.nc <= 384 && v.nc % 2 == 0 && ml_sap_fused_smem(v) <= 227 * 1024;
+    return v.Vb1 == 2 * v.Vb1e && kG * v.Vb1e * v.nc <= 768 && v.nc % 2 == 0 && ml_sap_fused_smem(v) <= 227 * 1024;
 }
 
 int launch_ml_sap_fused(const MLView<float>& v, const cplx<float>* b, cplx<float>* z, int nrhs, int colour, int mr_steps,
@@ -245,7 +250,7 @@ int launch_ml_sap_fused(const MLView<float>& v, const cplx<float>* b, cplx<float
         return true;
     }();
     (void)attr;
-    const int threads = ((v.Vb1e * v.nc + 31) / 32) * 32;
+    const int threads = ((kG * v.Vb1e * v.nc + 31) / 32) * 32;
     const dim3 grid((unsigned)(v.NB2 / 2), (unsigned)((nrhs + kR - 1) / kR));
     ml_sap_fused_kernel<<<grid, threads, smem, st>>>(v, b, z, nrhs, colour, mr_steps);
     DD_CHECK_LAUNCH();

@@ -429,6 +429,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=20.0)
     ap.add_argument("--no-small", action="store_true", help="skip the 8^4 and 16^4 configurations")
     ap.add_argument("--no-two-level", action="store_true", help="skip the two-level solve on the three-level handle")
+    ap.add_argument("--no-conforming", action="store_true",
+                    help="skip the half-precision variant whose smoother reads FP32 links and site terms")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi samples of the timed region in this file")
     ap.add_argument("--levels", type=int, default=None, choices=[2, 3],  # with --profile-case: 3 adds the level-1 kernels
                     help="2 or 3 (the recursion to a third level: level-1 blocks 2^4, N_1 = 20, adaptive level-1 setup); "
@@ -574,6 +576,8 @@ def main():
     # Dslash bandwidth at the workload's size and right-hand sides (half of the headline metric):
     # kernel time from CUDA events around each Dslash launch, algorithmic bytes per launch
     dslash_rates = measure_dslash(solver, b[:chk], peaks()[0])
+    # and for one right-hand side (links and site terms not shared across fields: the HBM-bound case)
+    dslash_1rhs = measure_dslash(solver, b[:1], peaks()[0]) if chk > 1 else None
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region: b goes
     # in, z comes out; the zero-guess entry point never reads z (the paper's zero initial guess)
     e2e = None
@@ -665,6 +669,7 @@ def main():
         "gauge_generation_seconds": t_gauge,
         "kernel_profile_first_step": prof_all,
         "dslash": dslash_rates,
+        "dslash_1rhs": dslash_1rhs,
         **({"two_level_same_handle": two_level} if two_level else {}),
     }
     if args.levels == 3:
@@ -696,6 +701,47 @@ def main():
                                          "rel_residual": st1[0]["rel_residual"], "status": rc1, "setup_seconds": t_plain_setup,
                                          "speedup_of_value": value / (1.0 / tp)}
         plain.close()
+    # the half-precision variant whose smoother keeps FP32 links and site terms (FP16 only on P, D_c
+    # and D_ee^-1): its own handle and setup, one warm-up and two timed steps of the same batch
+    if (args.precision == "half" and args.workload.startswith("32x32x32x64") and not args.no_conforming and world == 1):
+        Uc = synth.gauge_field(dims, w["eps"], w["seed"])
+        pc = ddamg.default_params(n_vec=w["N"], nu=w["nu"], precision=ddamg.PREC_HALF,
+                                  outer=ddamg.OUTER_REFINE if args.outer == "refine" else ddamg.OUTER_DW, cycle_tol=args.cycle_tol,
+                                  smoother_fp16=0, n_kv=w.get("n_kv", 25), lean=w.get("lean", 0), setup_group=w.get("setup_group", 0))
+        sc = ddamg.Solver(dims, Uc, m0, C_SW, pc, setup=True)
+        del Uc
+        if args.levels == 3:
+            mlc = ddamg.ml_default_params(inner=1 if args.ml_inner == "vcycle" else 0)
+            sc.ml_setup(synth.gaussian_coarse(sc.n_coarse, sc.coarse_dof, mlc.n_vec1, seed=w["seed"] + 11), mlc)
+        sc.set_stream(stream.cuda_stream)
+        fn_c = sc.ml_solve_zero_guess if args.levels == 3 else sc.solve_zero_guess
+        bc = torch.from_numpy(bh).to("cuda")
+        zc = torch.zeros_like(bc)
+
+        def step_c():
+            st = []
+            for g0 in range(0, nr, group):
+                _, sg, rc = fn_c(bc[g0:g0 + group], zc[g0:g0 + group])
+                if rc != 0:
+                    raise RuntimeError(f"solve status {rc}")
+                st += sg
+            return st
+
+        step_c()
+        torch.cuda.synchronize()
+        c0e, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0e.record(stream)
+        stc = [step_c() for _ in range(2)]
+        c1e.record(stream)
+        torch.cuda.synchronize()
+        msc = c0e.elapsed_time(c1e) / 2
+        line["fp32_smoother_variant"] = {"value": nr / (msc / 1e3), "unit": "solves/s", "ms_per_step": msc, "steps": 2, "warmup": 1,
+                                         "fgmres_iterations": max(q["iterations"] for q in stc[-1]),
+                                         "max_rel_residual": max(q["rel_residual"] for q in stc[-1]),
+                                         "precision": "FP16 P, D_c and D_ee^-1; FP32 smoother links and site terms; FP32 V-cycle arithmetic"}
+        sc.close()
+        del bc, zc
+        torch.cuda.empty_cache()
     # the smaller configurations, each set up and solved on its own: the oracle's 8^4 lattice (FP64
     # throughout, nu = 3) and the 16^4 lattice (FP32 V-cycle, one Gaussian right-hand side)
     if not args.no_small and world == 1 and args.workload.startswith("32x32x32x64"):

@@ -36,6 +36,10 @@ struct MLView {
     const cplx<T>* B1;
     const cplx<T>* Dinv1;
     const cplx<T>* P1;
+    // half-precision handles: FP16 copies of B1 and Dinv1 (one __half2 (re, im) per entry, same
+    // order), read by the fused SAP colour step only; null otherwise
+    const void* B1h = nullptr;
+    const void* Dinv1h = nullptr;
 };
 
 template <typename T>

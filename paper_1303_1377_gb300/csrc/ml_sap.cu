@@ -31,14 +31,30 @@ struct HalfVec {
     __device__ __forceinline__ cplx<float>* at(int s, int a) const { return p + ((size_t)s * nc + a) * kR; }
 };
 
-// acc[j] += sum_col B[col][row] v[col][q0 + j] for the column-major nc x nc block B (global) and the
-// shared-memory vector v ([nc][kR]), j < kT
-__device__ __forceinline__ void row_times(cplx<float> (&acc)[kT], const cplx<float>* __restrict__ B, int nc, int row,
+// the operator's entries: FP32 complex, or FP16 (re, im) pairs on half-precision handles
+template <bool H16>
+struct OpRef {
+    const void* B;
+    const void* Dinv;
+    __device__ __forceinline__ cplx<float> at(const void* base, size_t q) const {
+        if constexpr (H16) {
+            const float2 f = __half22float2(__ldg(reinterpret_cast<const __half2*>(base) + q));
+            return mk(f.x, f.y);
+        } else {
+            return ldg_c(reinterpret_cast<const cplx<float>*>(base) + q);
+        }
+    }
+};
+
+// acc[j] += sum_col B[col][row] v[col][q0 + j] for the column-major nc x nc block at entry `first` of
+// `base` (global) and the shared-memory vector v ([nc][kR]), j < kT
+template <bool H16>
+__device__ __forceinline__ void row_times(cplx<float> (&acc)[kT], const OpRef<H16>& op, const void* base, size_t first, int nc, int row,
                                           const cplx<float>* v, int q0, float sign = 1.f) {
-    const cplx<float>* bp = B + row;
+    const size_t bp = first + row;
 #pragma unroll 4
     for (int col = 0; col < nc; ++col) {
-        const cplx<float> bv0 = ldg_c(bp + (size_t)col * nc);
+        const cplx<float> bv0 = op.at(base, bp + (size_t)col * nc);
         const cplx<float> bv = mk(sign * bv0.re, sign * bv0.im);
         const float4* v4 = reinterpret_cast<const float4*>(v + (size_t)col * kR + q0);
 #pragma unroll
@@ -57,6 +73,7 @@ __device__ __forceinline__ void zero(cplx<float> (&acc)[kT]) {
 
 }  // namespace
 
+template <bool H16>
 __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, const cplx<float>* __restrict__ b,
                                                               cplx<float>* __restrict__ z, int nrhs, int colour, int mr_steps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -70,6 +87,9 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
     const int hg = act ? t / (He * nc) : 0, tt = act ? t % (He * nc) : 0;
     const int s = tt / nc, row = tt % nc;
     const int q0 = hg * kT;  // this thread's first right-hand side within the CTA
+    const OpRef<H16> op{H16 ? v.B1h : (const void*)v.B1, H16 ? v.Dinv1h : (const void*)v.Dinv1};
+    const size_t nn = (size_t)nc * nc;
+    auto blk = [&](int c, int d) { return ((size_t)c * 9 + d) * nn; };  // first entry of block d of site c
 
     // shared memory: six half-block vectors, site tables, MR step sizes
     const size_t hv = (size_t)He * nc * kR;
@@ -103,7 +123,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
                 Stg.at(ss, col)[r] = r < nr ? z[(size_t)(r0 + r) * fs + (size_t)n * nc + col] : czero<float>();
             }
             __syncthreads();
-            if (act) row_times(acc, ml_block(v, pass ? co : ce, d), nc, row, Stg.at(s, 0), q0);
+            if (act) row_times(acc, op, op.B, blk(pass ? co : ce, d), nc, row, Stg.at(s, 0), q0);
             __syncthreads();
         }
         if (act) {
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
     // ---- t_e = A_ee^{-1} r_e
     if (act) {
         zero(acc);
-        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, Re.at(s, 0), q0);
+        row_times(acc, op, op.Dinv, (size_t)ce * nn, nc, row, Re.at(s, 0), q0);
         cplx<float>* o = Te.at(s, row) + q0;
 #pragma unroll
         for (int j = 0; j < kT; ++j) o[j] = acc[j];
@@ -130,7 +150,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
         zero(acc);
         for (int d = 0; d < 8; ++d) {
             const int n = nbl[(He + s) * 8 + d];
-            if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
+            if (n >= 0) row_times(acc, op, op.B, blk(co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
         }
         const cplx<float>* ro = So.at(s, row) + q0;
         cplx<float>* o = Rho.at(s, row) + q0;
@@ -148,7 +168,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
             zero(acc);
             for (int d = 0; d < 8; ++d) {
                 const int n = nbl[s * 8 + d];
-                if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Rho.at(n - He, 0), q0);
+                if (n >= 0) row_times(acc, op, op.B, blk(ce, 1 + d), nc, row, Rho.at(n - He, 0), q0);
             }
             cplx<float>* o = So.at(s, row) + q0;
 #pragma unroll
@@ -157,7 +177,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
         __syncthreads();
         if (act) {  // t_e = A_ee^{-1} u_e
             zero(acc);
-            row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0), q0);
+            row_times(acc, op, op.Dinv, (size_t)ce * nn, nc, row, So.at(s, 0), q0);
             cplx<float>* o = Te.at(s, row) + q0;
 #pragma unroll
             for (int j = 0; j < kT; ++j) o[j] = acc[j];
@@ -165,10 +185,10 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
         __syncthreads();
         if (act) {  // s_o = A_oo rho - A_oe t_e
             zero(acc);
-            row_times(acc, ml_block(v, co, 0), nc, row, Rho.at(s, 0), q0);
+            row_times(acc, op, op.B, blk(co, 0), nc, row, Rho.at(s, 0), q0);
             for (int d = 0; d < 8; ++d) {
                 const int n = nbl[(He + s) * 8 + d];
-                if (n >= 0) row_times(acc, ml_block(v, co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
+                if (n >= 0) row_times(acc, op, op.B, blk(co, 1 + d), nc, row, Te.at(n, 0), q0, -1.f);
             }
             cplx<float>* o = So.at(s, row) + q0;
 #pragma unroll
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
         zero(acc);
         for (int d = 0; d < 8; ++d) {
             const int n = nbl[s * 8 + d];
-            if (n >= 0) row_times(acc, ml_block(v, ce, 1 + d), nc, row, Xo.at(n - He, 0), q0, -1.f);
+            if (n >= 0) row_times(acc, op, op.B, blk(ce, 1 + d), nc, row, Xo.at(n - He, 0), q0, -1.f);
         }
         const cplx<float>* re = Re.at(s, row) + q0;
         cplx<float>* o = So.at(s, row) + q0;
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, c
     __syncthreads();
     if (act) {
         zero(acc);
-        row_times(acc, v.Dinv1 + (size_t)ce * nc * nc, nc, row, So.at(s, 0), q0);
+        row_times(acc, op, op.Dinv, (size_t)ce * nn, nc, row, So.at(s, 0), q0);
         const cplx<float>* xo = Xo.at(s, row) + q0;
 #pragma unroll
         for (int j = 0; j < kT; ++j) {
@@ -246,13 +266,17 @@ int launch_ml_sap_fused(const MLView<float>& v, const cplx<float>* b, cplx<float
                         cudaStream_t st) {
     const size_t smem = ml_sap_fused_smem(v);
     static const bool attr = [] {
-        cudaFuncSetAttribute(ml_sap_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(ml_sap_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(ml_sap_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         return true;
     }();
     (void)attr;
     const int threads = ((kG * v.Vb1e * v.nc + 31) / 32) * 32;
     const dim3 grid((unsigned)(v.NB2 / 2), (unsigned)((nrhs + kR - 1) / kR));
-    ml_sap_fused_kernel<<<grid, threads, smem, st>>>(v, b, z, nrhs, colour, mr_steps);
+    if (v.B1h && v.Dinv1h)
+        ml_sap_fused_kernel<true><<<grid, threads, smem, st>>>(v, b, z, nrhs, colour, mr_steps);
+    else
+        ml_sap_fused_kernel<false><<<grid, threads, smem, st>>>(v, b, z, nrhs, colour, mr_steps);
     DD_CHECK_LAUNCH();
     return 0;
 }

@@ -145,7 +145,9 @@ def test_level1_setup(case, update):
 @pytest.mark.parametrize("prec", ["SINGLE", "HALF"])
 def test_three_level_solve_mixed_precision(case, prec):
     """SINGLE and HALF handles: level-1 and level-2 solves in FP32 inside the handle's outer scheme;
-    the true FP64 residual still reaches 1e-10 and the recursion runs."""
+    the true FP64 residual still reaches 1e-10 and the recursion runs.  The level-1 SAP reads D_1 in
+    FP32 on SINGLE handles (stated 1e-6) and in FP16 on HALF handles (stated 2e-3 relative to the
+    field maximum, the bound of the fine smoother with its FP16 operator)."""
     ddamg, D = case["ddamg"], case["D"]
     U = synth.gauge_field(DIMS, 0.5, seed=111)
     p = ddamg.default_params(n_vec=N0, block=BLK, precision=getattr(ddamg, "PREC_" + prec), nu=2)
@@ -155,7 +157,7 @@ def test_three_level_solve_mixed_precision(case, prec):
         s.ml_build(synth.gaussian_coarse(4 ** 4, 2 * N0, N1, seed=113), ddamg.ml_default_params(block1=BLK1, n_vec1=N1, nu1=2))
         x = synth.gaussian_coarse(4 ** 4, 2 * N0, 2, seed=123)
         ref = case["oracle"]().levels[1].sap
-        assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < 1e-6
+        assert rel(s.ml_apply_sap1(x, 2), np.stack([ref.apply(x[r], 2) for r in range(2)])) < {"SINGLE": 1e-6, "HALF": 2e-3}[prec]
         z, st, rc = s.ml_solve(b)
         counts = s.ml_counts()
     assert rc == 0

@@ -3,6 +3,7 @@
 // GMRES for the odd-even coarse system (Sec. 6) and the outer FGMRES (Sec. 5),
 // and every extern "C" entry point declared in include/ddamg.h.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -116,6 +117,21 @@ struct KrylovBufs {
     int* h_steps = nullptr;
     double* h_resid = nullptr;
     int* h_flags = nullptr;
+    // Arnoldi steps captured as CUDA graphs (problems that allow it, KrylovProblem::graph), one per
+    // step index k.  The signature lists every pointer and size the captured launches baked in; a step
+    // runs eagerly the first time a signature is seen, is captured the second time and replayed after.
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::array<uintptr_t, 12> sig{};
+        bool seen = false;
+    };
+    std::vector<StepGraph> graphs;
+    bool graphs_off = false;  // a capture failed: steps of this solver run eagerly from then on
+    void drop_graphs() {
+        for (auto& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
     int alloc(int nr, int mm) {
         if (nr <= nrhs && mm == m) return 0;
         release();
@@ -162,6 +178,7 @@ struct KrylovBufs {
         return 0;
     }
     void release() {
+        drop_graphs();
         dfree(s.H);
         dfree(s.cs);
         dfree(s.sn);
@@ -668,6 +685,10 @@ struct KrylovProblem {
     bool lag_check = false;  // decide "all converged" from the flags of the previous step, without waiting for
                              // the current one (the GPU keeps a step queued; a step after convergence changes
                              // nothing, since inactive right-hand sides are frozen on the device)
+    bool graph = false;         // the Arnoldi step (A and the FP32 one-pass Gram-Schmidt) may be captured and replayed:
+                                // A has no host synchronisation, and graph_sig names the buffers it bakes in
+    std::array<const void*, 4> graph_sig{};
+    unsigned graph_prof_mask = 0;  // profile families that A records (no capture while one of them is timed)
     bool has_deadline = false;  // wall-clock limit: checked at every host synchronisation of the iteration;
     std::chrono::steady_clock::time_point deadline{};  // once passed, x takes the current cycle's update and the solve returns
     cplx<TV>* Vb;          // basis [(m+1)][nrhs][n]
@@ -865,52 +886,100 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
             bool lean_step = false;
             if constexpr (std::is_same<TV, dwf>::value || std::is_same<TV, float>::value)
                 lean_step = std::is_same<TV, dwf>::value || P.lean;
-            if (lean_step) {
-                // w is formed in the V_{k+1} slot; one multi-dot gives <V_i, w> (i <= k) and ||w||^2,
-                // the axpy kernel returns ||w'||^2, and the second classical Gram-Schmidt pass runs
-                // only when the first one cancelled more than 1 - eta of w (eta = 1e-3, decided on the
-                // device).  With the 48-bit double-word basis one pass leaves a non-orthogonality of
-                // about 1e-14 ||w|| / ||w'||, far below what a 1e-10 solve needs; the FP64 true residual
-                // at every restart certifies convergence whatever the basis quality.
-                // (FP32 basis: the same scheme; one pass leaves about 1e-7 ||w|| / ||w'|| of
-                // non-orthogonality, ample for a cycle that reduces the residual by cycle_tol)
-                cplx<TV>* wk = P.Vb + (size_t)(k + 1) * bstride;
-                DD_TRY(P.A(zk, wk));
-                const double vb = (double)sizeof(cplx<TV>) * n * nr;
-                Prof pr(h, PF_ORTHO, vb * (2 * (k + 1) + 6));
-                // the last product is ||w||^2 before orthogonalisation, kept for the DGKS test
-                DD_TRY(lean_multidot(P.Vb, bstride, n, k + 2, wk, nr, kb.hcol, kb, nullptr, st, kb.nbefore));
-                DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, kb, kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
-                if (P.reorth) {
-                    DD_TRY(dgks(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, s.active, nr, 1e-3, kb.dflag, st));
-                    DD_TRY(lean_multidot(P.Vb, bstride, n, k + 1, wk, nr, kb.hcol2, kb, kb.dflag, st));
-                    DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol2, nr, kb, kb.hcol + (size_t)(k + 1) * nr, kb.dflag, st));
-                    DD_TRY(add_columns_flag(kb.hcol, kb.hcol2, (k + 1) * nr, kb.dflag, st));
-                }
-                DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
-                if constexpr (std::is_same<TV, float>::value) {
-                    if (scale_f32(wk, kb.scale, n, nr, st)) {
-                        set_error("FP32 basis: odd length or misaligned vector");
-                        return DDAMG_ERR_INVALID_ARG;
+            // a captured step: FP32 one-pass Gram-Schmidt without the DGKS pass, no preconditioner, the
+            // Gram-Schmidt family not being timed (event records cannot time a graph's insides)
+            auto step_body = [&]() -> int {
+                if (lean_step) {
+                    // w is formed in the V_{k+1} slot; one multi-dot gives <V_i, w> (i <= k) and ||w||^2,
+                    // the axpy kernel returns ||w'||^2, and the second classical Gram-Schmidt pass runs
+                    // only when the first one cancelled more than 1 - eta of w (eta = 1e-3, decided on the
+                    // device).  With the 48-bit double-word basis one pass leaves a non-orthogonality of
+                    // about 1e-14 ||w|| / ||w'||, far below what a 1e-10 solve needs; the FP64 true residual
+                    // at every restart certifies convergence whatever the basis quality.
+                    // (FP32 basis: the same scheme; one pass leaves about 1e-7 ||w|| / ||w'|| of
+                    // non-orthogonality, ample for a cycle that reduces the residual by cycle_tol)
+                    cplx<TV>* wk = P.Vb + (size_t)(k + 1) * bstride;
+                    DD_TRY(P.A(zk, wk));
+                    const double vb = (double)sizeof(cplx<TV>) * n * nr;
+                    Prof pr(h, PF_ORTHO, vb * (2 * (k + 1) + 6));
+                    // the last product is ||w||^2 before orthogonalisation, kept for the DGKS test
+                    DD_TRY(lean_multidot(P.Vb, bstride, n, k + 2, wk, nr, kb.hcol, kb, nullptr, st, kb.nbefore));
+                    DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol, nr, kb, kb.hcol + (size_t)(k + 1) * nr, nullptr, st));
+                    if (P.reorth) {
+                        DD_TRY(dgks(kb.nbefore, kb.hcol + (size_t)(k + 1) * nr, s.active, nr, 1e-3, kb.dflag, st));
+                        DD_TRY(lean_multidot(P.Vb, bstride, n, k + 1, wk, nr, kb.hcol2, kb, kb.dflag, st));
+                        DD_TRY(lean_axpy_norm(wk, P.Vb, bstride, n, k + 1, kb.hcol2, nr, kb, kb.hcol + (size_t)(k + 1) * nr, kb.dflag, st));
+                        DD_TRY(add_columns_flag(kb.hcol, kb.hcol2, (k + 1) * nr, kb.dflag, st));
+                    }
+                    DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
+                    if constexpr (std::is_same<TV, float>::value) {
+                        if (scale_f32(wk, kb.scale, n, nr, st)) {
+                            set_error("FP32 basis: odd length or misaligned vector");
+                            return DDAMG_ERR_INVALID_ARG;
+                        }
+                    } else {
+                        DD_TRY(baxpy<TV>(kb, wk, false, wk, 0, 1, kb.scale, n, nr, 1.0, st));
                     }
                 } else {
-                    DD_TRY(baxpy<TV>(kb, wk, false, wk, 0, 1, kb.scale, n, nr, 1.0, st));
+                    DD_TRY(P.A(zk, P.w));
+                    // classical Gram-Schmidt (twice when reorth)
+                    const double vb = (double)sizeof(cplx<TV>) * n * nr;
+                    Prof pr(h, PF_ORTHO, vb * ((k + 1) * (P.reorth ? 4 : 2) + 4));
+                    DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol, st));
+                    DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol, n, nr, -1.0, st));
+                    if (P.reorth) {
+                        DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol2, st));
+                        DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol2, n, nr, -1.0, st));
+                        DD_TRY(add_columns(kb.hcol, kb.hcol2, (k + 1) * nr, st));
+                    }
+                    DD_TRY(bdot<TV>(kb, P.w, 0, 1, P.w, n, nr, kb.hcol + (size_t)(k + 1) * nr, st));
+                    DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
+                    DD_TRY(baxpy<TV>(kb, P.Vb + (size_t)(k + 1) * bstride, false, P.w, 0, 1, kb.scale, n, nr, 1.0, st));
+                }
+                return 0;
+            };
+            bool graph_step = false;
+            if constexpr (std::is_same<TV, float>::value)  // (the legacy default streams cannot be captured)
+                graph_step = lean_step && P.graph && !kb.graphs_off && !P.M && !P.reorth &&
+                             !(h->prof_mask & ((1u << PF_ORTHO) | P.graph_prof_mask)) &&
+                             st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+            if (graph_step) {
+                if ((int)kb.graphs.size() < P.m) kb.graphs.resize(P.m);
+                KrylovBufs::StepGraph& sg = kb.graphs[k];
+                const std::array<uintptr_t, 12> sig = {(uintptr_t)P.Vb, (uintptr_t)n, (uintptr_t)nr, (uintptr_t)kb.s.H,
+                                                       (uintptr_t)kb.hcol, (uintptr_t)kb.dscr, (uintptr_t)kb.tickets,
+                                                       (uintptr_t)P.graph_sig[0], (uintptr_t)P.graph_sig[1], (uintptr_t)P.graph_sig[2],
+                                                       (uintptr_t)P.graph_sig[3], (uintptr_t)(P.cycle_tol * 1e15)};
+                if (sg.exec && sg.sig == sig) {
+                    DD_CUDA(cudaGraphLaunch(sg.exec, st));
+                } else if (sg.seen && sg.sig == sig) {  // second time: capture, then replay
+                    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+                    sg.exec = nullptr;
+                    DD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    const int rc = step_body();  // recorded, not run
+                    cudaGraph_t g = nullptr;
+                    cudaError_t e = cudaStreamEndCapture(st, &g);
+                    if (rc == 0 && e == cudaSuccess) {
+                        e = cudaGraphInstantiate(&sg.exec, g, 0);
+                        if (e != cudaSuccess) sg.exec = nullptr;
+                    }
+                    if (g) cudaGraphDestroy(g);
+                    if (sg.exec) {
+                        DD_CUDA(cudaGraphLaunch(sg.exec, st));
+                    } else {  // not capturable after all: run the step eagerly, and do not try this problem again
+                        (void)cudaGetLastError();
+                        kb.graphs_off = true;
+                        DD_TRY(step_body());
+                    }
+                } else {  // first time with this signature: run eagerly
+                    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+                    sg.exec = nullptr;
+                    sg.sig = sig;
+                    sg.seen = true;
+                    DD_TRY(step_body());
                 }
             } else {
-                DD_TRY(P.A(zk, P.w));
-                // classical Gram-Schmidt (twice when reorth)
-                const double vb = (double)sizeof(cplx<TV>) * n * nr;
-                Prof pr(h, PF_ORTHO, vb * ((k + 1) * (P.reorth ? 4 : 2) + 4));
-                DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol, st));
-                DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol, n, nr, -1.0, st));
-                if (P.reorth) {
-                    DD_TRY(bdot<TV>(kb, P.Vb, bstride, k + 1, P.w, n, nr, kb.hcol2, st));
-                    DD_TRY(baxpy<TV>(kb, P.w, true, P.Vb, bstride, k + 1, kb.hcol2, n, nr, -1.0, st));
-                    DD_TRY(add_columns(kb.hcol, kb.hcol2, (k + 1) * nr, st));
-                }
-                DD_TRY(bdot<TV>(kb, P.w, 0, 1, P.w, n, nr, kb.hcol + (size_t)(k + 1) * nr, st));
-                DD_TRY(arnoldi_update(s, k, kb.hcol, kb.scale, st));
-                DD_TRY(baxpy<TV>(kb, P.Vb + (size_t)(k + 1) * bstride, false, P.w, 0, 1, kb.scale, n, nr, 1.0, st));
+                DD_TRY(step_body());
             }
             ++total;
             if (P.fixed) {
@@ -1035,6 +1104,9 @@ static int coarse_solve(ddamg_handle* h, const cplx<T>* bc, cplx<T>* xc, int nrh
     P.w = w;
     P.wB = w;
     P.enabled_host = nullptr;
+    P.graph = true;  // A is two stencil launches on te and the handle's coarse operator
+    P.graph_sig = {te, h->half() ? (const void*)h->Bh : (const void*)L.cop.B, (const void*)(uintptr_t)h->NB, nullptr};
+    P.graph_prof_mask = 1u << PF_COARSE;
     KrylovResult R;
     DD_TRY((krylov<T, T, T>(h, h->kc, P, R)));
     long long it = 0;

@@ -225,6 +225,11 @@ def test_coarsest_operator_at_benchmark_shape(prec, tol):
         s.ml_build(v1, ddamg.ml_default_params(block1=blk, n_vec1=n1, nu1=2))
         assert rel(s.ml_apply_D2(e), ref) < tol
         assert rel(s.ml_apply_D2(e[:5]), ref[:5]) < tol
+        # level-1 V-cycles whose level-2 GMRES steps run eagerly, are captured as CUDA graphs, then
+        # replayed: the three agree bit for bit
+        x1 = synth.gaussian_coarse(4 ** 4, 2 * n0, nr, seed=146)
+        v1s = [s.ml_vcycle1(x1) for _ in range(3)]
+        assert all(np.array_equal(o, v1s[0]) for o in v1s[1:])
         if prec == "HALF":
             D2 = ml.levels[1].Dc
             r16 = lambda a: a.astype(np.float32).astype(np.float16).astype(np.float64)  # noqa: E731

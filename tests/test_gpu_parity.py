@@ -158,7 +158,11 @@ def test_coarse_solve_fixed_iterations(name, dd):
         with c.solver(dd.PREC_DOUBLE) as s:
             assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-13
         with c.solver(dd.PREC_SINGLE) as s:
-            assert relerr(s.coarse_solve(e, fixed_iters=k), ref) < 1e-6
+            # the FP32 Arnoldi steps run eagerly, are captured as CUDA graphs on the second call and
+            # replayed on the third: every call meets the oracle, and all three agree bit for bit
+            outs = [s.coarse_solve(e, fixed_iters=k) for _ in range(3)]
+            assert relerr(outs[0], ref) < 1e-6
+            assert all(np.array_equal(o, outs[0]) for o in outs[1:])
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -209,7 +213,10 @@ def test_half_precision_operators(dd):
         assert relerr(s.restrict(x), np.stack([agg.restrict(x[r]) for r in range(2)])) < 4e-3
         assert relerr(s.prolong(e), np.stack([agg.prolong(e[r]) for r in range(5)])) < 4e-3
         assert relerr(s.apply_Dc(e), np.stack([Dc.apply(e[r]) for r in range(5)])) < 4e-3
-        assert relerr(s.coarse_solve(e, fixed_iters=6), np.stack([cs.solve(e[r], fixed_iters=6) for r in range(5)])) < 2e-2
+        ref = np.stack([cs.solve(e[r], fixed_iters=6) for r in range(5)])
+        outs = [s.coarse_solve(e, fixed_iters=6) for _ in range(3)]  # eager, captured, replayed steps
+        assert relerr(outs[0], ref) < 2e-2
+        assert all(np.array_equal(o, outs[0]) for o in outs[1:])
 
 
 @pytest.mark.parametrize("prec,outer", [("DOUBLE", "DW"), ("SINGLE", "DW"), ("SINGLE", "REFINE"), ("HALF", "DW"),

@@ -124,6 +124,7 @@ struct KrylovBufs {
         cudaGraphExec_t exec = nullptr;
         std::array<uintptr_t, 12> sig{};
         bool seen = false;
+        size_t nkern = 0;  // kernel launches in the graph (counted again at every replay)
     };
     std::vector<StepGraph> graphs;
     bool graphs_off = false;  // a capture failed: steps of this solver run eagerly from then on
@@ -587,7 +588,7 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
             if constexpr (std::is_same<T, float>::value) {
                 if (f16) {
                     // half-precision V-cycle: links and site terms of the smoother stored in FP16
-                    const FineOpAoS16 op{LinksAoS16{h->Uaos16}, CloverAoS16{h->clov_aos16}, CloverAoS16{h->clovinv_aos16}};
+                    const FineOpAoS16 op{LinksAoS16{h->Uaos16}, CloverAoS16{h->clov_aos16}, CloverAoS16{h->clovinv_aos16}, h->d_tc_err};
                     DD_TRY(launch_sap_colour_aos16(h->g, op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
                     continue;
                 }
@@ -952,6 +953,7 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
                                                        (uintptr_t)P.graph_sig[3], (uintptr_t)(P.cycle_tol * 1e15)};
                 if (sg.exec && sg.sig == sig) {
                     DD_CUDA(cudaGraphLaunch(sg.exec, st));
+                    g_launches += sg.nkern;
                 } else if (sg.seen && sg.sig == sig) {  // second time: capture, then replay
                     if (sg.exec) cudaGraphExecDestroy(sg.exec);
                     sg.exec = nullptr;
@@ -960,6 +962,8 @@ static int krylov(ddamg_handle* h, KrylovBufs& kb, KrylovProblem<TB, TV, TZ>& P,
                     cudaGraph_t g = nullptr;
                     cudaError_t e = cudaStreamEndCapture(st, &g);
                     if (rc == 0 && e == cudaSuccess) {
+                        // (the capture counted the graph's launches once: they run once right below)
+                        if (cudaGraphGetNodes(g, nullptr, &sg.nkern) != cudaSuccess) sg.nkern = 0;
                         e = cudaGraphInstantiate(&sg.exec, g, 0);
                         if (e != cudaSuccess) sg.exec = nullptr;
                     }

@@ -65,22 +65,6 @@ __device__ __forceinline__ void load_link(cplx<float> (&W)[9], const LinksAoS16&
         W[k] = mk(f.x, f.y);
     }
 }
-// FP16 per-site links of one block staged in shared memory ([local site][4][3] uint4, the global
-// layout of LinksAoS16 from site `base` on)
-struct LinksSmem16 {
-    const uint4* s;
-    int base;
-};
-__device__ __forceinline__ void load_link(cplx<float> (&W)[9], const LinksSmem16& U, int /*V*/, int mu, int i) {
-    const uint4* q = U.s + ((i - U.base) * 4 + mu) * 3;
-    const uint4 a = q[0], b = q[1], c = q[2];
-    const unsigned w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float2 f = h2f(w[k]);
-        W[k] = mk(f.x, f.y);
-    }
-}
 // acc += hop of psi_n (the neighbour spinor) through link W in direction MU,
 // FWD: (I - gamma_mu) (x) W with W = U_mu(x);  !FWD: (I + gamma_mu) (x) W^H with W = U_mu(x - mu).
 // acc collects  [g ; -s B^H g],  g = W h (or W^H h), s = +1 forward / -1 backward.

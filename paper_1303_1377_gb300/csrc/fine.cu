@@ -9,7 +9,6 @@
 //                                 each 6 real diagonal entries + 15 complex upper entries
 #include <cuda_fp16.h>
 
-#include "bulk.cuh"
 #include "kernels.h"
 #include "dirac.cuh"
 #include "dw.cuh"
@@ -579,27 +578,12 @@ __device__ __forceinline__ void site_D44(const Geom& g, const OpT& op, const cpl
     for (int k = 0; k < 12; ++k) out.v[k] = out.v[k] - T(0.5) * acc.v[k];
 }
 
-// FP16 operator (FineOpAoS16): the block's links (256 sites x 4 x 48 bytes, contiguous in the
-// per-site layout) are brought into shared memory by one bulk copy issued at the start, which runs
-// while the prologue forms the residual from global memory; the in-block hops of the MR steps then
-// read their links from shared memory.  A copy that does not complete within about a second sets
-// op.err and leaves z untouched.
-constexpr int kSap44Links = 256 * 4 * 3;  // uint4 per staged block
-template <typename OpT>
-__host__ __device__ constexpr bool sap44_stages() {
-    return std::is_same<OpT, FineOpAoS16>::value;
-}
-template <typename OpT>
-__host__ __device__ constexpr size_t sap44_smem_base() {
-    return (size_t)4 * (36 * 128 + 4) * sizeof(cplx<float>) + (size_t)16 * 4 * sizeof(float4) + 4 * sizeof(cplx<float>);
-}
-
 template <typename OpT>
 __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cplx<float>* __restrict__ bsrc, cplx<float>* __restrict__ z,
                                                        int colour, int nrhs, int mr_steps) {
     using T = float;
     constexpr int R = 4, H = 128, NW = 16;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ unsigned char smem_raw[];
     const int slot = threadIdx.x % R;
     const int t = threadIdx.x / R;
     const int slot_stride = 36 * H + 4;  // complex numbers per slot (+4: bank offset between slots)
@@ -618,23 +602,6 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
     const size_t off = (size_t)(act ? r : 0) * 12 * g.V;
     const cplx<T>* b = bsrc + off;
     cplx<T>* zr = z + off;
-    // the links of the MR steps: staged in shared memory (FP16 operator) or read from global memory
-    uint4* Ls = reinterpret_cast<uint4*>(smem_raw + sap44_smem_base<OpT>());
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(Ls + kSap44Links);
-    if constexpr (sap44_stages<OpT>()) {
-        if (threadIdx.x == 0) {
-            mbar_init(bar, 1);
-            mbar_arrive_expect_tx(bar, kSap44Links * 16u);
-            bulk_g2s(Ls, op.U.p + (size_t)blk * kSap44Links, kSap44Links * 16u, bar);
-        }
-    }
-    auto mr_links = [&]() {
-        if constexpr (sap44_stages<OpT>())
-            return LinksSmem16{Ls, blk * 256};
-        else
-            return op.U;
-    };
-    const auto UL = mr_links();
     {
         int bn[8];
 #pragma unroll
@@ -653,21 +620,11 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
         }
     }
     __syncthreads();  // every read of z in this block is done: z may be updated from here on
-    if constexpr (sap44_stages<OpT>()) {
-        const bool ok = mbar_wait_bounded(bar, 0);
-        if (__syncthreads_or(!ok)) {  // the links never arrived: flag it, let the copy drain, leave z as it was
-            if (threadIdx.x == 0) {
-                if (op.err) atomicExch(op.err, 1);
-                mbar_wait_bounded(bar, 0);
-            }
-            return;
-        }
-    }
     if (act) {  // z_e += A_ee^{-1} r_e; rho = r_o - D_oe A_ee^{-1} r_e; x_o = 0
 #pragma unroll
         for (int k = 0; k < 12; ++k) zr[(size_t)k * g.V + ie] = zr[(size_t)k * g.V + ie] + SE[k * H + t];
         Spinor<T> hs;
-        hops44(UL, SE, Lo, nb_even, io, hs);
+        hops44(op.U, SE, Lo, nb_even, io, hs);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             SO[k * H + t] = SX[k * H + t] + T(0.5) * hs.v[k];
@@ -678,7 +635,7 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
     for (int it = 0; it < mr_steps; ++it) {
         if (act) {  // even: SE = A_ee^{-1} D_eo rho
             Spinor<T> hs, tmp2;
-            hops44(UL, SO, Le, nb_odd, ie, hs);
+            hops44(op.U, SO, Le, nb_odd, ie, hs);
 #pragma unroll
             for (int k = 0; k < 12; ++k) hs.v[k] = T(-0.5) * hs.v[k];
             herm_apply(op.clovinv, g.V, ie, hs, tmp2);
@@ -693,7 +650,7 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
 #pragma unroll
             for (int k = 0; k < 12; ++k) rho.v[k] = SO[k * H + t];
             herm_apply(op.clov, g.V, io, rho, sr);
-            hops44(UL, SE, Lo, nb_even, io, hs);
+            hops44(op.U, SE, Lo, nb_even, io, hs);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 sr.v[k] = sr.v[k] + T(0.5) * hs.v[k];
@@ -739,7 +696,7 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
     }
     if (act) {  // x_e = A_ee^{-1} (r_e - D_eo x_o); z += x
         Spinor<T> hs, tmp2;
-        hops44(UL, SX, Le, nb_odd, ie, hs);
+        hops44(op.U, SX, Le, nb_odd, ie, hs);
 #pragma unroll
         for (int k = 0; k < 12; ++k) hs.v[k] = T(0.5) * hs.v[k];  // x_e = A_ee^{-1} r_e (added above) + A_ee^{-1} (1/2 hops x_o)
         herm_apply(op.clovinv, g.V, ie, hs, tmp2);
@@ -754,8 +711,8 @@ __global__ void __launch_bounds__(512, 1) sap44_kernel(Geom g, OpT op, const cpl
 template <typename OpT>
 static int launch_sap44(const Geom& g, const OpT& op, const cplx<float>* b, cplx<float>* z, int colour, int nrhs, int mr_steps,
                         cudaStream_t st) {
-    constexpr int R = 4, H = 128;
-    const size_t smem = sap44_smem_base<OpT>() + (sap44_stages<OpT>() ? (size_t)kSap44Links * 16 + 16 : 0);
+    constexpr int R = 4, H = 128, NW = 16;
+    const size_t smem = (size_t)R * (36 * H + 4) * sizeof(cplx<float>) + (size_t)NW * R * sizeof(float4) + R * sizeof(cplx<float>);
     // set once per kernel instance (a function-local static initialiser is thread safe)
     static const bool attr = [] {
         cudaFuncSetAttribute(sap44_kernel<OpT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

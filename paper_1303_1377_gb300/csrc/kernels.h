@@ -23,7 +23,6 @@ struct FineOpAoS {  // LinksAoS, CloverAoS: common.cuh
 struct FineOpAoS16 {
     LinksAoS16 U;
     CloverAoS16 clov, clovinv;
-    int* err = nullptr;  // set to 1 by a SAP kernel whose bulk copy of a block's links did not complete
 };
 
 // coarse stencil in storage type S (float, double or __half2 packed as cplx<half>)

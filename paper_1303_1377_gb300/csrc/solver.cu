@@ -588,7 +588,7 @@ static int sap(ddamg_handle* h, const cplx<T>* b, cplx<T>* z, int nrhs, int nu) 
             if constexpr (std::is_same<T, float>::value) {
                 if (f16) {
                     // half-precision V-cycle: links and site terms of the smoother stored in FP16
-                    const FineOpAoS16 op{LinksAoS16{h->Uaos16}, CloverAoS16{h->clov_aos16}, CloverAoS16{h->clovinv_aos16}, h->d_tc_err};
+                    const FineOpAoS16 op{LinksAoS16{h->Uaos16}, CloverAoS16{h->clov_aos16}, CloverAoS16{h->clovinv_aos16}};
                     DD_TRY(launch_sap_colour_aos16(h->g, op, b, z, colour, nrhs, h->p.mr_steps, h->stream));
                     continue;
                 }

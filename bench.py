@@ -380,6 +380,33 @@ def run_small(name, reps=3):
     return out
 
 
+def gpu_local_cpus(dev):
+    """The host CPUs that nvidia-smi lists as local to CUDA device `dev` (matched by UUID), or None.
+    Pinned buffers first touched by a thread running there sit in the GPU's own host memory."""
+    import torch
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid).lower()
+        q = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"], capture_output=True, text=True,
+                           timeout=30).stdout
+        idx = next((int(line.split(",")[0]) for line in q.splitlines()
+                    if len(line.split(",")) >= 2 and line.split(",")[1].strip().lower().endswith(uuid)), None)
+        if idx is None:
+            return None
+        topo = [line.split("\t") for line in subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True,
+                                                             timeout=30).stdout.splitlines() if line.strip()]
+        head = [c.strip() for c in topo[0]]
+        col = head.index("CPU Affinity")
+        row = next(r for r in topo[1:] if r[0].strip() == f"GPU{idx}")
+        cpus = set()
+        for part in row[col].strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        return cpus & os.sched_getaffinity(0) or None
+    except Exception:  # no nvidia-smi, another table layout: leave the placement to the OS
+        return None
+
+
 def measure_dslash(solver, b, hbm_peak, reps=10):
     """FP32 and FP64 Dslash (the fine D of Sec. 2.2) on the batch b (device, complex128): average launch
     time from the library's per-launch CUDA events and the algorithmic bytes per launch (links and site
@@ -582,6 +609,12 @@ def main():
     # in, z comes out; the zero-guess entry point never reads z (the paper's zero initial guess)
     e2e = None
     if not args.no_e2e:
+        # the host buffers go to the GPU's own host memory: this thread runs on the GPU's local CPUs
+        # while it allocates and first touches them (the oracle's worker pool later gets every core)
+        aff0 = os.sched_getaffinity(0)
+        local_cpus = gpu_local_cpus(local)
+        if local_cpus:
+            os.sched_setaffinity(0, local_cpus)
         bhost = torch.from_numpy(bh).pin_memory()
         zhost = torch.empty_like(bhost).pin_memory()
         solver.set_stream(None)
@@ -609,7 +642,9 @@ def main():
         del dev
         e2e = {"value": world * nr * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "entry": "ddamg_ml_solve_zero_guess" if args.levels == 3 else "ddamg_solve_batch_zero_guess",
-               "host_link_copy": link}
+               "host_link_copy": link,
+               "host_cpus": f"{len(local_cpus)} CPUs local to the GPU (nvidia-smi topo)" if local_cpus else "placement left to the OS"}
+        os.sched_setaffinity(0, aff0)
     # roofline of the dominant kernel: HBM-bound families against the measured copy bandwidth;
     # families whose algorithmic flops per byte exceed the FP32 ridge against the FP32 FMA peak
     # (SMs x 128 FP32 lanes x 2 flops x the maximum SM clock)

@@ -34,3 +34,33 @@ def test_both_arms_share_metric_and_workload_text():
     assert bench.metric_name("32x32x32x64") == "solves/s to rel. residual 1e-10 (32^3x64, 12 point sources)"
     d = bench.workload_description("32x32x32x64", w, -0.931885)
     assert "32x32x32x64 lattice (L0=64)" in d and "12 point sources per step" in d and "N_v=20" in d
+
+
+def test_gpu_local_cpus_from_the_topology_table(monkeypatch):
+    """The end-to-end host buffers are placed from the CPUs nvidia-smi lists as local to the GPU:
+    the device is found by UUID, the CPU Affinity column parsed (ranges and lists) and intersected
+    with the process's own CPUs; anything unexpected leaves the placement to the OS."""
+    import os
+    import types
+
+    import torch
+
+    table = ("\tGPU0\tGPU1\tNIC0\tCPU Affinity\tNUMA Affinity\tGPU NUMA ID\n"
+             "GPU0\t X \tNV18\tSYS\t0-1,3\t0\t2\n"
+             "GPU1\tNV18\t X \tSYS\t4-5\t1\t3\n"
+             "NIC0\tSYS\tSYS\t X \t\t\t\n")
+
+    def run(cmd, **kw):
+        out = table if "topo" in cmd else "0, GPU-aaaa-0000\n1, GPU-bbbb-1111\n"
+        return types.SimpleNamespace(stdout=out)
+
+    monkeypatch.setattr(bench.subprocess, "run", run)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: types.SimpleNamespace(uuid="bbbb-1111"))
+    monkeypatch.setattr(os, "sched_getaffinity", lambda pid: {0, 1, 2, 3, 4})
+    assert bench.gpu_local_cpus(0) == {4}  # GPU1's CPUs 4-5, of which this process may use 4
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: types.SimpleNamespace(uuid="aaaa-0000"))
+    assert bench.gpu_local_cpus(0) == {0, 1, 3}
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: types.SimpleNamespace(uuid="cccc-2222"))
+    assert bench.gpu_local_cpus(0) is None  # not listed
+    monkeypatch.setattr(bench.subprocess, "run", lambda cmd, **kw: types.SimpleNamespace(stdout="no table here"))
+    assert bench.gpu_local_cpus(0) is None

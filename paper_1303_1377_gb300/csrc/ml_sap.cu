@@ -9,8 +9,8 @@
 // its 27 launches per colour and their round trips of every MR vector through global memory.
 //
 // Thread (group h, slot s, row a) owns component a of the block's s-th even site and of its s-th odd
-// site, for the right-hand sides 6h..6h+5 of the CTA (two groups: twice the warps of one thread per
-// row, and half the accumulators per thread).  A block of D_1 is read by its nc row threads as one
+// site, for the right-hand sides 4h..4h+3 of the CTA (three groups: three times the warps of one
+// thread per row, and a third of the accumulators per thread).  A block of D_1 is read by its nc row threads as one
 // coalesced column per step (the second group finds it in L1); the vector it multiplies is read
 // from shared memory, one broadcast per column and right-hand-side pair.
 #include "kernels.h"
@@ -21,7 +21,7 @@ namespace ddamg {
 namespace {
 
 constexpr int kR = 12;  // right-hand sides per CTA
-constexpr int kT = 6;   // right-hand sides per thread (kR / kT thread groups)
+constexpr int kT = 4;   // right-hand sides per thread (kR / kT thread groups)
 constexpr int kG = kR / kT;
 
 // shared-memory vector of one half block: [slot][component][kR]
@@ -74,7 +74,7 @@ __device__ __forceinline__ void zero(cplx<float> (&acc)[kT]) {
 }  // namespace
 
 template <bool H16>
-__global__ void __launch_bounds__(768, 1) ml_sap_fused_kernel(MLView<float> v, const cplx<float>* __restrict__ b,
+__global__ void __launch_bounds__(1024, 1) ml_sap_fused_kernel(MLView<float> v, const cplx<float>* __restrict__ b,
                                                               cplx<float>* __restrict__ z, int nrhs, int colour, int mr_steps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = v.nc, He = v.Vb1e, Vb = v.Vb1;
@@ -259,7 +259,7 @@ static size_t ml_sap_fused_smem(const MLView<float>& v) {
 }
 
 bool ml_sap_fused_supported(const MLView<float>& v) {
-    return v.Vb1 == 2 * v.Vb1e && kG * v.Vb1e * v.nc <= 768 && v.nc % 2 == 0 && ml_sap_fused_smem(v) <= 227 * 1024;
+    return v.Vb1 == 2 * v.Vb1e && kG * v.Vb1e * v.nc <= 1024 && v.nc % 2 == 0 && ml_sap_fused_smem(v) <= 227 * 1024;
 }
 
 int launch_ml_sap_fused(const MLView<float>& v, const cplx<float>* b, cplx<float>* z, int nrhs, int colour, int mr_steps,

@@ -2118,7 +2118,6 @@ static int apply_Dc_T(ddamg_handle* h, const double* in, double* out, int n_rhs)
     cplx<T>* a = h->ws_fine[4].as<cplx<T>>();
     cplx<T>* o = a + cn * n_rhs;
     DD_TRY(coarse_in<T>(h, in, n_rhs, a));
-    Level<T> L = level<T>(h);
     {
         Prof pr(h, PF_COARSE, (double)h->NB * 9 * h->nc * h->nc * sizeof(cplx<T>));
         DD_TRY(c_full<T>(h, a, o, n_rhs));

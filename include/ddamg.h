@@ -346,7 +346,11 @@ void ddamg_debug_fail_allocs(int n);
  *   the level-1 V-cycle (inner = 0), or one level-1 V-cycle (inner = 1).
  * P_1, D_2 and its inverses are built in FP64; the level-1 and level-2 solves run in the handle's
  * V-cycle precision (FP64 on DOUBLE handles, FP32 on SINGLE and HALF handles, with FP32 copies of
- * D_1, P_1, D_2 and the inverses).  The third level is tied to the coarse operator it was built
+ * D_1, P_1, D_2 and the inverses).  HALF handles also keep FP16 copies: the level-1 SAP reads D_1 and
+ * its even inverses in FP16 (FP32 arithmetic), and the coarsest level's GMRES and ddamg_ml_apply_D2
+ * apply D_2 (and its even inverses) from FP16 tensor-core fragments, with each right-hand-side entry
+ * entering as an FP16 hi + lo pair so that the product is the FP16-rounded matrix times the FP32
+ * vector to about 2^-22 (2 n_vec1 divisible by 8; otherwise FP32).  The third level is tied to the coarse operator it was built
  * from: after ddamg_run_setup, ddamg_setup_from_vectors or ddamg_set_mass the calls below return
  * DDAMG_ERR_NOT_READY until ddamg_ml_build runs again.
  * Level-1 vectors use the coarse layout of ddamg_restrict ([n_rhs][coarse sites lex][2N]);

@@ -64,3 +64,39 @@ def test_gpu_local_cpus_from_the_topology_table(monkeypatch):
     assert bench.gpu_local_cpus(0) is None  # not listed
     monkeypatch.setattr(bench.subprocess, "run", lambda cmd, **kw: types.SimpleNamespace(stdout="no table here"))
     assert bench.gpu_local_cpus(0) is None
+
+
+def test_workload_masses_follow_their_records():
+    """A workload's mass is its lattice's recorded m0, or -Re(lambda_L) + the workload's own gap when
+    it sets one (the 48^3 x 96 workload: edge + 1e-3)."""
+    import json
+
+    data = json.load(open(bench.WORKLOADS_JSON))
+    for name, w in bench.WORKLOADS.items():
+        m0, rec = bench.workload_m0(w)
+        assert rec is data[w["m0_key"]] or rec == data[w["m0_key"]]
+        if "gap" in w:
+            assert abs(m0 - (-rec["lambda_L_m0_0"][0] + w["gap"])) < 1e-12
+        else:
+            assert m0 == float(rec["m0"])
+    m48, rec48 = bench.workload_m0(bench.WORKLOADS["48x48x48x96"])
+    assert abs(m48 - (-1.188968176108723 + 1e-3)) < 1e-9 and rec48["dims"] == [96, 48, 48, 48]
+
+
+def test_spectral_edge_record_merges_into_the_workload_file(tmp_path, monkeypatch):
+    """spectral_edge --record merges a record written by --out (on the GPU machine) into the workload
+    file, leaving the other entries as they were."""
+    import json
+    import sys
+
+    from paper_1303_1377_gb300 import spectral_edge
+
+    wl = tmp_path / "workloads.json"
+    wl.write_text(json.dumps({"a": {"m0": 1.0}, "b": {"m0": 2.0}}))
+    rec = tmp_path / "edge.json"
+    rec.write_text(json.dumps({"b": {"m0": -3.0, "lambda_L_m0_0": [3.0, 0.0]}}))
+    monkeypatch.setattr(spectral_edge, "WORKLOADS", str(wl))
+    monkeypatch.setattr(sys, "argv", ["spectral_edge", "--record", str(rec)])
+    spectral_edge.main()
+    out = json.loads(wl.read_text())
+    assert out == {"a": {"m0": 1.0}, "b": {"m0": -3.0, "lambda_L_m0_0": [3.0, 0.0]}}

@@ -223,8 +223,8 @@ int gauge_to_internal(const cplx<double>* in, cplx<double>* out, const int* lex_
     return 0;
 }
 
-// Hessenberg bookkeeping of batched (F)GMRES: one thread per right-hand side.
-// Column k of H arrives in hcol[i * nrhs + r] (i <= k) with hnorm = ||w|| in hcol[(k+1) * nrhs + r].
+// Hessenberg bookkeeping of batched (F)GMRES: one thread per right-hand side (the update: one warp).
+// Column k of H arrives in hcol[i * nrhs + r] (i <= k) with ||w||^2 in hcol[(k+1) * nrhs + r].re.
 // One warp per right-hand side: the lanes fetch the new Hessenberg column and the stored rotations
 // side by side into shared memory, lane 0 applies the rotations in order (the only sequential part),
 // and the lanes write the column back.
